@@ -1,0 +1,28 @@
+"""Plain FP64 CPU oracle for the Basic Scheme on anisotropic patterns.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product package may import, call or
+link this package; only ``tests/``, ``__graft_entry__.smoke()`` and the CPU
+baseline legs of ``bench.py`` use it.  It shares no code with the CUDA path.
+
+Everything here follows Bergmann & Merkert, "FFT-based homogenization on
+periodic anisotropic translation invariant spaces" (arXiv 1701.04685):
+
+* ``lattice``    -- pattern P(M), generating set G(M^T), pattern DFT (Sec. 2.1,
+                    Eqs. (Fouriermatrix), (FourierTransform)); an independent
+                    Smith-normal-form index map used by the fast variant.
+* ``material``   -- Mandel layout of Sym_d / SSym_d (Sec. 3.1) and isotropic
+                    stiffness tensors.
+* ``generators`` -- Fourier symbols of the Dirichlet kernel, the de la Vallee
+                    Poussin means and the periodised box splines (Sec. 2.2,
+                    Def. dlVP) and the orthonormalised alias weights
+                    (Lemma FI:Props (iii)).
+* ``green``      -- Green operator Gamma^0 (Def. projection, Eq. (gamma)) and the
+                    periodised Green operator Gamma^p (Def.
+                    gamma_tilde_fourier).
+* ``scheme``     -- fixed-point iteration on Eq. (pde_coefficients), Cauchy
+                    residual (Sec. 4) and the effective stiffness (Sec. 3.1).
+
+Parity status: every function is pinned by ``tests/test_oracle_*.py`` except
+the reference-medium rule (``material.reference_medium_ms``), which the paper
+never states: parity unpinned.
+"""

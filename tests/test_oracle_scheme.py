@@ -1,0 +1,155 @@
+"""Pins of the oracle's fixed-point iteration (Eq. (pde_coefficients), Sec. 4) and C_eff."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import generators as G
+from oracle import green, material, scheme
+
+
+def _setup(M, gen, phases, phase_of, transform_cls=scheme.SNFTransform, C0=None):
+    d = len(M)
+    T = transform_cls(M)
+    ids = phase_of(T.points / T.D)
+    lm = [material.lame(E, nu) for E, nu in phases]
+    Cp = np.stack([material.isotropic_mandel(l, m, d) for l, m in lm])
+    if C0 is None:
+        l0, m0 = material.reference_medium_ms([l for l, _ in lm], [m for _, m in lm])
+        C0 = material.isotropic_mandel(l0, m0, d)
+    C = Cp[ids]
+    Gp = green.gamma_p_table(M, gen, C0, T.freqs)
+    return T, C, C0, Gp, ids, Cp
+
+
+def _disk_phase(r, c=(0.1, -0.05)):
+    return lambda y: W.phase_ids(y, np.array([c]), np.array([r]))
+
+
+GENS2 = [G.Generator("dirichlet"), G.Generator("dlvp", alpha=[0.25, 0.25]),
+         G.Generator("dlvp", alpha=[0.45, 0.0]),
+         G.Generator("boxspline", xi=G.tensor_boxspline_xi(2, 2), radius=4)]
+
+
+@pytest.mark.parametrize("gen", GENS2, ids=lambda g: g.kind + str(g.alpha))
+def test_homogeneous_medium_converges_in_one_step(gen):
+    """C constant: tau is constant, its DFT lives at h = 0 only, and E^_0 = 0 -> E = 0."""
+    M = [[12, 3], [0, 10]]
+    T, C, C0, Gp, _, _ = _setup(M, gen, [(7.0, 0.3), (7.0, 0.3)], lambda y: np.zeros(len(y), int),
+                                C0=material.isotropic_mandel(1.0, 2.0, 2))
+    out = scheme.solve(T, Gp, C, C0, np.eye(3), tol=0.0, max_iter=2)
+    assert np.abs(out["E"]).max() < 1e-13
+    assert all(h[1] < 1e-13 for h in out["resid"])
+
+
+@pytest.mark.parametrize("M", [[[6, 2], [0, 5]], [[4, -2], [4, 14]], [[3, 1, 0], [0, 2, 1], [1, 0, 3]]])
+def test_brute_dft_route_equals_snf_route(M, rng):
+    d = len(M)
+    gen = G.Generator("dlvp", alpha=[0.3] * d)
+    cen = rng.uniform(-0.5, 0.5, size=(1, d))
+    ph = lambda y: W.phase_ids(y, cen, np.array([0.3]))
+    Tb, Cb, C0, Gpb, _, _ = _setup(M, gen, [(1.0, 0.3), (20.0, 0.25)], ph, scheme.BruteTransform)
+    Ts, Cs, _, Gps, _, _ = _setup(M, gen, [(1.0, 0.3), (20.0, 0.25)], ph, scheme.SNFTransform)
+    e0 = np.eye(material.nv(d))[:2]
+    ob = scheme.solve(Tb, Gpb, Cb, C0, e0, max_iter=12)
+    os_ = scheme.solve(Ts, Gps, Cs, C0, e0, max_iter=12)
+    idx = {tuple(p): i for i, p in enumerate(Tb.points.tolist())}
+    perm = np.array([idx[tuple(p)] for p in Ts.points.tolist()])
+    assert np.abs(ob["E"][:, perm] - os_["E"]).max() < 1e-12
+    assert ob["imag_max"].max() < 1e-13
+
+
+def test_forms_A_and_B_agree_iff_dirichlet():
+    """Remark constants: eps - Gamma^p C0 eps = eps0 holds iff Dirichlet, so the paper's
+    form (A) and the strain-update form (B) give the same iterates only then."""
+    M = [[15, 4], [0, 17]]   # odd det: no boundary frequencies
+    ph = _disk_phase(0.3)
+    for gen, same in [(G.Generator("dirichlet"), True), (G.Generator("dlvp", alpha=[0.25, 0.25]), False)]:
+        T, C, C0, Gp, _, _ = _setup(M, gen, [(1.0, 0.3), (10.0, 0.3)], ph)
+        a = scheme.solve(T, Gp, C, C0, np.eye(3), max_iter=15, form="A")
+        b = scheme.solve(T, Gp, C, C0, np.eye(3), max_iter=15, form="B")
+        diff = np.abs(a["E"] - b["E"]).max()
+        if same:
+            assert diff < 1e-12
+        else:
+            assert diff > 1e-6
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_laminate_matches_lamination_formulas(axis):
+    """Grid-aligned laminate with Dirichlet kernel on diag(N,N): C_eff equals the textbook
+    lamination formulas evaluated with the sampled volume fractions."""
+    N = 16
+    M = [[N, 0], [0, N]]
+    phases = [(1.0, 0.3), (12.0, 0.22)]
+    T, C, C0, Gp, ids, _ = _setup(M, G.Generator("dirichlet"), phases,
+                                  lambda y: W.laminate_ids(y, axis, 0.35))
+    out = scheme.solve(T, Gp, C, C0, np.eye(3), tol=1e-14, max_iter=3000)
+    Ceff = scheme.effective_stiffness(out["mean_stress"], np.eye(3))
+    lam = np.array([material.lame(E, nu)[0] for E, nu in phases])[ids]
+    mu = np.array([material.lame(E, nu)[1] for E, nu in phases])[ids]
+    P = lam + 2 * mu
+    n_n = 1.0 / np.mean(1.0 / P)                               # C_nnnn
+    n_t = np.mean(lam / P) * n_n                               # C_nntt
+    t_t = np.mean(P - lam ** 2 / P) + np.mean(lam / P) ** 2 * n_n
+    s_s = 1.0 / np.mean(1.0 / mu)                              # C_ntnt
+    n, t = (0, 1) if axis == 0 else (1, 0)
+    expect = np.zeros((3, 3))
+    expect[n, n], expect[t, t] = n_n, t_t
+    expect[n, t] = expect[t, n] = n_t
+    expect[2, 2] = 2 * s_s                                     # Mandel shear entry
+    assert np.abs(Ceff - expect).max() / np.abs(expect).max() < 1e-10
+
+
+@pytest.mark.parametrize("gen", GENS2, ids=lambda g: g.kind + str(g.alpha))
+def test_ceff_symmetric(gen):
+    M = [[16, 0], [0, 16]] if gen.kind == "dirichlet" else [[15, 4], [0, 17]]
+    T, C, C0, Gp, _, _ = _setup(M, gen, [(1.0, 0.3), (10.0, 0.3)], _disk_phase(0.25))
+    out = scheme.solve(T, Gp, C, C0, np.eye(3), tol=1e-13, max_iter=3000)
+    Ce = scheme.effective_stiffness(out["mean_stress"], np.eye(3))
+    assert np.abs(Ce - Ce.T).max() / np.abs(Ce).max() < 1e-10
+
+
+def test_ceff_between_reuss_and_voigt():
+    """Galerkin energy argument (Dirichlet): <C^-1>^-1 <= C_eff <= <C> in Loewner order."""
+    M = [[16, 0], [0, 16]]
+    T, C, C0, Gp, _, _ = _setup(M, G.Generator("dirichlet"), [(1.0, 0.3), (30.0, 0.2)],
+                                _disk_phase(0.3))
+    out = scheme.solve(T, Gp, C, C0, np.eye(3), tol=1e-13, max_iter=5000)
+    Ce = scheme.effective_stiffness(out["mean_stress"], np.eye(3))
+    Ce = 0.5 * (Ce + Ce.T)
+    voigt = C.mean(axis=0)
+    reuss = np.linalg.inv(np.linalg.inv(C).mean(axis=0))
+    assert np.linalg.eigvalsh(voigt - Ce).min() > -1e-10
+    assert np.linalg.eigvalsh(Ce - reuss).min() > -1e-10
+    assert np.linalg.eigvalsh(voigt - Ce).max() > 1e-3   # not trivially equal
+
+
+@pytest.mark.parametrize("gen", GENS2[:2] + GENS2[3:], ids=lambda g: g.kind)
+def test_converged_iterate_solves_discrete_equation(gen):
+    """At the fixed point, E + Gamma^p (C - C0)(E + eps0) = 0 (Eq. (pde_coefficients)),
+    checked with the literal DFT matrix while the iteration used the FFT route."""
+    M = [[6, 2], [0, 5]]
+    ph = _disk_phase(0.3, (0.0, 0.0))
+    Ts, Cs, C0, Gps, _, _ = _setup(M, gen, [(1.0, 0.3), (8.0, 0.3)], ph)
+    out = scheme.solve(Ts, Gps, Cs, C0, np.eye(3), tol=1e-14, max_iter=3000)
+    Tb, Cb, _, Gpb, _, _ = _setup(M, gen, [(1.0, 0.3), (8.0, 0.3)], ph, scheme.BruteTransform)
+    idx = {tuple(p): i for i, p in enumerate(Ts.points.tolist())}
+    perm = np.array([idx[tuple(p)] for p in Tb.points.tolist()])
+    for L in range(3):
+        E = out["E"][L][perm]
+        e0 = np.eye(3)[L][None, :]
+        tau = np.einsum("mab,mb->ma", Cb - C0, E + e0)
+        res = E + scheme.apply_operator(Tb, Gpb, tau).real
+        # Gamma^p_0 tau^_0 is dropped by the mean-strain constraint; it is 0 anyway here
+        assert np.abs(res).max() < 1e-11
+
+
+def test_literal_dirichlet_complex_iterate():
+    """Literal half-open Dirichlet symbol: real iterate on odd det, complex on even det."""
+    ph = _disk_phase(0.3)
+    for M, real in [([[7, 0], [0, 9]], True), ([[8, 0], [0, 8]], False)]:
+        T, C, C0, Gp, _, _ = _setup(M, G.Generator("dirichlet_literal"), [(1.0, 0.3), (10.0, 0.3)],
+                                    ph, scheme.BruteTransform)
+        out = scheme.solve(T, Gp, C, C0, np.eye(3), max_iter=5, complex_iterate=True)
+        im = np.abs(out["E"].imag).max()
+        assert (im < 1e-13) if real else (im > 1e-6)
