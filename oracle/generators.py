@@ -26,7 +26,12 @@ weight of alias z of frequency h (u = M^{-T} h) is
     w_z(h) = g(u + z)^2 / sum_{z'} g(u + z')^2,
 
 the factor that multiplies Gamma^0 in Def. gamma_tilde_fourier.  The sum runs
-over z in {-R..R}^d; for the box spline R is the truncation radius.
+over the aliases with |u_i + z_i| <= R + 1/2 for every i (R is the truncation
+radius of the box spline): z_i in {-R..R}, plus z_i = R + 1 where u_i = -1/2.
+The paper only says the box-spline bracket sums are precomputed with finitely
+many terms (33^2 in Sec. 4.2); truncating to a cube that is symmetric in
+M^{-T} k keeps Gamma^p_{-h} = Gamma^p_h, so Gamma^p maps real fields to real
+fields.  For the frequency-compact symbols (Dirichlet, dlVP) nothing is cut.
 """
 from __future__ import annotations
 
@@ -57,7 +62,14 @@ def tensor_boxspline_xi(d, order):
 
 
 def alias_set(d, radius):
-    return np.array(list(itertools.product(range(-radius, radius + 1), repeat=d)), dtype=np.int64)
+    """Candidate shifts z in {-R..R+1}^d; ``alias_mask`` keeps |u + z| <= R + 1/2."""
+    return np.array(list(itertools.product(range(-radius, radius + 2), repeat=d)), dtype=np.int64)
+
+
+def alias_mask(unum, Z, D, radius):
+    """True where every |u_i + z_i| <= R + 1/2 (u = unum / D), evaluated exactly."""
+    t = np.abs(2 * (np.asarray(unum, dtype=np.int64)[..., None, :] + D * Z))
+    return np.all(t <= (2 * radius + 1) * D, axis=-1)
 
 
 def symbol(gen, unum, D):
@@ -94,6 +106,7 @@ def alias_weights(gen, unum, D):
     """Orthonormalised weights w_z for one frequency: returns (Z, w) with sum w = 1."""
     d = len(unum)
     Z = alias_set(d, gen.radius)
+    Z = Z[alias_mask(unum, Z, D, gen.radius)]
     g = symbol(gen, np.asarray(unum, dtype=np.int64)[None, :] + D * Z, D)
     s = np.sum(g * g)
     if s <= 0:

@@ -92,7 +92,9 @@ def gamma_p_table(M, gen, C0m, freqs):
     Mt = np.array(lattice.transpose(L.M), dtype=np.int64)
     unum = L.sign * (freqs @ adjT.T)                     # numerators of M^{-T} h
     Z = gen_mod.alias_set(d, gen.radius)
+    keep = gen_mod.alias_mask(unum, Z, D, gen.radius)                    # (n, nz)
     g = np.stack([gen_mod.symbol(gen, unum + D * z, D) for z in Z], axis=0)  # (nz, n)
+    g = g * keep.T
     s = np.sum(g * g, axis=0)
     if np.any(s <= 0):
         raise ValueError("orthonormalisation impossible: the alias sum of |c_k(f)|^2 vanishes")

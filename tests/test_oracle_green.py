@@ -209,7 +209,8 @@ def test_gamma_p_even_symbol_gives_real_operator(M):
     if len(H) > 4096:
         H = H[::37]
     Hn = np.array([lattice.reduce_freq(M, -h) for h in H])
-    for gen in (G.Generator("dirichlet"), G.Generator("dlvp", alpha=[0.25, 0.25])):
+    for gen in (G.Generator("dirichlet"), G.Generator("dlvp", alpha=[0.25, 0.25]),
+                G.Generator("boxspline", xi=G.tensor_boxspline_xi(2, 2), radius=3)):
         a = green.gamma_p_table(M, gen, C0, H)
         b = green.gamma_p_table(M, gen, C0, Hn)
         assert np.abs(a - b).max() < 1e-14
