@@ -1,0 +1,206 @@
+/*
+ * fftHomog.h -- C ABI of the GB300 Basic-Scheme solver for FFT-based
+ * homogenisation on anisotropic patterns.
+ *
+ * Method: Bergmann & Merkert, "FFT-based homogenization on periodic
+ * anisotropic translation invariant spaces", arXiv 1701.04685.  The library
+ * solves Eq. (pde_coefficients) of Thm. pde_discretization,
+ *
+ *     E_y + Gamma^p_y (C(y) - C0) : (E_y + eps0) = 0,      y in P(M),
+ *
+ * by the fixed-point iteration of Sec. 4 (Moulinec & Suquet), with the pattern
+ * DFT of Eq. (Fouriermatrix) evaluated as a d-dimensional FFT on the
+ * Smith-normal-form grid of M and the periodised Green operator Gamma^p of
+ * Def. gamma_tilde_fourier tabulated once in FP64.
+ *
+ * Conventions used by every entry point:
+ *  - Tensors are in Mandel form: a symmetric strain/stress is a vector of
+ *    n_v = 3 (d = 2: 11, 22, sqrt2*12) or n_v = 6 (d = 3: 11, 22, 33, sqrt2*23,
+ *    sqrt2*13, sqrt2*12) reals; a stiffness is a symmetric n_v x n_v matrix,
+ *    row-major.  The Frobenius product of Sec. 3.1 is the Euclidean product.
+ *  - Pattern points are stored in "storage order": row-major over the
+ *    non-trivial Smith-normal-form axes (the largest axis contiguous).
+ *    fh_pattern_points() gives each stored point's coordinates y.
+ *  - Host pointers are plain CPU memory.  Arguments documented as "host or
+ *    device" may be either; the library asks the CUDA runtime which one.
+ *  - Every call returns an fh_status; nothing aborts, traps or exits.  On an
+ *    error the thread-local message of fh_last_error() says what failed.
+ *  - A solver belongs to one CUDA stream; calls on one solver must not run
+ *    concurrently.  Different solvers are independent.
+ *  - The library allocates and owns all device work memory and the Gamma^p
+ *    table; the caller owns every buffer it passes in.
+ */
+#ifndef FFTHOMOG_H
+#define FFTHOMOG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FH_OK = 0,
+  FH_NOT_CONVERGED = 1,   /* max_iter reached; results are valid            */
+  FH_DIVERGED = 2,        /* residual kept growing; results are valid        */
+  FH_NONFINITE = 3,       /* NaN/Inf met in the residual; iteration stopped  */
+  FH_ERR_ARG = -1,        /* invalid argument                                */
+  FH_ERR_SINGULAR_M = -2, /* det M = 0                                       */
+  FH_ERR_OVERFLOW = -3,   /* sizes or integer index maps exceed int64/int32  */
+  FH_ERR_NO_ONB = -4,     /* alias sum of |c_k(f)|^2 vanishes: translates not
+                             linearly independent (Lemma FI:Props (ii))      */
+  FH_ERR_CUDA = -5,       /* a CUDA runtime call failed                      */
+  FH_ERR_TIMEOUT = -6,    /* reserved: a bounded device wait gave up         */
+  FH_ERR_INTERNAL = -7,   /* internal consistency check failed               */
+  FH_ERR_UNSUPPORTED = -8,/* e.g. an FFT axis with a prime factor > 13       */
+  FH_ERR_STATE = -9       /* call order violated (e.g. solve before stiffness) */
+} fh_status;
+
+/* Generator f of the space of translates V^f_M (Sec. 2.2). */
+typedef enum {
+  FH_GEN_DIRICHLET = 0,  /* Dirichlet kernel D_M; on boundary frequencies
+                            |(M^-T h)_i| = 1/2 the modified kernel's symbol
+                            1/2 is used so that Gamma^p is even (real).      */
+  FH_GEN_DLVP = 1,       /* de la Vallee Poussin mean, Def. dlVP: per-axis
+                            trapezoid g, flat for |u_i| <= 1/2 - alpha_i, zero
+                            for |u_i| >= 1/2 + alpha_i, linear in between.   */
+  FH_GEN_BOXSPLINE = 2   /* periodised pattern box spline: g(u) =
+                            prod_{xi in Xi} sinc(pi xi^T u), alias sums
+                            truncated to z in {-r..r}^d (Sec. 3.2 end).      */
+} fh_gen_kind;
+
+#define FH_MAX_XI 16
+#define FH_MAX_LOADS 16
+
+typedef struct {
+  int kind;                 /* fh_gen_kind                                   */
+  double alpha[3];          /* FH_GEN_DLVP: half ramp width per axis, [0,1/2];
+                               1/2 is the Fejer kernel, 0 the modified
+                               Dirichlet kernel                              */
+  int n_xi;                 /* FH_GEN_BOXSPLINE: number s of directions      */
+  double xi[3 * FH_MAX_XI]; /* FH_GEN_BOXSPLINE: direction k is
+                               xi[3k .. 3k+d-1]                               */
+  int alias_radius;         /* FH_GEN_BOXSPLINE: r in 0..16                  */
+} fh_generator;
+
+typedef enum { FH_PREC_FP64 = 0, FH_PREC_FP32 = 1 } fh_precision;
+
+typedef struct {
+  double tol;      /* Cauchy tolerance: a load stops after the first iteration n
+                      with r_n = ||E_n - E_{n-1}|| / ||E_n + eps0|| <= tol
+                      (Sec. 4; Frobenius l2 over P(M)).  0 = run max_iter.   */
+  int max_iter;    /* >= 1                                                    */
+  int precision;   /* fh_precision of the FFT, stress and Green stages; the
+                      table build, residual norms and mean stresses are FP64
+                      in every mode                                          */
+  int init;        /* 0: start from E = 0; 1: start from the strain left by
+                      the previous solve or set by fh_set_strain (resume)    */
+  int chunk;       /* iterations per captured CUDA-graph replay; 0 = 32      */
+} fh_solve_opts;
+
+typedef struct {
+  int iterations[FH_MAX_LOADS];        /* iterations run, per load            */
+  double residual[FH_MAX_LOADS];       /* last r_n, per load                  */
+  int status[FH_MAX_LOADS];            /* fh_status per load (0, 1, 2 or 3)   */
+  double mean_stress[FH_MAX_LOADS * 6];/* <C:(E+eps0)> per load, Mandel, FP64 */
+  double elapsed_ms;                   /* device time from first launch to
+                                          the mean-stress reduction          */
+} fh_result;
+
+typedef struct fh_pattern fh_pattern;
+typedef struct fh_solver fh_solver;
+
+/* Pattern P(M) and generating set G(M^T) of a regular integer matrix M
+ * (Sec. 2.1).  d in {2,3}; M is d x d row-major.  Builds the Smith normal form
+ * U M V = diag(d_1..d_d) in exact int64 arithmetic and the index maps
+ *   point n -> y = M^-1 U^-1 n reduced to [-1/2,1/2)^d,
+ *   frequency l -> h = V^-T l reduced to G(M^T),
+ * so that exp(-2 pi i h^T y) = exp(-2 pi i sum_i l_i n_i / d_i) and the pattern
+ * DFT of Eq. (Fouriermatrix) is a plain FFT on the grid.  Errors:
+ * FH_ERR_SINGULAR_M, FH_ERR_OVERFLOW (entries so large that the exact maps
+ * could overflow int64, or m >= 2^31), FH_ERR_ARG. */
+fh_status fh_pattern_create(int d, const int64_t* M, fh_pattern** out);
+void fh_pattern_destroy(fh_pattern* p);
+
+/* m = |det M|, the number of non-trivial SNF axes and their lengths in storage
+ * order (dims[ndims-1] is the contiguous one).  dims must hold 3 ints. */
+fh_status fh_pattern_info(const fh_pattern* p, int64_t* m, int* ndims, int* dims);
+
+/* Host array y[m*d]: coordinates of the stored points, y = a / m exactly with
+ * the integer numerators a of fh_pattern_numerators(). */
+fh_status fh_pattern_points(const fh_pattern* p, double* y);
+/* Host array a[m*d] of int64 numerators: y = a / m, -m <= 2a < m. */
+fh_status fh_pattern_numerators(const fh_pattern* p, int64_t* a);
+/* Host array h[nh*d] of the frequencies of the stored half spectrum: row-major
+ * over (l_0, .., l_{ndims-2}, l_last in [0, dims_last/2]).  nh is returned in
+ * *nh when h is NULL. */
+fh_status fh_pattern_half_freqs(const fh_pattern* p, int64_t* h, int64_t* nh);
+
+/* Solver for one pattern and generator on one CUDA stream (cudaStream_t,
+ * NULL = legacy default stream).  Allocates device work memory for up to
+ * nload_max load cases (1..FH_MAX_LOADS).  The pattern may be destroyed
+ * afterwards.  Errors: FH_ERR_ARG, FH_ERR_UNSUPPORTED (an SNF axis longer
+ * than 4096 or with a prime factor > 13), FH_ERR_CUDA. */
+fh_status fh_solver_create(const fh_pattern* p, const fh_generator* gen,
+                           int nload_max, void* cuda_stream, fh_solver** out);
+void fh_solver_destroy(fh_solver* s);
+
+/* Piecewise-constant stiffness (Sec. 3.1, C in SSym_d(L^inf)): phase[m]
+ * (uint8, storage order, host or device) selects one of nphase (1..16)
+ * Mandel matrices Cp[nphase*n_v*n_v] (host).  C is sampled at the pattern
+ * points (collocation, Thm. pde_discretization).  Errors: FH_ERR_ARG when a
+ * phase id >= nphase is found (checked on the device). */
+fh_status fh_set_stiffness_phases(fh_solver* s, const uint8_t* phase, int nphase,
+                                  const double* Cp);
+
+/* Reference medium C0 (n_v x n_v Mandel, host).  NULL selects the rule of
+ * Moulinec & Suquet (1998): isotropic with lambda0, mu0 the midpoints of the
+ * phases' ranges (phases read as isotropic: lambda = C[0][1], 2 mu = C[n_v-1]
+ * [n_v-1]).  The paper leaves C0 open.  Builds the Gamma^p table of
+ * Def. gamma_tilde_fourier on the device in FP64: for every stored frequency
+ * h, sum_z w_z(h) Gamma^0(h + M^T z) with the orthonormalised alias weights
+ * w_z = g(u+z)^2 / sum_z' g(u+z')^2, u = M^-T h (Lemma FI:Props (iii)), and
+ * Gamma^0(k) : tau = sym(k (x) K(k)^-1 tau k), K_ik = C0_ijkl k_j k_l
+ * (Def. projection).  Must follow fh_set_stiffness_phases.  Errors:
+ * FH_ERR_STATE, FH_ERR_NO_ONB, FH_ERR_ARG (C0 not positive definite). */
+fh_status fh_set_reference(fh_solver* s, const double* C0);
+
+/* Run the fixed point for nload (1..nload_max) macroscopic strains
+ * eps0[nload*n_v] (host, Mandel), all load cases together on the device:
+ *   tau = (C - C0):(E + eps0);  E^_h = -Gamma^p_h tau^_h,  E^_0 = 0;
+ *   E = inverse DFT;  r_n as in fh_solve_opts.tol.
+ * Each load stops on its own.  Fills *res (host).  Returns FH_OK when every
+ * load converged, else the worst per-load status (FH_NONFINITE >
+ * FH_DIVERGED > FH_NOT_CONVERGED), or an error code. */
+fh_status fh_solve(fh_solver* s, int nload, const double* eps0,
+                   const fh_solve_opts* opts, fh_result* res);
+
+/* Copy the strain fluctuation E of one load (component-major: E[c*m + i] is
+ * component c at stored point i) into host or device memory, as doubles. */
+fh_status fh_get_strain(const fh_solver* s, int load, double* E);
+/* Set the start E of one load for the next solve with init = 1 (host or
+ * device, layout of fh_get_strain). */
+fh_status fh_set_strain(fh_solver* s, int load, const double* E);
+
+/* Effective stiffness C_eff (Sec. 3.1, read as <C:(E+eps0)> = C_eff eps0)
+ * from the last solve, which must have had nload = n_v linearly independent
+ * eps0.  Ceff[n_v*n_v] host, row-major; voigt != 0 converts Mandel to Voigt
+ * (C_V = C_M / (s_a s_b), s = 1 normal, sqrt2 shear). */
+fh_status fh_get_ceff(const fh_solver* s, double* Ceff, int voigt);
+
+/* Host copy of the Gamma^p table: G[nh * n_v * n_v], the full symmetric
+ * matrix for every stored half-spectrum frequency (order of
+ * fh_pattern_half_freqs). */
+fh_status fh_get_green(const fh_solver* s, double* G);
+
+/* Residual history r_1..r_n of one load from the last solve: hist[n] host;
+ * *n receives the count (hist may be NULL to query it). */
+fh_status fh_get_residuals(const fh_solver* s, int load, double* hist, int* n);
+
+const char* fh_status_string(fh_status st);
+const char* fh_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FFTHOMOG_H */

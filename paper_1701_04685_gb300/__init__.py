@@ -1,0 +1,294 @@
+"""GB300 Basic-Scheme solver for FFT-based homogenisation on anisotropic patterns.
+
+Thin ctypes binding of the C ABI in ``include/fftHomog.h`` (argument
+marshalling only; every step of the iteration runs in the CUDA library
+``_build/libffthomog.so``).  Method: Bergmann & Merkert, arXiv 1701.04685 --
+the fixed point of Eq. (pde_coefficients) on the pattern P(M) with the
+periodised Green operator Gamma^p of Def. gamma_tilde_fourier.
+
+Arrays may be numpy arrays (host) or CUDA torch tensors (device) where the C
+ABI says "host or device".  The library must have been built
+(``paper_1701_04685_gb300.build.build()``); importing the binding never falls
+back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB
+
+FH_OK, FH_NOT_CONVERGED, FH_DIVERGED, FH_NONFINITE = 0, 1, 2, 3
+FH_GEN_DIRICHLET, FH_GEN_DLVP, FH_GEN_BOXSPLINE = 0, 1, 2
+FH_PREC_FP64, FH_PREC_FP32 = 0, 1
+FH_MAX_LOADS = 16
+FH_MAX_XI = 16
+
+_STATUS = {0: "ok", 1: "not converged", 2: "diverged", 3: "non-finite", -1: "invalid argument",
+           -2: "singular M", -3: "overflow", -4: "no orthonormal basis", -5: "CUDA error",
+           -6: "timeout", -7: "internal error", -8: "unsupported", -9: "call order"}
+
+
+class FhError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)} ({status}): {msg}")
+        self.status = status
+
+
+class fh_generator(C.Structure):
+    _fields_ = [("kind", C.c_int), ("alpha", C.c_double * 3), ("n_xi", C.c_int),
+                ("xi", C.c_double * (3 * FH_MAX_XI)), ("alias_radius", C.c_int)]
+
+
+class fh_solve_opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("precision", C.c_int),
+                ("init", C.c_int), ("chunk", C.c_int)]
+
+
+class fh_result(C.Structure):
+    _fields_ = [("iterations", C.c_int * FH_MAX_LOADS), ("residual", C.c_double * FH_MAX_LOADS),
+                ("status", C.c_int * FH_MAX_LOADS), ("mean_stress", C.c_double * (FH_MAX_LOADS * 6)),
+                ("elapsed_ms", C.c_double)]
+
+
+_lib = None
+
+
+def library():
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"CUDA library {LIB} is missing: run paper_1701_04685_gb300.build.build()")
+        lib = C.CDLL(LIB)
+        P, I, D, V = C.c_void_p, C.c_int, C.c_double, None
+        sig = {
+            "fh_pattern_create": (I, [I, P, C.POINTER(P)]),
+            "fh_pattern_destroy": (V, [P]),
+            "fh_pattern_info": (I, [P, P, P, P]),
+            "fh_pattern_points": (I, [P, P]),
+            "fh_pattern_numerators": (I, [P, P]),
+            "fh_pattern_half_freqs": (I, [P, P, P]),
+            "fh_solver_create": (I, [P, C.POINTER(fh_generator), I, P, C.POINTER(P)]),
+            "fh_solver_destroy": (V, [P]),
+            "fh_set_stiffness_phases": (I, [P, P, I, P]),
+            "fh_set_reference": (I, [P, P]),
+            "fh_solve": (I, [P, I, P, C.POINTER(fh_solve_opts), C.POINTER(fh_result)]),
+            "fh_get_strain": (I, [P, I, P]),
+            "fh_set_strain": (I, [P, I, P]),
+            "fh_get_ceff": (I, [P, P, I]),
+            "fh_get_green": (I, [P, P]),
+            "fh_get_residuals": (I, [P, I, P, P]),
+            "fh_status_string": (C.c_char_p, [I]),
+            "fh_last_error": (C.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    """Names of the C entry points the binding expects (all declared in fftHomog.h)."""
+    return ["fh_pattern_create", "fh_pattern_destroy", "fh_pattern_info", "fh_pattern_points",
+            "fh_pattern_numerators", "fh_pattern_half_freqs", "fh_solver_create", "fh_solver_destroy",
+            "fh_set_stiffness_phases", "fh_set_reference", "fh_solve", "fh_get_strain", "fh_set_strain",
+            "fh_get_ceff", "fh_get_green", "fh_get_residuals", "fh_status_string", "fh_last_error"]
+
+
+def _check(rc, ok=(FH_OK,)):
+    if rc not in ok:
+        raise FhError(rc, library().fh_last_error().decode())
+    return rc
+
+
+def _ptr(a):
+    """Address of a contiguous numpy array or torch tensor."""
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(a.data_ptr())
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return C.c_void_p(a.ctypes.data)
+
+
+def nv_of(d):
+    return 3 if d == 2 else 6
+
+
+# ---------------------------------------------------------------------------
+# stiffness helpers (Mandel form, Sec. 3.1)
+# ---------------------------------------------------------------------------
+
+def lame(E, nu):
+    """Lame constants lambda, mu of an isotropic solid (also used for plane strain)."""
+    return E * nu / ((1 + nu) * (1 - 2 * nu)), E / (2 * (1 + nu))
+
+
+def isotropic_stiffness(lam, mu, d):
+    """Mandel matrix of C = lam I(x)I + 2 mu Id: diagonal blocks lam + 2 mu / lam, shear 2 mu."""
+    n = nv_of(d)
+    Cm = np.zeros((n, n))
+    Cm[:d, :d] = lam
+    Cm[np.arange(d), np.arange(d)] = lam + 2 * mu
+    Cm[np.arange(d, n), np.arange(d, n)] = 2 * mu
+    return Cm
+
+
+def generator(kind="dirichlet", alpha=None, xi=None, radius=0):
+    """fh_generator for 'dirichlet', 'dlvp' (alpha = half ramp widths) or 'boxspline' (xi: d x s)."""
+    g = fh_generator()
+    if kind == "dirichlet":
+        g.kind = FH_GEN_DIRICHLET
+    elif kind == "dlvp":
+        g.kind = FH_GEN_DLVP
+        for i, a in enumerate(alpha):
+            g.alpha[i] = float(a)
+    elif kind == "boxspline":
+        g.kind = FH_GEN_BOXSPLINE
+        xi = np.asarray(xi, dtype=float)
+        d, s = xi.shape
+        g.n_xi = s
+        for k in range(s):
+            for i in range(d):
+                g.xi[3 * k + i] = xi[i, k]
+        g.alias_radius = int(radius)
+    else:
+        raise ValueError(kind)
+    return g
+
+
+def tensor_boxspline(d, order, radius):
+    """Box spline with `order` copies of each unit vector (tensor-product B-spline)."""
+    return generator("boxspline", xi=np.concatenate([np.eye(d)] * order, axis=1), radius=radius)
+
+
+# ---------------------------------------------------------------------------
+# pattern and solver objects (one method per C entry point)
+# ---------------------------------------------------------------------------
+
+class Pattern:
+    """P(M) and G(M^T) of a regular integer matrix M (fh_pattern_*)."""
+
+    def __init__(self, M):
+        M = np.ascontiguousarray(np.asarray(M, dtype=np.int64))
+        self.d = M.shape[0]
+        self.M = M
+        h = C.c_void_p()
+        _check(library().fh_pattern_create(self.d, _ptr(M), C.byref(h)))
+        self._h = h
+        m = C.c_int64()
+        nd = C.c_int()
+        dims = (C.c_int * 3)()
+        _check(library().fh_pattern_info(h, C.byref(m), C.byref(nd), dims))
+        self.m = m.value
+        self.dims = [dims[k] for k in range(nd.value)]
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.fh_pattern_destroy(self._h)
+            self._h = None
+
+    def points(self):
+        y = np.empty((self.m, self.d))
+        _check(library().fh_pattern_points(self._h, _ptr(y)))
+        return y
+
+    def numerators(self):
+        a = np.empty((self.m, self.d), dtype=np.int64)
+        _check(library().fh_pattern_numerators(self._h, _ptr(a)))
+        return a
+
+    def half_freqs(self):
+        nh = C.c_int64()
+        _check(library().fh_pattern_half_freqs(self._h, None, C.byref(nh)))
+        h = np.empty((nh.value, self.d), dtype=np.int64)
+        _check(library().fh_pattern_half_freqs(self._h, _ptr(h), C.byref(nh)))
+        return h
+
+
+class Solver:
+    """Basic-Scheme solver for one pattern and generator (fh_solver_*)."""
+
+    def __init__(self, pattern, gen, nload_max, stream=0):
+        self.pattern = pattern
+        self.d = pattern.d
+        self.nv = nv_of(self.d)
+        self.m = pattern.m
+        h = C.c_void_p()
+        _check(library().fh_solver_create(pattern._h, C.byref(gen), int(nload_max), C.c_void_p(stream), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.fh_solver_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def set_stiffness_phases(self, phase, Cp):
+        Cp = np.ascontiguousarray(np.asarray(Cp, dtype=np.float64))
+        if hasattr(phase, "data_ptr"):
+            ph = phase
+        else:
+            ph = np.ascontiguousarray(np.asarray(phase, dtype=np.uint8))
+        _check(library().fh_set_stiffness_phases(self._h, _ptr(ph), int(Cp.shape[0]), _ptr(Cp)))
+
+    def set_reference(self, C0=None):
+        if C0 is None:
+            _check(library().fh_set_reference(self._h, None))
+        else:
+            C0 = np.ascontiguousarray(np.asarray(C0, dtype=np.float64))
+            _check(library().fh_set_reference(self._h, _ptr(C0)))
+
+    def solve(self, eps0, tol=1e-8, max_iter=1000, precision=FH_PREC_FP64, init=0, chunk=0):
+        eps0 = np.ascontiguousarray(np.atleast_2d(np.asarray(eps0, dtype=np.float64)))
+        opts = fh_solve_opts(float(tol), int(max_iter), int(precision), int(init), int(chunk))
+        res = fh_result()
+        rc = library().fh_solve(self._h, eps0.shape[0], _ptr(eps0), C.byref(opts), C.byref(res))
+        _check(rc, ok=(FH_OK, FH_NOT_CONVERGED, FH_DIVERGED, FH_NONFINITE))
+        n = eps0.shape[0]
+        return {
+            "status": rc,
+            "iterations": np.array(res.iterations[:n]),
+            "residual": np.array(res.residual[:n]),
+            "load_status": np.array(res.status[:n]),
+            "mean_stress": np.array(res.mean_stress[: n * 6]).reshape(n, 6)[:, : self.nv],
+            "elapsed_ms": res.elapsed_ms,
+        }
+
+    def get_strain(self, load, out=None):
+        """E of one load as (n_v, m) float64 (numpy, or into a given CUDA tensor)."""
+        if out is None:
+            out = np.empty((self.nv, self.m))
+        _check(library().fh_get_strain(self._h, int(load), _ptr(out)))
+        return out
+
+    def set_strain(self, load, E):
+        if not hasattr(E, "data_ptr"):
+            E = np.ascontiguousarray(np.asarray(E, dtype=np.float64))
+        _check(library().fh_set_strain(self._h, int(load), _ptr(E)))
+
+    def get_ceff(self, voigt=False):
+        out = np.empty((self.nv, self.nv))
+        _check(library().fh_get_ceff(self._h, _ptr(out), int(bool(voigt))))
+        return out
+
+    def get_green(self):
+        nh = len(self.pattern.half_freqs())
+        out = np.empty((nh, self.nv, self.nv))
+        _check(library().fh_get_green(self._h, _ptr(out)))
+        return out
+
+    def get_residuals(self, load):
+        n = C.c_int()
+        _check(library().fh_get_residuals(self._h, int(load), None, C.byref(n)))
+        out = np.empty(n.value)
+        if n.value:
+            _check(library().fh_get_residuals(self._h, int(load), _ptr(out), C.byref(n)))
+        return out

@@ -1,0 +1,230 @@
+// Shared-memory mixed-radix FFT used by the pattern-DFT passes.
+//
+// The pattern DFT of the paper's Eq. (Fouriermatrix) becomes, through the
+// Smith-normal-form index map, an ordinary multi-dimensional DFT on the
+// stored grid.  Every pass of the solver transforms a batch of lines that sit
+// in shared memory; this file holds that line transform: a Stockham
+// (self-sorting) radix decomposition L = r_0 r_1 ... with radices
+// 2, 3, 4, 5, 8 written out and 7, 11, 13 done as small direct DFTs.
+//
+// Forward (DIR = -1) computes X_k = sum_n x_n exp(-2 pi i k n / L); inverse
+// (DIR = +1) the same with +i and no 1/L factor.  Twiddles come from a table
+// tw[t] = exp(-2 pi i t / L), t = 0..L-1, computed once on the host in FP64
+// (and rounded to FP32 for the FP32 path); no trigonometric function is
+// evaluated on the device.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace fh {
+
+template <typename T> struct cplx_t;
+template <> struct cplx_t<double> { using type = double2; };
+template <> struct cplx_t<float> { using type = float2; };
+
+template <typename T> using cplx = typename cplx_t<T>::type;
+
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  C r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+// multiply by DIR * i   (DIR = -1: -i, DIR = +1: +i)
+template <int DIR, typename C> __device__ __forceinline__ C mul_i(C a) {
+  C r;
+  if (DIR > 0) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
+  return r;
+}
+template <typename C> __device__ __forceinline__ C cscale(C a, decltype(a.x) s) { C r; r.x = a.x * s; r.y = a.y * s; return r; }
+
+struct DevPlan {
+  int L;
+  int np;
+  int r[24];
+};
+
+constexpr int MAX_RADIX = 13;
+
+// Small DFTs in registers, X_k = sum_t v_t w^{kt}, w = exp(DIR 2 pi i / r).
+template <int DIR, typename T>
+__device__ __forceinline__ void dft2(cplx<T>* v) {
+  cplx<T> a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+
+template <int DIR, typename T>
+__device__ __forceinline__ void dft4(cplx<T>* v) {
+  cplx<T> t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+  cplx<T> t2 = cadd(v[1], v[3]), t3 = mul_i<DIR>(csub(v[1], v[3]));
+  v[0] = cadd(t0, t2);
+  v[2] = csub(t0, t2);
+  v[1] = cadd(t1, t3);
+  v[3] = csub(t1, t3);
+}
+
+template <int DIR, typename T>
+__device__ __forceinline__ void dft8(cplx<T>* v) {
+  const T h = T(0.70710678118654752440084436210485);
+  cplx<T> e[4] = {v[0], v[2], v[4], v[6]};
+  cplx<T> o[4] = {v[1], v[3], v[5], v[7]};
+  dft4<DIR, T>(e);
+  dft4<DIR, T>(o);
+  // w8^k with w8 = (1 + DIR i)/sqrt2
+  cplx<T> o1, o2, o3;
+  o1.x = h * (o[1].x - DIR * o[1].y);
+  o1.y = h * (o[1].y + DIR * o[1].x);
+  o2 = mul_i<DIR>(o[2]);
+  o3.x = h * (-o[3].x - DIR * o[3].y);
+  o3.y = h * (-o[3].y + DIR * o[3].x);
+  v[0] = cadd(e[0], o[0]); v[4] = csub(e[0], o[0]);
+  v[1] = cadd(e[1], o1);   v[5] = csub(e[1], o1);
+  v[2] = cadd(e[2], o2);   v[6] = csub(e[2], o2);
+  v[3] = cadd(e[3], o3);   v[7] = csub(e[3], o3);
+}
+
+template <int DIR, typename T>
+__device__ __forceinline__ void dft3(cplx<T>* v) {
+  const T c = T(-0.5);
+  const T s = T(0.86602540378443864676372317075294);  // sqrt(3)/2
+  cplx<T> sum = cadd(v[1], v[2]);
+  cplx<T> dif = csub(v[1], v[2]);
+  cplx<T> a = v[0];
+  cplx<T> m;
+  m.x = a.x + c * sum.x;
+  m.y = a.y + c * sum.y;
+  cplx<T> r = mul_i<DIR>(cscale(dif, s));
+  v[0] = cadd(a, sum);
+  v[1] = cadd(m, r);
+  v[2] = csub(m, r);
+}
+
+template <int DIR, typename T>
+__device__ __forceinline__ void dft5(cplx<T>* v) {
+  const T c1 = T(0.30901699437494742410229341718282);   // cos(2 pi/5)
+  const T c2 = T(-0.80901699437494742410229341718282);  // cos(4 pi/5)
+  const T s1 = T(0.95105651629515357211643933337938);   // sin(2 pi/5)
+  const T s2 = T(0.58778525229247312916870595463907);   // sin(4 pi/5)
+  cplx<T> a = v[0];
+  cplx<T> p1 = cadd(v[1], v[4]), d1 = csub(v[1], v[4]);
+  cplx<T> p2 = cadd(v[2], v[3]), d2 = csub(v[2], v[3]);
+  cplx<T> m1, m2, q1, q2;
+  m1.x = a.x + c1 * p1.x + c2 * p2.x; m1.y = a.y + c1 * p1.y + c2 * p2.y;
+  m2.x = a.x + c2 * p1.x + c1 * p2.x; m2.y = a.y + c2 * p1.y + c1 * p2.y;
+  q1.x = s1 * d1.x + s2 * d2.x; q1.y = s1 * d1.y + s2 * d2.y;
+  q2.x = s2 * d1.x - s1 * d2.x; q2.y = s2 * d1.y - s1 * d2.y;
+  q1 = mul_i<DIR>(q1);
+  q2 = mul_i<DIR>(q2);
+  v[0] = cadd(a, cadd(p1, p2));
+  v[1] = cadd(m1, q1);
+  v[4] = csub(m1, q1);
+  v[2] = cadd(m2, q2);
+  v[3] = csub(m2, q2);
+}
+
+// direct DFT of a small prime radix R; w^{kt} = tw[((k t) mod R) * (L / R)]
+template <int R, int DIR, typename T>
+__device__ __forceinline__ void dft_direct(cplx<T>* v, const cplx<T>* __restrict__ tw, int L) {
+  cplx<T> out[R];
+  const int step = L / R;
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    cplx<T> acc = v[0];
+#pragma unroll
+    for (int t = 1; t < R; ++t) {
+      cplx<T> w = tw[((k * t) % R) * step];
+      if (DIR > 0) w.y = -w.y;
+      acc = cadd(acc, cmul(v[t], w));
+    }
+    out[k] = acc;
+  }
+#pragma unroll
+  for (int k = 0; k < R; ++k) v[k] = out[k];
+}
+
+template <int R, int DIR, typename T>
+__device__ __forceinline__ void dft_small(cplx<T>* v, const cplx<T>* __restrict__ tw, int L) {
+  if (R == 2) dft2<DIR, T>(v);
+  else if (R == 3) dft3<DIR, T>(v);
+  else if (R == 4) dft4<DIR, T>(v);
+  else if (R == 5) dft5<DIR, T>(v);
+  else if (R == 8) dft8<DIR, T>(v);
+  else dft_direct<R, DIR, T>(v, tw, L);
+}
+
+// One Stockham stage of radix R: sub-transforms of size Ns are combined into
+// size Ns*R.  Butterfly j reads in[j + t*L/R] (t < R), applies the twiddles
+// w^{t k}, k = j mod Ns, w = exp(DIR 2 pi i / (Ns R)), does a length-R DFT and
+// writes out[(j / Ns) * Ns * R + k + t*Ns].
+template <int R, int DIR, typename T>
+__device__ __forceinline__ void stockham_stage(const cplx<T>* in, cplx<T>* out, int nlines, int ls, int L, int Ns,
+                                               const cplx<T>* __restrict__ tw) {
+  const int nb = L / R;
+  const int stride = L / (Ns * R);
+  const int total = nlines * nb;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int line = idx / nb;
+    const int j = idx - line * nb;
+    const cplx<T>* li = in + line * ls;
+    cplx<T>* lo = out + line * ls;
+    const int k = j % Ns;
+    cplx<T> v[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) v[t] = li[j + t * nb];
+    if (k != 0) {
+#pragma unroll
+      for (int t = 1; t < R; ++t) {
+        cplx<T> w = tw[t * k * stride];
+        if (DIR > 0) w.y = -w.y;
+        v[t] = cmul(v[t], w);
+      }
+    }
+    dft_small<R, DIR, T>(v, tw, L);
+    const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+    for (int t = 0; t < R; ++t) lo[base + t * Ns] = v[t];
+  }
+}
+
+// Transform `nlines` lines of length plan.L in place in shared memory.
+// Line q occupies buf[q*ls .. q*ls + L); tmp has the same shape (ping-pong
+// buffer).  Every thread of the block must call this.  On return the result
+// is in buf.
+template <int DIR, typename T>
+__device__ void fft_lines(cplx<T>* buf, cplx<T>* tmp, int nlines, int ls, const DevPlan& plan,
+                          const cplx<T>* __restrict__ tw) {
+  const int L = plan.L;
+  cplx<T>* in = buf;
+  cplx<T>* out = tmp;
+  int Ns = 1;
+  for (int s = 0; s < plan.np; ++s) {
+    const int r = plan.r[s];
+    switch (r) {
+      case 2: stockham_stage<2, DIR, T>(in, out, nlines, ls, L, Ns, tw); break;
+      case 3: stockham_stage<3, DIR, T>(in, out, nlines, ls, L, Ns, tw); break;
+      case 4: stockham_stage<4, DIR, T>(in, out, nlines, ls, L, Ns, tw); break;
+      case 5: stockham_stage<5, DIR, T>(in, out, nlines, ls, L, Ns, tw); break;
+      case 7: stockham_stage<7, DIR, T>(in, out, nlines, ls, L, Ns, tw); break;
+      case 8: stockham_stage<8, DIR, T>(in, out, nlines, ls, L, Ns, tw); break;
+      case 11: stockham_stage<11, DIR, T>(in, out, nlines, ls, L, Ns, tw); break;
+      default: stockham_stage<13, DIR, T>(in, out, nlines, ls, L, Ns, tw); break;
+    }
+    __syncthreads();
+    cplx<T>* sw = in; in = out; out = sw;
+    Ns *= r;
+  }
+  if (in != buf) {
+    const int total = nlines * L;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int line = idx / L;
+      const int x = idx - line * L;
+      buf[line * ls + x] = in[line * ls + x];
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace fh

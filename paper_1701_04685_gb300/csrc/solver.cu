@@ -1,0 +1,809 @@
+// C ABI of the Basic-Scheme solver (declared in include/fftHomog.h).
+//
+// Host orchestration only: argument checks, device memory, the Gamma^p table
+// build, and the iteration loop.  The iteration body (row pass + line passes,
+// see kernels.cuh) is captured once per (precision, load count, chunk) into a
+// CUDA graph of `chunk` iterations; the host replays it and reads one flag per
+// replay.  Loads that have converged make their blocks return at entry, so the
+// per-load iteration counts are exact.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.hpp"
+#include "kernels.cuh"
+
+namespace fh {
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+}  // namespace fh
+
+using fh::Control;
+using fh::DevPlan;
+using fh::GridInfo;
+using fh::LoadState;
+
+#define CK(call)                                                                     \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      fh::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));             \
+      return FH_ERR_CUDA;                                                            \
+    }                                                                                \
+  } while (0)
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kHistCap = 65536;
+constexpr size_t kMaxSmem = 227 * 1024;
+constexpr int kMaxPhases = 16;
+
+int mandel_nv(int d) { return d == 2 ? 3 : 6; }
+
+struct Axis {
+  int L = 1;
+  DevPlan plan{};
+  double2* tw64 = nullptr;
+  float2* tw32 = nullptr;
+};
+
+struct GraphEntry {
+  int prec, nload, chunk;
+  cudaGraphExec_t exec;
+};
+
+}  // namespace
+
+struct fh_solver {
+  fh::Pattern P;
+  fh_generator gen{};
+  cudaStream_t user = nullptr;
+  cudaStream_t work = nullptr;
+  int nload_max = 0;
+  GridInfo g{};
+  Axis ax[3];
+  // device memory
+  double* E64 = nullptr;
+  float* E32 = nullptr;
+  void* S = nullptr;
+  uint8_t* phase = nullptr;
+  double* Cp64 = nullptr;
+  double* dC64 = nullptr;
+  float* dC32 = nullptr;
+  double* G64 = nullptr;
+  float* G32 = nullptr;
+  Control* ctl = nullptr;
+  LoadState* st = nullptr;
+  double* partials = nullptr;
+  double* partials2 = nullptr;
+  double* hist = nullptr;
+  double* mstress = nullptr;
+  int* err = nullptr;
+  double* scratch64 = nullptr;  // nv*m doubles, for strain copies
+  int* h_flag = nullptr;        // pinned
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_user = nullptr;
+  // host state
+  int nphase = 0;
+  double Cp[kMaxPhases * 36] = {};
+  double C0[36] = {};
+  bool have_phases = false, have_table = false;
+  int E_prec = -1;  // precision of the strain currently held in E
+  int last_nload = 0;
+  double last_eps0[FH_MAX_LOADS * 6] = {};
+  double last_ms[FH_MAX_LOADS * 6] = {};
+  bool have_solution = false;
+  int last_iters[FH_MAX_LOADS] = {};
+  // launch shapes per precision (0: fp64, 1: fp32)
+  int rpb[2] = {1, 1};
+  int row_bpl[2] = {1, 1};
+  size_t row_smem[2] = {0, 0};
+  int lineW[2][3] = {};
+  int ntiles[2][3] = {};
+  size_t line_smem[2][3] = {};
+  std::vector<GraphEntry> graphs;
+};
+
+namespace {
+
+size_t csize(int prec) { return prec == FH_PREC_FP64 ? sizeof(double2) : sizeof(float2); }
+
+void choose_shapes(fh_solver* s, int prec) {
+  const GridInfo& g = s->g;
+  const int sms = 152;
+  const int nl = s->nload_max;
+  auto row_smem = [&](int rpb) { return (size_t)2 * ((rpb * g.nv + 1) / 2) * g.L * csize(prec); };
+  int rpb = 1;
+  while (rpb * 2 <= g.nrows && (g.nrows * nl) / (rpb * 2) >= 2 * sms && row_smem(rpb * 2) <= 96 * 1024) rpb *= 2;
+  s->rpb[prec] = rpb;
+  s->row_bpl[prec] = (int)((g.nrows + rpb - 1) / rpb);
+  s->row_smem[prec] = row_smem(rpb);
+  for (int a = 0; a + 1 < g.nd; ++a) {
+    const int N = g.dims[a];
+    long long others = 1;
+    for (int k = 0; k + 1 < g.nd; ++k)
+      if (k != a) others *= g.dims[k];
+    int W = 16;
+    auto smem = [&](int w) { return (size_t)2 * g.nv * w * N * csize(prec); };
+    auto blocks = [&](int w) { return (long long)nl * others * ((g.H + w - 1) / w); };
+    const int wmin = prec == FH_PREC_FP64 ? 2 : 4;
+    while (W > wmin && (smem(W) > 96 * 1024 || blocks(W) < 2 * sms)) W /= 2;
+    while (W > 1 && smem(W) > kMaxSmem) W /= 2;
+    s->lineW[prec][a] = W;
+    s->ntiles[prec][a] = (g.H + W - 1) / W;
+    s->line_smem[prec][a] = smem(W);
+  }
+}
+
+template <typename T>
+const typename fh::cplx_t<T>::type* twp(const Axis& a);
+template <>
+const double2* twp<double>(const Axis& a) { return a.tw64; }
+template <>
+const float2* twp<float>(const Axis& a) { return a.tw32; }
+
+template <typename T>
+T* Eptr(fh_solver* s);
+template <>
+double* Eptr<double>(fh_solver* s) { return s->E64; }
+template <>
+float* Eptr<float>(fh_solver* s) { return s->E32; }
+
+template <typename T>
+const T* dCptr(fh_solver* s);
+template <>
+const double* dCptr<double>(fh_solver* s) { return s->dC64; }
+template <>
+const float* dCptr<float>(fh_solver* s) { return s->dC32; }
+
+template <typename T>
+const T* Gptr(fh_solver* s);
+template <>
+const double* Gptr<double>(fh_solver* s) { return s->G64; }
+template <>
+const float* Gptr<float>(fh_solver* s) { return s->G32; }
+
+// Enqueue the line passes of one iteration (everything between two row passes).
+template <typename T>
+void enqueue_line_passes(fh_solver* s, int prec, int nload) {
+  const GridInfo& g = s->g;
+  using C = typename fh::cplx_t<T>::type;
+  C* S = reinterpret_cast<C*>(s->S);
+  if (g.nd == 1) {
+    const long long total = (long long)nload * g.nhalf;
+    const int blocks = (int)std::min<long long>((total + kThreads - 1) / kThreads, 4096);
+    fh::green_1d<T><<<blocks, kThreads, 0, s->work>>>(g, S, Gptr<T>(s), s->st, nload);
+    return;
+  }
+  auto launch = [&](int a, int mode) {
+    long long n_outer = 1, n_inner = 1;
+    for (int k = 0; k < a; ++k) n_outer *= g.dims[k];
+    for (int k = a + 1; k + 1 < g.nd; ++k) n_inner *= g.dims[k];
+    const long long blocks = (long long)nload * n_outer * n_inner * s->ntiles[prec][a];
+    const size_t sm = s->line_smem[prec][a];
+    if (mode == 0)
+      fh::line_pass<T, 0><<<(unsigned)blocks, kThreads, sm, s->work>>>(g, s->ax[a].plan, twp<T>(s->ax[a]), S, Gptr<T>(s), s->st, a,
+                                                                       s->lineW[prec][a], s->ntiles[prec][a], (int)n_outer, (int)n_inner);
+    else if (mode == 1)
+      fh::line_pass<T, 1><<<(unsigned)blocks, kThreads, sm, s->work>>>(g, s->ax[a].plan, twp<T>(s->ax[a]), S, Gptr<T>(s), s->st, a,
+                                                                       s->lineW[prec][a], s->ntiles[prec][a], (int)n_outer, (int)n_inner);
+    else
+      fh::line_pass<T, 2><<<(unsigned)blocks, kThreads, sm, s->work>>>(g, s->ax[a].plan, twp<T>(s->ax[a]), S, Gptr<T>(s), s->st, a,
+                                                                       s->lineW[prec][a], s->ntiles[prec][a], (int)n_outer, (int)n_inner);
+  };
+  // forward along axes nd-2 .. 1, then axis 0 with the Green step, then inverse 1 .. nd-2
+  for (int a = g.nd - 2; a >= 1; --a) launch(a, 0);
+  launch(0, 2);
+  for (int a = 1; a <= g.nd - 2; ++a) launch(a, 1);
+}
+
+template <typename T, bool FIRST>
+void enqueue_row_pass(fh_solver* s, int prec, int nload) {
+  const GridInfo& g = s->g;
+  using C = typename fh::cplx_t<T>::type;
+  const int last = g.nd - 1;
+  const int blocks = nload * s->row_bpl[prec];
+  fh::row_pass<T, FIRST><<<blocks, kThreads, s->row_smem[prec], s->work>>>(
+      g, s->ax[last].plan, twp<T>(s->ax[last]), Eptr<T>(s), reinterpret_cast<C*>(s->S), s->phase, dCptr<T>(s), s->ctl, s->st,
+      s->partials, s->hist, s->rpb[prec], s->row_bpl[prec]);
+}
+
+template <typename T>
+fh_status set_smem_attrs(fh_solver* s, int prec) {
+  const size_t rs = s->row_smem[prec];
+  if (rs > kMaxSmem) {
+    fh::set_error("contiguous axis too long for this precision (shared memory)");
+    return FH_ERR_UNSUPPORTED;
+  }
+  CK(cudaFuncSetAttribute(fh::row_pass<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
+  CK(cudaFuncSetAttribute(fh::row_pass<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
+  size_t lm = 0;
+  for (int a = 0; a + 1 < s->g.nd; ++a) lm = std::max(lm, s->line_smem[prec][a]);
+  if (lm > kMaxSmem) {
+    fh::set_error("axis too long for this precision (shared memory)");
+    return FH_ERR_UNSUPPORTED;
+  }
+  if (lm > 0) {
+    CK(cudaFuncSetAttribute(fh::line_pass<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lm));
+    CK(cudaFuncSetAttribute(fh::line_pass<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lm));
+    CK(cudaFuncSetAttribute(fh::line_pass<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lm));
+  }
+  return FH_OK;
+}
+
+template <typename T>
+fh_status get_graph(fh_solver* s, int prec, int nload, int chunk, cudaGraphExec_t* out) {
+  for (auto& e : s->graphs)
+    if (e.prec == prec && e.nload == nload && e.chunk == chunk) {
+      *out = e.exec;
+      return FH_OK;
+    }
+  CK(cudaStreamBeginCapture(s->work, cudaStreamCaptureModeThreadLocal));
+  for (int i = 0; i < chunk; ++i) {
+    enqueue_line_passes<T>(s, prec, nload);
+    enqueue_row_pass<T, false>(s, prec, nload);
+  }
+  cudaGraph_t graph;
+  CK(cudaStreamEndCapture(s->work, &graph));
+  cudaGraphExec_t exec;
+  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    fh::set_error(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    return FH_ERR_CUDA;
+  }
+  s->graphs.push_back({prec, nload, chunk, exec});
+  *out = exec;
+  return FH_OK;
+}
+
+template <typename T>
+fh_status run_solve(fh_solver* s, int prec, int nload, int chunk, int max_iter) {
+  fh_status rc = set_smem_attrs<T>(s, prec);
+  if (rc != FH_OK) return rc;
+  cudaGraphExec_t exec;
+  rc = get_graph<T>(s, prec, nload, chunk, &exec);
+  if (rc != FH_OK) return rc;
+  CK(cudaEventRecord(s->ev0, s->work));
+  enqueue_row_pass<T, true>(s, prec, nload);
+  CK(cudaGetLastError());
+  long long launched = 0;
+  for (;;) {
+    CK(cudaGraphLaunch(exec, s->work));
+    launched += chunk;
+    CK(cudaMemcpyAsync(s->h_flag, &s->ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, s->work));
+    CK(cudaStreamSynchronize(s->work));
+    if (*s->h_flag) break;
+    if (launched > (long long)max_iter + chunk) {
+      fh::set_error("iteration state did not terminate");
+      return FH_ERR_INTERNAL;
+    }
+  }
+  const int bpl = std::max(1, (int)std::min<long long>((s->g.m + kThreads - 1) / kThreads, 64));
+  fh::mean_stress<T><<<nload * bpl, kThreads, 0, s->work>>>(s->g, Eptr<T>(s), s->phase, s->Cp64, s->ctl, s->partials2,
+                                                            s->mstress, bpl);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(s->ev1, s->work));
+  return FH_OK;
+}
+
+void free_all(fh_solver* s) {
+  for (auto& e : s->graphs) cudaGraphExecDestroy(e.exec);
+  s->graphs.clear();
+  void* ptrs[] = {s->E64, s->E32, s->S, s->phase, s->Cp64, s->dC64, s->dC32, s->G64, s->G32, s->ctl, s->st,
+                  s->partials, s->partials2, s->hist, s->mstress, s->err, s->scratch64};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (auto& a : s->ax) {
+    if (a.tw64) cudaFree(a.tw64);
+    if (a.tw32) cudaFree(a.tw32);
+  }
+  if (s->h_flag) cudaFreeHost(s->h_flag);
+  if (s->ev0) cudaEventDestroy(s->ev0);
+  if (s->ev1) cudaEventDestroy(s->ev1);
+  if (s->ev_user) cudaEventDestroy(s->ev_user);
+  if (s->work) cudaStreamDestroy(s->work);
+}
+
+// order the private work stream after everything already queued on the user stream
+fh_status join_user(fh_solver* s) {
+  CK(cudaEventRecord(s->ev_user, s->user));
+  CK(cudaStreamWaitEvent(s->work, s->ev_user, 0));
+  return FH_OK;
+}
+
+bool cholesky_ok(const double* A, int n) {
+  double L[36] = {};
+  for (int j = 0; j < n; ++j) {
+    double d = A[j * n + j];
+    for (int k = 0; k < j; ++k) d -= L[j * n + k] * L[j * n + k];
+    if (!(d > 0.0)) return false;
+    L[j * n + j] = std::sqrt(d);
+    for (int i = j + 1; i < n; ++i) {
+      double v = A[i * n + j];
+      for (int k = 0; k < j; ++k) v -= L[i * n + k] * L[j * n + k];
+      L[i * n + j] = v / L[j * n + j];
+    }
+  }
+  return true;
+}
+
+// Mandel matrix -> fourth-order tensor C_ijkl (3x3x3x3 storage)
+void mandel_to_c4(const double* Cm, int d, double* C4) {
+  const int I2[3] = {0, 1, 0}, J2[3] = {0, 1, 1};
+  const int I3[6] = {0, 1, 2, 1, 0, 0}, J3[6] = {0, 1, 2, 2, 2, 1};
+  const int* I = d == 2 ? I2 : I3;
+  const int* J = d == 2 ? J2 : J3;
+  const int nv = mandel_nv(d);
+  for (int q = 0; q < 81; ++q) C4[q] = 0.0;
+  for (int a = 0; a < nv; ++a)
+    for (int b = 0; b < nv; ++b) {
+      const double sa = I[a] == J[a] ? 1.0 : std::sqrt(2.0);
+      const double sb = I[b] == J[b] ? 1.0 : std::sqrt(2.0);
+      const double v = Cm[a * nv + b] / (sa * sb);
+      const int ij[2][2] = {{I[a], J[a]}, {J[a], I[a]}};
+      const int kl[2][2] = {{I[b], J[b]}, {J[b], I[b]}};
+      for (auto& p : ij)
+        for (auto& q : kl) C4[((p[0] * 3 + p[1]) * 3 + q[0]) * 3 + q[1]] = v;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fh_status_string(fh_status st) {
+  switch (st) {
+    case FH_OK: return "ok";
+    case FH_NOT_CONVERGED: return "not converged (max_iter reached)";
+    case FH_DIVERGED: return "diverged";
+    case FH_NONFINITE: return "non-finite residual";
+    case FH_ERR_ARG: return "invalid argument";
+    case FH_ERR_SINGULAR_M: return "singular pattern matrix";
+    case FH_ERR_OVERFLOW: return "integer overflow";
+    case FH_ERR_NO_ONB: return "translates cannot be orthonormalised";
+    case FH_ERR_CUDA: return "CUDA error";
+    case FH_ERR_TIMEOUT: return "device wait timed out";
+    case FH_ERR_INTERNAL: return "internal error";
+    case FH_ERR_UNSUPPORTED: return "unsupported size";
+    case FH_ERR_STATE: return "call order violated";
+  }
+  return "unknown status";
+}
+
+const char* fh_last_error(void) { return fh::g_err.c_str(); }
+
+fh_status fh_pattern_create(int d, const int64_t* M, fh_pattern** out) {
+  if (!M || !out) { fh::set_error("null argument"); return FH_ERR_ARG; }
+  fh_pattern* p = new fh_pattern();
+  fh_status rc = fh::build_pattern(d, M, &p->p);
+  if (rc != FH_OK) { delete p; return rc; }
+  *out = p;
+  return FH_OK;
+}
+
+void fh_pattern_destroy(fh_pattern* p) { delete p; }
+
+fh_status fh_pattern_info(const fh_pattern* p, int64_t* m, int* ndims, int* dims) {
+  if (!p) { fh::set_error("null pattern"); return FH_ERR_ARG; }
+  if (m) *m = p->p.D;
+  if (ndims) *ndims = p->p.nd;
+  if (dims)
+    for (int k = 0; k < 3; ++k) dims[k] = k < p->p.nd ? p->p.dims[k] : 1;
+  return FH_OK;
+}
+
+fh_status fh_pattern_numerators(const fh_pattern* p, int64_t* a) {
+  if (!p || !a) { fh::set_error("null argument"); return FH_ERR_ARG; }
+  const int d = p->p.d;
+  for (int64_t i = 0; i < p->p.D; ++i) p->p.point_numerator(i, a + i * d);
+  return FH_OK;
+}
+
+fh_status fh_pattern_points(const fh_pattern* p, double* y) {
+  if (!p || !y) { fh::set_error("null argument"); return FH_ERR_ARG; }
+  const int d = p->p.d;
+  int64_t a[3];
+  for (int64_t i = 0; i < p->p.D; ++i) {
+    p->p.point_numerator(i, a);
+    for (int k = 0; k < d; ++k) y[i * d + k] = (double)a[k] / (double)p->p.D;
+  }
+  return FH_OK;
+}
+
+fh_status fh_pattern_half_freqs(const fh_pattern* p, int64_t* h, int64_t* nh) {
+  if (!p) { fh::set_error("null pattern"); return FH_ERR_ARG; }
+  const int64_t n = p->p.n_half();
+  if (nh) *nh = n;
+  if (!h) return FH_OK;
+  for (int64_t f = 0; f < n; ++f) p->p.half_freq(f, h + f * p->p.d);
+  return FH_OK;
+}
+
+fh_status fh_solver_create(const fh_pattern* p, const fh_generator* gen, int nload_max, void* stream,
+                           fh_solver** out) {
+  if (!p || !gen || !out) { fh::set_error("null argument"); return FH_ERR_ARG; }
+  if (nload_max < 1 || nload_max > FH_MAX_LOADS) { fh::set_error("nload_max out of range"); return FH_ERR_ARG; }
+  if (gen->kind < FH_GEN_DIRICHLET || gen->kind > FH_GEN_BOXSPLINE) { fh::set_error("unknown generator"); return FH_ERR_ARG; }
+  const int d = p->p.d;
+  if (gen->kind == FH_GEN_DLVP)
+    for (int i = 0; i < d; ++i)
+      if (!(gen->alpha[i] >= 0.0 && gen->alpha[i] <= 0.5)) { fh::set_error("dlVP alpha outside [0, 1/2]"); return FH_ERR_ARG; }
+  if (gen->kind == FH_GEN_BOXSPLINE) {
+    if (gen->n_xi < 1 || gen->n_xi > FH_MAX_XI) { fh::set_error("box spline n_xi out of range"); return FH_ERR_ARG; }
+    if (gen->alias_radius < 0 || gen->alias_radius > 16) { fh::set_error("alias radius out of range"); return FH_ERR_ARG; }
+  }
+  fh_solver* s = new fh_solver();
+  s->P = p->p;
+  s->gen = *gen;
+  s->user = reinterpret_cast<cudaStream_t>(stream);
+  s->nload_max = nload_max;
+  GridInfo& g = s->g;
+  g.d = d;
+  g.nv = mandel_nv(d);
+  g.ntri = g.nv * (g.nv + 1) / 2;
+  g.nd = s->P.nd;
+  for (int k = 0; k < 3; ++k) g.dims[k] = k < g.nd ? s->P.dims[k] : 1;
+  g.L = g.dims[g.nd - 1];
+  g.H = g.L / 2 + 1;
+  g.m = s->P.D;
+  g.nrows = g.m / g.L;
+  g.nhalf = s->P.n_half();
+  g.inv_m = 1.0 / (double)g.m;
+  for (int k = 0; k < g.nd; ++k) {
+    if (g.dims[k] > 4096) { delete s; fh::set_error("SNF axis longer than 4096"); return FH_ERR_UNSUPPORTED; }
+    fh::FftPlan fp;
+    if (!fh::make_plan(g.dims[k], &fp)) { delete s; fh::set_error("SNF axis length has a prime factor > 13"); return FH_ERR_UNSUPPORTED; }
+    s->ax[k].L = fp.L;
+    s->ax[k].plan.L = fp.L;
+    s->ax[k].plan.np = fp.np;
+    for (int q = 0; q < 24; ++q) s->ax[k].plan.r[q] = fp.r[q];
+  }
+  choose_shapes(s, FH_PREC_FP64);
+  choose_shapes(s, FH_PREC_FP32);
+  auto fail = [&](fh_status rc) { free_all(s); delete s; return rc; };
+#define CKS(call)                                                             \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      fh::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));      \
+      return fail(FH_ERR_CUDA);                                               \
+    }                                                                         \
+  } while (0)
+  CKS(cudaStreamCreateWithFlags(&s->work, cudaStreamNonBlocking));
+  CKS(cudaEventCreate(&s->ev0));
+  CKS(cudaEventCreate(&s->ev1));
+  CKS(cudaEventCreateWithFlags(&s->ev_user, cudaEventDisableTiming));
+  const size_t nfield = (size_t)nload_max * g.nv * g.m;
+  const size_t nspec = (size_t)nload_max * g.nv * g.nhalf;
+  CKS(cudaMalloc(&s->E64, nfield * sizeof(double)));
+  CKS(cudaMalloc(&s->E32, nfield * sizeof(float)));
+  CKS(cudaMalloc(&s->S, nspec * sizeof(double2)));
+  CKS(cudaMalloc(&s->phase, (size_t)g.m));
+  CKS(cudaMalloc(&s->Cp64, kMaxPhases * 36 * sizeof(double)));
+  CKS(cudaMalloc(&s->dC64, kMaxPhases * 36 * sizeof(double)));
+  CKS(cudaMalloc(&s->dC32, kMaxPhases * 36 * sizeof(float)));
+  CKS(cudaMalloc(&s->G64, (size_t)g.ntri * g.nhalf * sizeof(double)));
+  CKS(cudaMalloc(&s->G32, (size_t)g.ntri * g.nhalf * sizeof(float)));
+  CKS(cudaMalloc(&s->ctl, sizeof(Control)));
+  CKS(cudaMalloc(&s->st, FH_MAX_LOADS * sizeof(LoadState)));
+  const size_t nblk = (size_t)nload_max * std::max(s->row_bpl[0], s->row_bpl[1]);
+  CKS(cudaMalloc(&s->partials, 2 * nblk * sizeof(double)));
+  CKS(cudaMalloc(&s->partials2, (size_t)nload_max * 64 * fh::MAXV * sizeof(double)));
+  CKS(cudaMalloc(&s->hist, (size_t)nload_max * kHistCap * sizeof(double)));
+  CKS(cudaMalloc(&s->mstress, FH_MAX_LOADS * fh::MAXV * sizeof(double)));
+  CKS(cudaMalloc(&s->err, sizeof(int)));
+  CKS(cudaMallocHost(&s->h_flag, sizeof(int)));
+  CKS(cudaMemset(s->ctl, 0, sizeof(Control)));
+  CKS(cudaMemset(s->st, 0, FH_MAX_LOADS * sizeof(LoadState)));
+  CKS(cudaMemset(s->err, 0, sizeof(int)));
+  CKS(cudaMemset(s->E64, 0, nfield * sizeof(double)));
+  // twiddles exp(-2 pi i t / L), evaluated in long double on the host
+  for (int k = 0; k < g.nd; ++k) {
+    const int L = s->ax[k].L;
+    std::vector<double2> t64(L);
+    std::vector<float2> t32(L);
+    for (int t = 0; t < L; ++t) {
+      const long double ang = 2.0L * 3.141592653589793238462643383279502884L * (long double)t / (long double)L;
+      t64[t].x = (double)cosl(ang);
+      t64[t].y = (double)(-sinl(ang));
+      t32[t].x = (float)t64[t].x;
+      t32[t].y = (float)t64[t].y;
+    }
+    CKS(cudaMalloc(&s->ax[k].tw64, L * sizeof(double2)));
+    CKS(cudaMalloc(&s->ax[k].tw32, L * sizeof(float2)));
+    CKS(cudaMemcpy(s->ax[k].tw64, t64.data(), L * sizeof(double2), cudaMemcpyHostToDevice));
+    CKS(cudaMemcpy(s->ax[k].tw32, t32.data(), L * sizeof(float2), cudaMemcpyHostToDevice));
+  }
+#undef CKS
+  *out = s;
+  return FH_OK;
+}
+
+void fh_solver_destroy(fh_solver* s) {
+  if (!s) return;
+  if (s->work) cudaStreamSynchronize(s->work);
+  free_all(s);
+  delete s;
+}
+
+fh_status fh_set_stiffness_phases(fh_solver* s, const uint8_t* phase, int nphase, const double* Cp) {
+  if (!s || !phase || !Cp) { fh::set_error("null argument"); return FH_ERR_ARG; }
+  if (nphase < 1 || nphase > kMaxPhases) { fh::set_error("nphase must be 1..16"); return FH_ERR_ARG; }
+  const int nv = s->g.nv;
+  for (int q = 0; q < nphase; ++q)
+    for (int a = 0; a < nv; ++a)
+      for (int b = 0; b < nv; ++b) {
+        const double v = Cp[(q * nv + a) * nv + b];
+        if (!std::isfinite(v)) { fh::set_error("non-finite stiffness"); return FH_ERR_ARG; }
+        if (std::fabs(v - Cp[(q * nv + b) * nv + a]) > 1e-12 * (1.0 + std::fabs(v))) {
+          fh::set_error("phase stiffness is not symmetric (major symmetry)");
+          return FH_ERR_ARG;
+        }
+      }
+  fh_status rc = join_user(s);
+  if (rc != FH_OK) return rc;
+  CK(cudaMemcpyAsync(s->phase, phase, (size_t)s->g.m, cudaMemcpyDefault, s->work));
+  CK(cudaMemsetAsync(s->err, 0, sizeof(int), s->work));
+  fh::check_phases<<<256, kThreads, 0, s->work>>>(s->phase, s->g.m, nphase, s->err);
+  CK(cudaGetLastError());
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->work));
+  CK(cudaStreamSynchronize(s->work));
+  if (herr != 0) { fh::set_error("phase id >= nphase"); return FH_ERR_ARG; }
+  s->nphase = nphase;
+  std::memcpy(s->Cp, Cp, sizeof(double) * nphase * nv * nv);
+  CK(cudaMemcpy(s->Cp64, s->Cp, sizeof(double) * nphase * nv * nv, cudaMemcpyHostToDevice));
+  s->have_phases = true;
+  s->have_table = false;
+  return FH_OK;
+}
+
+fh_status fh_set_reference(fh_solver* s, const double* C0) {
+  if (!s) { fh::set_error("null solver"); return FH_ERR_ARG; }
+  if (!s->have_phases) { fh::set_error("set the stiffness before the reference medium"); return FH_ERR_STATE; }
+  const int nv = s->g.nv, d = s->g.d;
+  double c0[36] = {};
+  if (C0) {
+    std::memcpy(c0, C0, sizeof(double) * nv * nv);
+  } else {
+    // Moulinec-Suquet rule on isotropic phases: lambda = C_1122, 2 mu = C_shear,shear (Mandel)
+    double lmin = 1e300, lmax = -1e300, mmin = 1e300, mmax = -1e300;
+    for (int q = 0; q < s->nphase; ++q) {
+      const double* C = s->Cp + q * nv * nv;
+      const double lam = C[0 * nv + 1];
+      const double mu = 0.5 * C[(nv - 1) * nv + (nv - 1)];
+      lmin = std::min(lmin, lam); lmax = std::max(lmax, lam);
+      mmin = std::min(mmin, mu); mmax = std::max(mmax, mu);
+    }
+    const double lam0 = 0.5 * (lmin + lmax), mu0 = 0.5 * (mmin + mmax);
+    for (int a = 0; a < d; ++a)
+      for (int b = 0; b < d; ++b) c0[a * nv + b] = lam0 + (a == b ? 2.0 * mu0 : 0.0);
+    for (int a = d; a < nv; ++a) c0[a * nv + a] = 2.0 * mu0;
+  }
+  for (int a = 0; a < nv; ++a)
+    for (int b = 0; b < nv; ++b)
+      if (!std::isfinite(c0[a * nv + b]) || std::fabs(c0[a * nv + b] - c0[b * nv + a]) > 1e-12 * (1 + std::fabs(c0[a * nv + b]))) {
+        fh::set_error("C0 not finite/symmetric");
+        return FH_ERR_ARG;
+      }
+  if (!cholesky_ok(c0, nv)) { fh::set_error("C0 is not positive definite"); return FH_ERR_ARG; }
+  std::memcpy(s->C0, c0, sizeof(c0));
+  fh::GreenParams GP{};
+  GP.d = d; GP.nv = nv; GP.ntri = s->g.ntri; GP.nd = s->g.nd;
+  for (int k = 0; k < 3; ++k) GP.dims[k] = s->g.dims[k];
+  GP.H = s->g.H; GP.nhalf = s->g.nhalf; GP.D = s->P.D; GP.sign = s->P.sign;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      GP.M[i][j] = s->P.M[i][j];
+      GP.adjT[i][j] = s->P.adjT[i][j];
+      GP.Fmap[i][j] = s->P.Fmap[i][j];
+    }
+  GP.kind = s->gen.kind;
+  for (int i = 0; i < 3; ++i) GP.alpha[i] = s->gen.alpha[i];
+  GP.n_xi = s->gen.n_xi;
+  for (int q = 0; q < 3 * 16; ++q) GP.xi[q] = s->gen.xi[q];
+  GP.radius = s->gen.alias_radius;
+  mandel_to_c4(c0, d, GP.C4);
+  fh_status rc = join_user(s);
+  if (rc != FH_OK) return rc;
+  CK(cudaMemsetAsync(s->err, 0, sizeof(int), s->work));
+  const int blocks = (int)((s->g.nhalf + 127) / 128);
+  fh::green_table<<<blocks, 128, 0, s->work>>>(GP, s->G64, s->G32, s->err);
+  CK(cudaGetLastError());
+  // stiffness differences C_p - C0
+  double dc[kMaxPhases * 36];
+  float dcf[kMaxPhases * 36];
+  for (int q = 0; q < s->nphase; ++q)
+    for (int e = 0; e < nv * nv; ++e) {
+      dc[q * nv * nv + e] = s->Cp[q * nv * nv + e] - c0[e];
+      dcf[q * nv * nv + e] = (float)dc[q * nv * nv + e];
+    }
+  CK(cudaMemcpyAsync(s->dC64, dc, sizeof(double) * s->nphase * nv * nv, cudaMemcpyHostToDevice, s->work));
+  CK(cudaMemcpyAsync(s->dC32, dcf, sizeof(float) * s->nphase * nv * nv, cudaMemcpyHostToDevice, s->work));
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->work));
+  CK(cudaStreamSynchronize(s->work));
+  if (herr != 0) {
+    fh::set_error("alias sum of |c_k(f)|^2 vanishes: translates cannot be orthonormalised");
+    return (fh_status)herr;
+  }
+  s->have_table = true;
+  return FH_OK;
+}
+
+fh_status fh_solve(fh_solver* s, int nload, const double* eps0, const fh_solve_opts* opts, fh_result* res) {
+  if (!s || !eps0 || !opts) { fh::set_error("null argument"); return FH_ERR_ARG; }
+  if (!s->have_table) { fh::set_error("set stiffness and reference medium first"); return FH_ERR_STATE; }
+  if (nload < 1 || nload > s->nload_max) { fh::set_error("nload out of range"); return FH_ERR_ARG; }
+  if (opts->max_iter < 1 || opts->max_iter > 10000000 || !(opts->tol >= 0.0)) { fh::set_error("bad tol/max_iter"); return FH_ERR_ARG; }
+  if (opts->precision != FH_PREC_FP64 && opts->precision != FH_PREC_FP32) { fh::set_error("unknown precision"); return FH_ERR_ARG; }
+  if (opts->init != 0 && opts->init != 1) { fh::set_error("init must be 0 or 1"); return FH_ERR_ARG; }
+  const int nv = s->g.nv;
+  for (int i = 0; i < nload * nv; ++i)
+    if (!std::isfinite(eps0[i])) { fh::set_error("non-finite eps0"); return FH_ERR_ARG; }
+  const int prec = opts->precision;
+  const int chunk = opts->chunk > 0 ? std::min(opts->chunk, 1024) : 32;
+  Control h{};
+  for (int l = 0; l < nload; ++l)
+    for (int c = 0; c < nv; ++c) h.eps0[l][c] = eps0[l * nv + c];
+  h.tol = opts->tol;
+  h.max_iter = opts->max_iter;
+  h.nload = nload;
+  h.hist_cap = kHistCap;
+  fh_status rc = join_user(s);
+  if (rc != FH_OK) return rc;
+  CK(cudaMemcpyAsync(s->ctl, &h, sizeof(Control), cudaMemcpyHostToDevice, s->work));
+  CK(cudaMemsetAsync(s->st, 0, FH_MAX_LOADS * sizeof(LoadState), s->work));
+  const size_t nfield = (size_t)nload * nv * s->g.m;
+  const unsigned conv_blocks = 1024;
+  if (opts->init == 0) {
+    if (prec == FH_PREC_FP64) CK(cudaMemsetAsync(s->E64, 0, nfield * sizeof(double), s->work));
+    else CK(cudaMemsetAsync(s->E32, 0, nfield * sizeof(float), s->work));
+  } else if (s->E_prec != prec) {
+    if (prec == FH_PREC_FP64) fh::convert_copy<double, float><<<conv_blocks, kThreads, 0, s->work>>>(s->E64, s->E32, (long long)nfield);
+    else fh::convert_copy<float, double><<<conv_blocks, kThreads, 0, s->work>>>(s->E32, s->E64, (long long)nfield);
+    CK(cudaGetLastError());
+  }
+  s->E_prec = prec;
+  rc = prec == FH_PREC_FP64 ? run_solve<double>(s, prec, nload, chunk, opts->max_iter)
+                            : run_solve<float>(s, prec, nload, chunk, opts->max_iter);
+  if (rc != FH_OK) return rc;
+  LoadState hs[FH_MAX_LOADS];
+  double ms[FH_MAX_LOADS * fh::MAXV];
+  CK(cudaMemcpyAsync(hs, s->st, sizeof(LoadState) * nload, cudaMemcpyDeviceToHost, s->work));
+  CK(cudaMemcpyAsync(ms, s->mstress, sizeof(double) * nload * fh::MAXV, cudaMemcpyDeviceToHost, s->work));
+  CK(cudaStreamSynchronize(s->work));
+  float ms_elapsed = 0.f;
+  CK(cudaEventElapsedTime(&ms_elapsed, s->ev0, s->ev1));
+  fh_status worst = FH_OK;
+  auto rank = [](int st) { return st == FH_NONFINITE ? 3 : st == FH_DIVERGED ? 2 : st == FH_NOT_CONVERGED ? 1 : 0; };
+  if (res) std::memset(res, 0, sizeof(*res));
+  for (int l = 0; l < nload; ++l) {
+    if (rank(hs[l].status) > rank(worst)) worst = (fh_status)hs[l].status;
+    s->last_iters[l] = hs[l].iter;
+    if (res) {
+      res->iterations[l] = hs[l].iter;
+      res->residual[l] = hs[l].r;
+      res->status[l] = hs[l].status;
+      for (int c = 0; c < nv; ++c) res->mean_stress[l * 6 + c] = ms[l * fh::MAXV + c];
+    }
+    for (int c = 0; c < nv; ++c) {
+      s->last_ms[l * 6 + c] = ms[l * fh::MAXV + c];
+      s->last_eps0[l * 6 + c] = eps0[l * nv + c];
+    }
+  }
+  if (res) res->elapsed_ms = ms_elapsed;
+  s->last_nload = nload;
+  s->have_solution = true;
+  return worst;
+}
+
+fh_status fh_get_strain(const fh_solver* sc, int load, double* E) {
+  fh_solver* s = const_cast<fh_solver*>(sc);
+  if (!s || !E) { fh::set_error("null argument"); return FH_ERR_ARG; }
+  if (load < 0 || load >= s->nload_max) { fh::set_error("load out of range"); return FH_ERR_ARG; }
+  if (s->E_prec < 0) { fh::set_error("no strain available"); return FH_ERR_STATE; }
+  const size_t n = (size_t)s->g.nv * s->g.m;
+  const size_t off = (size_t)load * n;
+  fh_status rc = join_user(s);
+  if (rc != FH_OK) return rc;
+  if (s->E_prec == FH_PREC_FP64) {
+    CK(cudaMemcpyAsync(E, s->E64 + off, n * sizeof(double), cudaMemcpyDefault, s->work));
+  } else {
+    if (!s->scratch64) CK(cudaMalloc(&s->scratch64, n * sizeof(double)));
+    fh::convert_copy<double, float><<<1024, kThreads, 0, s->work>>>(s->scratch64, s->E32 + off, (long long)n);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(E, s->scratch64, n * sizeof(double), cudaMemcpyDefault, s->work));
+  }
+  CK(cudaStreamSynchronize(s->work));
+  return FH_OK;
+}
+
+fh_status fh_set_strain(fh_solver* s, int load, const double* E) {
+  if (!s || !E) { fh::set_error("null argument"); return FH_ERR_ARG; }
+  if (load < 0 || load >= s->nload_max) { fh::set_error("load out of range"); return FH_ERR_ARG; }
+  const size_t n = (size_t)s->g.nv * s->g.m;
+  fh_status rc = join_user(s);
+  if (rc != FH_OK) return rc;
+  if (s->E_prec == FH_PREC_FP32) {
+    // keep every load in one precision: bring the others to FP64 first
+    fh::convert_copy<double, float><<<1024, kThreads, 0, s->work>>>(s->E64, s->E32, (long long)(n * s->nload_max));
+    CK(cudaGetLastError());
+  }
+  CK(cudaMemcpyAsync(s->E64 + (size_t)load * n, E, n * sizeof(double), cudaMemcpyDefault, s->work));
+  CK(cudaStreamSynchronize(s->work));
+  s->E_prec = FH_PREC_FP64;
+  return FH_OK;
+}
+
+fh_status fh_get_ceff(const fh_solver* s, double* Ceff, int voigt) {
+  if (!s || !Ceff) { fh::set_error("null argument"); return FH_ERR_ARG; }
+  const int nv = s->g.nv;
+  if (!s->have_solution || s->last_nload != nv) { fh::set_error("C_eff needs a solve with nload = n_v"); return FH_ERR_STATE; }
+  // <sigma>_l = C_eff eps0_l  =>  S = E0 C^T  (rows l);  solve E0 X = S, C = X^T
+  double A[36], X[36];
+  for (int l = 0; l < nv; ++l)
+    for (int c = 0; c < nv; ++c) {
+      A[l * nv + c] = s->last_eps0[l * 6 + c];
+      X[l * nv + c] = s->last_ms[l * 6 + c];
+    }
+  for (int col = 0; col < nv; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < nv; ++r)
+      if (std::fabs(A[r * nv + col]) > std::fabs(A[piv * nv + col])) piv = r;
+    if (std::fabs(A[piv * nv + col]) < 1e-300) { fh::set_error("eps0 of the last solve is singular"); return FH_ERR_STATE; }
+    for (int c = 0; c < nv; ++c) { std::swap(A[col * nv + c], A[piv * nv + c]); std::swap(X[col * nv + c], X[piv * nv + c]); }
+    for (int r = 0; r < nv; ++r) {
+      if (r == col) continue;
+      const double f = A[r * nv + col] / A[col * nv + col];
+      for (int c = 0; c < nv; ++c) { A[r * nv + c] -= f * A[col * nv + c]; X[r * nv + c] -= f * X[col * nv + c]; }
+    }
+  }
+  for (int r = 0; r < nv; ++r)
+    for (int c = 0; c < nv; ++c) X[r * nv + c] /= A[r * nv + r];
+  const int d = s->g.d;
+  for (int a = 0; a < nv; ++a)
+    for (int b = 0; b < nv; ++b) {
+      double v = X[b * nv + a];
+      if (voigt) v /= ((a < d ? 1.0 : std::sqrt(2.0)) * (b < d ? 1.0 : std::sqrt(2.0)));
+      Ceff[a * nv + b] = v;
+    }
+  return FH_OK;
+}
+
+fh_status fh_get_green(const fh_solver* s, double* G) {
+  if (!s || !G) { fh::set_error("null argument"); return FH_ERR_ARG; }
+  if (!s->have_table) { fh::set_error("no table"); return FH_ERR_STATE; }
+  const int nv = s->g.nv, nt = s->g.ntri;
+  const size_t nh = (size_t)s->g.nhalf;
+  std::vector<double> t((size_t)nt * nh);
+  CK(cudaMemcpy(t.data(), s->G64, t.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  for (size_t f = 0; f < nh; ++f) {
+    int q = 0;
+    for (int a = 0; a < nv; ++a)
+      for (int b = a; b < nv; ++b) {
+        const double v = t[(size_t)q * nh + f];
+        G[f * nv * nv + a * nv + b] = v;
+        G[f * nv * nv + b * nv + a] = v;
+        ++q;
+      }
+  }
+  return FH_OK;
+}
+
+fh_status fh_get_residuals(const fh_solver* s, int load, double* hist, int* n) {
+  if (!s || !n) { fh::set_error("null argument"); return FH_ERR_ARG; }
+  if (!s->have_solution || load < 0 || load >= s->last_nload) { fh::set_error("no such load in the last solve"); return FH_ERR_STATE; }
+  const int cnt = std::min(s->last_iters[load], kHistCap);
+  *n = cnt;
+  if (hist && cnt > 0) CK(cudaMemcpy(hist, s->hist + (size_t)load * kHistCap, cnt * sizeof(double), cudaMemcpyDeviceToHost));
+  return FH_OK;
+}
+
+}  // extern "C"

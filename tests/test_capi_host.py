@@ -1,0 +1,96 @@
+"""C-ABI checks that need no GPU: the library loads, exports every declared entry
+point, and its host-side lattice maps agree with the oracle's enumeration."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import lattice
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fh():
+    from paper_1701_04685_gb300 import build
+    build.build()
+    import paper_1701_04685_gb300 as fh
+    fh.library()
+    return fh
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "fftHomog.h")).read()
+    return sorted(set(re.findall(r"\b(fh_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(fh):
+    lib = ctypes.CDLL(fh.LIB)
+    names = _declared()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(fh.exported_symbols()) == set(names)
+
+
+MATS = [[[128, 32], [0, 128]], [[4, -2], [4, 14]], [[3, 1, 0], [0, 2, 1], [1, 0, 3]],
+        [[64, 64], [-64, 64]], [[9, 3], [0, 15]], [[6, 0, 0], [0, 10, 0], [0, 0, 12]],
+        [[32, 0], [0, 32]], [[128, 272], [0, 128]]]
+
+
+@pytest.mark.parametrize("M", MATS)
+def test_pattern_maps_match_oracle(fh, M):
+    p = fh.Pattern(M)
+    D = abs(lattice.det_int(M))
+    assert p.m == D and int(np.prod(p.dims)) == D
+    A = p.numerators()
+    ref, _ = lattice.pattern(M)
+    assert sorted(map(tuple, A.tolist())) == sorted(map(tuple, ref.tolist()))
+    assert np.allclose(p.points(), A / D, rtol=0, atol=0)
+    H = p.half_freqs()
+    G = set(map(tuple, lattice.generating_set(M).tolist()))
+    assert all(tuple(h) in G for h in H)
+    assert len(set(map(tuple, H.tolist()))) == len(H)
+
+
+@pytest.mark.parametrize("M", MATS)
+def test_storage_grid_carries_the_pattern_dft(fh, M, rng):
+    """exp(-2 pi i h^T y) = exp(-2 pi i sum_k l_k n_k / dims_k) for stored points and
+    stored half-spectrum frequencies (Eq. (Fouriermatrix) on the storage grid)."""
+    p = fh.Pattern(M)
+    D = p.m
+    A = p.numerators()
+    H = p.half_freqs()
+    dims = p.dims
+    hl = dims[-1] // 2 + 1
+    half_shape = dims[:-1] + [hl]
+    for _ in range(300):
+        i = int(rng.integers(D))
+        f = int(rng.integers(len(H)))
+        n = np.unravel_index(i, dims)
+        l = np.unravel_index(f, half_shape)
+        lhs = int(H[f].astype(object).dot(A[i].astype(object))) % D
+        rhs = sum(int(l[k]) * int(n[k]) * (D // dims[k]) for k in range(len(dims))) % D
+        assert lhs == rhs
+
+
+def test_error_codes_without_gpu(fh):
+    with pytest.raises(fh.FhError) as e:
+        fh.Pattern([[2, 4], [1, 2]])
+    assert e.value.status == -2          # FH_ERR_SINGULAR_M
+    with pytest.raises(fh.FhError) as e:
+        fh.Pattern([[1 << 21, 0], [0, 3]])
+    assert e.value.status == -3          # FH_ERR_OVERFLOW
+    p = fh.Pattern([[17, 0], [0, 17]])   # axis of prime length 17
+    with pytest.raises(fh.FhError) as e:
+        fh.Solver(p, fh.generator("dirichlet"), 3)
+    assert e.value.status == -8          # FH_ERR_UNSUPPORTED
+    p = fh.Pattern([[8, 0], [0, 8]])
+    with pytest.raises(fh.FhError) as e:
+        fh.Solver(p, fh.generator("dlvp", alpha=[0.7, 0.1]), 3)
+    assert e.value.status == -1          # alpha outside [0, 1/2]
+    with pytest.raises(fh.FhError) as e:
+        fh.Solver(p, fh.generator("dirichlet"), 17)
+    assert e.value.status == -1          # nload_max > FH_MAX_LOADS

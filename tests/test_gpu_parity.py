@@ -1,0 +1,190 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Bar (FP64 mode): strain fields, residual histories, mean stresses and C_eff
+within 1e-10 relative of the oracle; the Gamma^p table within 1e-12.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from parity import Case, rel
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+@pytest.fixture(scope="module")
+def fh():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1701_04685_gb300 import build
+    build.build()
+    import paper_1701_04685_gb300 as fh
+    return fh
+
+
+def _disk(d, r=0.27, c=None):
+    c = np.full((1, d), 0.07) if c is None else c
+    return c, np.array([r])
+
+
+# (name, M, generator, phases, inclusions) -- shapes chosen to cover 1-, 2- and
+# 3-axis grids, odd and even lengths, radices 2/3/4/5/8, ragged tiles
+CASES = [
+    ("disk32_dirichlet", [[32, 0], [0, 32]], {"kind": "dirichlet"}, [(1.0, 0.3), (10.0, 0.3)], _disk(2, 0.2523, np.zeros((1, 2)))),
+    ("sheared_odd_dlvp", [[9, 3], [0, 15]], {"kind": "dlvp", "alpha": [0.25, 0.1]}, [(1.0, 0.3), (20.0, 0.25)], _disk(2)),
+    ("onedim_grid", [[3, 1], [0, 5]], {"kind": "dlvp", "alpha": [0.3, 0.3]}, [(1.0, 0.3), (5.0, 0.3)], _disk(2, 0.3)),
+    ("quincunx_box", [[8, 8], [-8, 8]], {"kind": "boxspline", "order": 2, "radius": 3}, [(2.0, 0.3), (30.0, 0.2)], _disk(2)),
+    ("radix_mix_2d", [[24, 0], [0, 40]], {"kind": "dirichlet"}, [(1.0, 0.3), (8.0, 0.3)], _disk(2, 0.3)),
+    ("grid3d_three_axes", [[2, 0, 0], [0, 4, 0], [0, 0, 8]], {"kind": "dirichlet"}, [(1.0, 0.3), (10.0, 0.3)], _disk(3, 0.3)),
+    ("box3d_small", [[12, 0, 0], [0, 12, 0], [0, 0, 12]], {"kind": "boxspline", "order": 2, "radius": 2},
+     [(1.0, 0.3), (50.0, 0.3)], _disk(3, 0.25)),
+    ("sheared3d_dlvp", [[6, 2, 0], [0, 6, 2], [0, 0, 10]], {"kind": "dlvp", "alpha": [0.2, 0.3, 0.1]},
+     [(1.0, 0.3), (15.0, 0.3)], _disk(3, 0.3)),
+]
+
+
+def _case(spec):
+    name, M, gen, phases, (c, r) = spec
+    return Case(M, gen, phases, c, r)
+
+
+@pytest.mark.parametrize("spec", CASES, ids=[c[0] for c in CASES])
+def test_green_table_matches_oracle(fh, spec):
+    case = _case(spec)
+    s = case.product(fh)
+    fp = case.freq_perm(case.pattern)
+    Gg = s.get_green()
+    Go = case.Gp[fp]
+    assert rel(Gg, Go) < 1e-12
+
+
+@pytest.mark.parametrize("spec", CASES, ids=[c[0] for c in CASES])
+def test_fixed_iterations_match_oracle(fh, spec):
+    case = _case(spec)
+    s = case.product(fh)
+    n = 25
+    out = s.solve(case.eps0, tol=0.0, max_iter=n)
+    ref = case.oracle_solve(tol=0.0, max_iter=n)
+    assert list(out["iterations"]) == [n] * case.nload
+    assert case.strain_error(s, ref["E"]) < TOL64
+    for L in range(case.nload):
+        assert rel(s.get_residuals(L), ref["resid"][L]) < 1e-9
+    assert rel(out["mean_stress"], ref["mean_stress"]) < TOL64
+
+
+def test_config_disk32_to_tolerance(fh):
+    """M = diag(32,32), Dirichlet, one disk of vf 0.2 at contrast 10, 3 loads, r <= 1e-8."""
+    w = W.disk32()
+    case = Case.from_workload(w)
+    s = case.product(fh)
+    out = s.solve(case.eps0, tol=w["tol"], max_iter=5000)
+    assert out["status"] == 0
+    ref = case.oracle_solve(tol=w["tol"], max_iter=5000)
+    assert np.all(np.abs(out["iterations"] - ref["iters"]) <= 1)
+    ref = case.oracle_solve(tol=0.0, max_iter=int(out["iterations"].max()))  # equal counts
+    # loads may stop at different n; compare each load at its own count
+    for L in range(3):
+        refL = case.oracle_solve(tol=0.0, max_iter=int(out["iterations"][L]), eps0=case.eps0[L:L + 1])
+        Eg = s.get_strain(L)
+        Eo = refL["E"][0][case.perm].T
+        assert np.abs(Eg - Eo).max() / np.abs(Eo + case.eps0[L][:, None]).max() < TOL64
+    from oracle import scheme as OS
+    Cg = s.get_ceff()
+    ms = np.stack([case.oracle_solve(tol=0.0, max_iter=int(out["iterations"][L]),
+                                     eps0=case.eps0[L:L + 1])["mean_stress"][0] for L in range(3)])
+    Co = OS.effective_stiffness(ms, case.eps0)
+    assert rel(Cg, Co) < TOL64
+    assert rel(Cg, Cg.T) < 1e-6
+
+
+def test_config_dlvp_sheared_full_size(fh):
+    """M = [[128,32],[0,128]] (grid 32 x 512), dlVP, 20 disks at contrast 100: the
+    benchmark workload, FP64, 200 iterations element by element against the oracle."""
+    w = W.dlvp_sheared()
+    case = Case.from_workload(w)
+    s = case.product(fh)
+    n = 200
+    out = s.solve(case.eps0, tol=0.0, max_iter=n)
+    ref = case.oracle_solve(tol=0.0, max_iter=n)
+    assert case.strain_error(s, ref["E"]) < TOL64
+    assert rel(out["mean_stress"], ref["mean_stress"]) < TOL64
+
+
+def test_homogeneous_medium_stops_after_one_iteration(fh):
+    case = Case([[16, 4], [0, 20]], {"kind": "dlvp", "alpha": [0.25, 0.25]}, [(3.0, 0.3), (3.0, 0.3)],
+                np.zeros((1, 2)), np.array([0.2]))
+    s = case.product(fh)
+    out = s.solve(case.eps0, tol=1e-12, max_iter=50)
+    assert list(out["iterations"]) == [1, 1, 1]
+    for L in range(3):
+        assert np.abs(s.get_strain(L)).max() < 1e-14
+
+
+def test_resume_is_bitwise_identical(fh):
+    case = _case(CASES[1])
+    s = case.product(fh)
+    s.solve(case.eps0, tol=0.0, max_iter=20)
+    E20 = [s.get_strain(L).copy() for L in range(3)]
+    s.solve(case.eps0, tol=0.0, max_iter=12)
+    s.solve(case.eps0, tol=0.0, max_iter=8, init=1)
+    for L in range(3):
+        assert np.array_equal(s.get_strain(L), E20[L])
+
+
+def test_set_strain_then_resume(fh):
+    case = _case(CASES[0])
+    s = case.product(fh)
+    ref = case.oracle_solve(tol=0.0, max_iter=15)
+    s.solve(case.eps0, tol=0.0, max_iter=5)
+    for L in range(3):
+        s.set_strain(L, np.ascontiguousarray(s.get_strain(L)))
+    s.solve(case.eps0, tol=0.0, max_iter=10, init=1)
+    assert case.strain_error(s, ref["E"]) < TOL64
+
+
+def test_device_pointers(fh):
+    import torch
+    case = _case(CASES[0])
+    s = case.product(fh, phase_tensor=lambda ids: torch.from_numpy(ids).cuda())
+    s.solve(case.eps0, tol=0.0, max_iter=10)
+    ref = case.oracle_solve(tol=0.0, max_iter=10)
+    out = torch.empty((3, case.D), dtype=torch.float64, device="cuda")
+    s.get_strain(1, out)
+    Eo = ref["E"][1][case.perm].T
+    assert np.abs(out.cpu().numpy() - Eo).max() < TOL64
+
+
+def test_error_paths(fh):
+    p = fh.Pattern([[8, 0], [0, 8]])
+    s = fh.Solver(p, fh.generator("dirichlet"), 3)
+    with pytest.raises(fh.FhError) as e:
+        s.solve(np.eye(3), tol=0.0, max_iter=3)
+    assert e.value.status == -9
+    Cp = np.stack([fh.isotropic_stiffness(1.0, 1.0, 2)] * 2)
+    with pytest.raises(fh.FhError) as e:
+        s.set_stiffness_phases(np.full(64, 2, np.uint8), Cp)   # phase id 2 >= nphase 2
+    assert e.value.status == -1
+    Cp[1] *= 4.0
+    s.set_stiffness_phases((np.arange(64) % 3 == 0).astype(np.uint8), Cp)
+    with pytest.raises(fh.FhError) as e:
+        s.set_reference(-np.eye(3))
+    assert e.value.status == -1
+    s.set_reference(None)
+    with pytest.raises(fh.FhError) as e:
+        s.solve(np.eye(3), tol=-1.0, max_iter=3)
+    assert e.value.status == -1
+    out = s.solve(np.eye(3), tol=0.0, max_iter=3)
+    assert out["status"] == 1 and list(out["iterations"]) == [3, 3, 3]
+
+
+def test_nonfinite_stiffness_is_reported(fh):
+    """A NaN in a phase stiffness is refused at the boundary (host check)."""
+    p = fh.Pattern([[8, 0], [0, 8]])
+    s = fh.Solver(p, fh.generator("dirichlet"), 3)
+    Cp = np.stack([fh.isotropic_stiffness(1.0, 1.0, 2)] * 2)
+    Cp[1, 0, 0] = np.nan
+    with pytest.raises(fh.FhError) as e:
+        s.set_stiffness_phases(np.zeros(64, np.uint8), Cp)
+    assert e.value.status == -1
