@@ -65,8 +65,10 @@ typedef enum {
                             trapezoid g, flat for |u_i| <= 1/2 - alpha_i, zero
                             for |u_i| >= 1/2 + alpha_i, linear in between.   */
   FH_GEN_BOXSPLINE = 2   /* periodised pattern box spline: g(u) =
-                            prod_{xi in Xi} sinc(pi xi^T u), alias sums
-                            truncated to z in {-r..r}^d (Sec. 3.2 end).      */
+                            prod_{xi in Xi} sinc(pi xi^T u); the alias sums
+                            (Sec. 3.2, end) keep the aliases k = h + M^T z
+                            with |(M^-T k)_i| <= r + 1/2, a cube symmetric in
+                            k so that Gamma^p stays even.                    */
 } fh_gen_kind;
 
 #define FH_MAX_XI 16
@@ -105,6 +107,7 @@ typedef struct {
   double mean_stress[FH_MAX_LOADS * 6];/* <C:(E+eps0)> per load, Mandel, FP64 */
   double elapsed_ms;                   /* device time from first launch to
                                           the mean-stress reduction          */
+  long long kernel_launches;           /* CUDA kernels launched by the solve */
 } fh_result;
 
 typedef struct fh_pattern fh_pattern;
@@ -196,6 +199,20 @@ fh_status fh_get_green(const fh_solver* s, double* G);
 /* Residual history r_1..r_n of one load from the last solve: hist[n] host;
  * *n receives the count (hist may be NULL to query it). */
 fh_status fh_get_residuals(const fh_solver* s, int load, double* hist, int* n);
+
+/* Profiling aid: time each kind of iteration pass of the current solver in
+ * isolation with CUDA events on the solver's stream, `reps` back-to-back
+ * launches each after one warm-up launch, for `nload` loads in the given
+ * precision.  ms[4] (host) receives the mean duration per launch of
+ *   [0] the row pass (contiguous axis, fused constitutive stage + residual),
+ *   [1] the axis-0 line pass with the Green step (or the Green step alone on
+ *       1-axis grids),
+ *   [2] a forward middle-axis line pass (3-axis grids, else 0),
+ *   [3] an inverse middle-axis line pass (3-axis grids, else 0).
+ * The passes run on the solver's own buffers and advance its iterate: call it
+ * after the results of the last solve have been read.  Requires a prior
+ * fh_solve with the same nload (it reuses that solve's eps0). */
+fh_status fh_profile_passes(fh_solver* s, int nload, int precision, int reps, double* ms);
 
 const char* fh_status_string(fh_status st);
 const char* fh_last_error(void);

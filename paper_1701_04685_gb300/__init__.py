@@ -50,7 +50,7 @@ class fh_solve_opts(C.Structure):
 class fh_result(C.Structure):
     _fields_ = [("iterations", C.c_int * FH_MAX_LOADS), ("residual", C.c_double * FH_MAX_LOADS),
                 ("status", C.c_int * FH_MAX_LOADS), ("mean_stress", C.c_double * (FH_MAX_LOADS * 6)),
-                ("elapsed_ms", C.c_double)]
+                ("elapsed_ms", C.c_double), ("kernel_launches", C.c_longlong)]
 
 
 _lib = None
@@ -81,6 +81,7 @@ def library():
             "fh_get_ceff": (I, [P, P, I]),
             "fh_get_green": (I, [P, P]),
             "fh_get_residuals": (I, [P, I, P, P]),
+            "fh_profile_passes": (I, [P, I, I, I, P]),
             "fh_status_string": (C.c_char_p, [I]),
             "fh_last_error": (C.c_char_p, []),
         }
@@ -97,7 +98,8 @@ def exported_symbols():
     return ["fh_pattern_create", "fh_pattern_destroy", "fh_pattern_info", "fh_pattern_points",
             "fh_pattern_numerators", "fh_pattern_half_freqs", "fh_solver_create", "fh_solver_destroy",
             "fh_set_stiffness_phases", "fh_set_reference", "fh_solve", "fh_get_strain", "fh_set_strain",
-            "fh_get_ceff", "fh_get_green", "fh_get_residuals", "fh_status_string", "fh_last_error"]
+            "fh_get_ceff", "fh_get_green", "fh_get_residuals", "fh_profile_passes", "fh_status_string",
+            "fh_last_error"]
 
 
 def _check(rc, ok=(FH_OK,)):
@@ -260,6 +262,7 @@ class Solver:
             "load_status": np.array(res.status[:n]),
             "mean_stress": np.array(res.mean_stress[: n * 6]).reshape(n, 6)[:, : self.nv],
             "elapsed_ms": res.elapsed_ms,
+            "kernel_launches": res.kernel_launches,
         }
 
     def get_strain(self, load, out=None):
@@ -292,3 +295,9 @@ class Solver:
         if n.value:
             _check(library().fh_get_residuals(self._h, int(load), _ptr(out), C.byref(n)))
         return out
+
+    def profile_passes(self, nload, precision=FH_PREC_FP64, reps=50):
+        """Mean ms per launch of [row pass, axis-0 Green pass, mid forward, mid inverse]."""
+        ms = np.zeros(4)
+        _check(library().fh_profile_passes(self._h, int(nload), int(precision), int(reps), _ptr(ms)))
+        return ms

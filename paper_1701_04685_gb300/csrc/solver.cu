@@ -262,8 +262,10 @@ fh_status get_graph(fh_solver* s, int prec, int nload, int chunk, cudaGraphExec_
   return FH_OK;
 }
 
+int line_launches_per_iter(const GridInfo& g) { return g.nd == 1 ? 1 : 1 + 2 * (g.nd - 2); }
+
 template <typename T>
-fh_status run_solve(fh_solver* s, int prec, int nload, int chunk, int max_iter) {
+fh_status run_solve(fh_solver* s, int prec, int nload, int chunk, int max_iter, long long* launches) {
   fh_status rc = set_smem_attrs<T>(s, prec);
   if (rc != FH_OK) return rc;
   cudaGraphExec_t exec;
@@ -289,6 +291,7 @@ fh_status run_solve(fh_solver* s, int prec, int nload, int chunk, int max_iter) 
                                                             s->mstress, bpl);
   CK(cudaGetLastError());
   CK(cudaEventRecord(s->ev1, s->work));
+  *launches = 2 + launched * (1 + line_launches_per_iter(s->g));
   return FH_OK;
 }
 
@@ -353,6 +356,72 @@ void mandel_to_c4(const double* Cm, int d, double* C4) {
     }
 }
 
+}  // namespace
+
+namespace {
+template <typename T>
+fh_status profile_passes(fh_solver* s, int prec, int nload, int reps, double* ms) {
+  fh_status rc = set_smem_attrs<T>(s, prec);
+  if (rc != FH_OK) return rc;
+  // every load active, no stopping: tol 0 and a max_iter beyond any count
+  int big = 0x7fffffff;
+  double zero = 0.0;
+  CK(cudaMemsetAsync(s->st, 0, FH_MAX_LOADS * sizeof(LoadState), s->work));
+  CK(cudaMemcpyAsync(&s->ctl->tol, &zero, sizeof(double), cudaMemcpyHostToDevice, s->work));
+  CK(cudaMemcpyAsync(&s->ctl->max_iter, &big, sizeof(int), cudaMemcpyHostToDevice, s->work));
+  CK(cudaMemcpyAsync(&s->ctl->nload, &nload, sizeof(int), cudaMemcpyHostToDevice, s->work));
+  const GridInfo& g = s->g;
+  using C = typename fh::cplx_t<T>::type;
+  C* S = reinterpret_cast<C*>(s->S);
+  for (int q = 0; q < 4; ++q) ms[q] = 0.0;
+  auto timed = [&](int q, auto&& launch) -> fh_status {
+    launch();
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(s->ev0, s->work));
+    for (int i = 0; i < reps; ++i) launch();
+    CK(cudaEventRecord(s->ev1, s->work));
+    CK(cudaEventSynchronize(s->ev1));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, s->ev0, s->ev1));
+    ms[q] = (double)t / reps;
+    return FH_OK;
+  };
+  rc = timed(0, [&] { enqueue_row_pass<T, false>(s, prec, nload); });
+  if (rc != FH_OK) return rc;
+  auto line = [&](int a, int mode) {
+    long long n_outer = 1, n_inner = 1;
+    for (int k = 0; k < a; ++k) n_outer *= g.dims[k];
+    for (int k = a + 1; k + 1 < g.nd; ++k) n_inner *= g.dims[k];
+    const unsigned blocks = (unsigned)((long long)nload * n_outer * n_inner * s->ntiles[prec][a]);
+    const size_t sm = s->line_smem[prec][a];
+    const int W = s->lineW[prec][a], nt = s->ntiles[prec][a];
+    if (mode == 0)
+      fh::line_pass<T, 0><<<blocks, kThreads, sm, s->work>>>(g, s->ax[a].plan, twp<T>(s->ax[a]), S, Gptr<T>(s), s->st, a, W, nt, (int)n_outer, (int)n_inner);
+    else if (mode == 1)
+      fh::line_pass<T, 1><<<blocks, kThreads, sm, s->work>>>(g, s->ax[a].plan, twp<T>(s->ax[a]), S, Gptr<T>(s), s->st, a, W, nt, (int)n_outer, (int)n_inner);
+    else
+      fh::line_pass<T, 2><<<blocks, kThreads, sm, s->work>>>(g, s->ax[a].plan, twp<T>(s->ax[a]), S, Gptr<T>(s), s->st, a, W, nt, (int)n_outer, (int)n_inner);
+  };
+  if (g.nd == 1) {
+    rc = timed(1, [&] {
+      const long long total = (long long)nload * g.nhalf;
+      const int blocks = (int)std::min<long long>((total + kThreads - 1) / kThreads, 4096);
+      fh::green_1d<T><<<blocks, kThreads, 0, s->work>>>(g, S, Gptr<T>(s), s->st, nload);
+    });
+    if (rc != FH_OK) return rc;
+  } else {
+    rc = timed(1, [&] { line(0, 2); });
+    if (rc != FH_OK) return rc;
+    if (g.nd == 3) {
+      rc = timed(2, [&] { line(1, 0); });
+      if (rc != FH_OK) return rc;
+      rc = timed(3, [&] { line(1, 1); });
+      if (rc != FH_OK) return rc;
+    }
+  }
+  CK(cudaStreamSynchronize(s->work));
+  return FH_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -671,8 +740,9 @@ fh_status fh_solve(fh_solver* s, int nload, const double* eps0, const fh_solve_o
     CK(cudaGetLastError());
   }
   s->E_prec = prec;
-  rc = prec == FH_PREC_FP64 ? run_solve<double>(s, prec, nload, chunk, opts->max_iter)
-                            : run_solve<float>(s, prec, nload, chunk, opts->max_iter);
+  long long launches = 0;
+  rc = prec == FH_PREC_FP64 ? run_solve<double>(s, prec, nload, chunk, opts->max_iter, &launches)
+                            : run_solve<float>(s, prec, nload, chunk, opts->max_iter, &launches);
   if (rc != FH_OK) return rc;
   LoadState hs[FH_MAX_LOADS];
   double ms[FH_MAX_LOADS * fh::MAXV];
@@ -698,7 +768,10 @@ fh_status fh_solve(fh_solver* s, int nload, const double* eps0, const fh_solve_o
       s->last_eps0[l * 6 + c] = eps0[l * nv + c];
     }
   }
-  if (res) res->elapsed_ms = ms_elapsed;
+  if (res) {
+    res->elapsed_ms = ms_elapsed;
+    res->kernel_launches = launches;
+  }
   s->last_nload = nload;
   s->have_solution = true;
   return worst;
@@ -795,6 +868,19 @@ fh_status fh_get_green(const fh_solver* s, double* G) {
       }
   }
   return FH_OK;
+}
+
+
+fh_status fh_profile_passes(fh_solver* s, int nload, int precision, int reps, double* ms) {
+  if (!s || !ms) { fh::set_error("null argument"); return FH_ERR_ARG; }
+  if (!s->have_solution || nload != s->last_nload) { fh::set_error("profile needs a prior solve with the same nload"); return FH_ERR_STATE; }
+  if (reps < 1 || reps > 100000) { fh::set_error("reps out of range"); return FH_ERR_ARG; }
+  if (precision != FH_PREC_FP64 && precision != FH_PREC_FP32) { fh::set_error("unknown precision"); return FH_ERR_ARG; }
+  if (precision != s->E_prec) { fh::set_error("profile precision must match the last solve"); return FH_ERR_STATE; }
+  fh_status rc = join_user(s);
+  if (rc != FH_OK) return rc;
+  return precision == FH_PREC_FP64 ? profile_passes<double>(s, precision, nload, reps, ms)
+                                   : profile_passes<float>(s, precision, nload, reps, ms);
 }
 
 fh_status fh_get_residuals(const fh_solver* s, int load, double* hist, int* n) {
