@@ -99,7 +99,7 @@ def exported_symbols():
             "fh_pattern_numerators", "fh_pattern_half_freqs", "fh_solver_create", "fh_solver_destroy",
             "fh_set_stiffness_phases", "fh_set_reference", "fh_solve", "fh_get_strain", "fh_set_strain",
             "fh_get_ceff", "fh_get_green", "fh_get_residuals", "fh_profile_passes", "fh_status_string",
-            "fh_last_error"]
+            "fh_last_error", "fh_mean_stress_noalloc"]
 
 
 def _check(rc, ok=(FH_OK,)):
