@@ -85,7 +85,13 @@ typedef struct {
   int alias_radius;         /* FH_GEN_BOXSPLINE: r in 0..16                  */
 } fh_generator;
 
-typedef enum { FH_PREC_FP64 = 0, FH_PREC_FP32 = 1 } fh_precision;
+/* FH_PREC_FP64: every stage in FP64.  FH_PREC_FP32: FFT, stress and Green
+ * stages in FP32 (table built in FP64 and rounded; residual sums carried with
+ * about 48 bits; mean stress in FP64).  FH_PREC_MIXED: the FP32 iteration to
+ * the tolerance, then one FP64 iteration from its iterate, which removes most
+ * of the FP32 rounding from E and C_eff; the reported residual of each load is
+ * that FP64 step's Cauchy residual and the iteration count includes it. */
+typedef enum { FH_PREC_FP64 = 0, FH_PREC_FP32 = 1, FH_PREC_MIXED = 2 } fh_precision;
 
 typedef struct {
   double tol;      /* Cauchy tolerance: a load stops after the first iteration n
@@ -98,6 +104,13 @@ typedef struct {
   int init;        /* 0: start from E = 0; 1: start from the strain left by
                       the previous solve or set by fh_set_strain (resume)    */
   int chunk;       /* iterations per captured CUDA-graph replay; 0 = 32      */
+  int path;        /* 0 = automatic; 1 = whole-GPU passes (one kernel per axis
+                      per iteration, CUDA-graph replays); 2 = cluster-resident
+                      (2-axis grids only: one thread-block cluster per load
+                      case holds the fields in distributed shared memory and
+                      runs every iteration in one launch).  Automatic picks 2
+                      when the fields fit, else 1.                            */
+  int cluster;     /* cluster size for path 2: 0 = automatic, 8 or 16        */
 } fh_solve_opts;
 
 typedef struct {
@@ -108,6 +121,8 @@ typedef struct {
   double elapsed_ms;                   /* device time from first launch to
                                           the mean-stress reduction          */
   long long kernel_launches;           /* CUDA kernels launched by the solve */
+  int path;                            /* path taken (1 or 2)                 */
+  int cluster;                         /* cluster size used by path 2         */
 } fh_result;
 
 typedef struct fh_pattern fh_pattern;

@@ -22,7 +22,7 @@ from .build import LIB
 
 FH_OK, FH_NOT_CONVERGED, FH_DIVERGED, FH_NONFINITE = 0, 1, 2, 3
 FH_GEN_DIRICHLET, FH_GEN_DLVP, FH_GEN_BOXSPLINE = 0, 1, 2
-FH_PREC_FP64, FH_PREC_FP32 = 0, 1
+FH_PREC_FP64, FH_PREC_FP32, FH_PREC_MIXED = 0, 1, 2
 FH_MAX_LOADS = 16
 FH_MAX_XI = 16
 
@@ -44,13 +44,14 @@ class fh_generator(C.Structure):
 
 class fh_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("precision", C.c_int),
-                ("init", C.c_int), ("chunk", C.c_int)]
+                ("init", C.c_int), ("chunk", C.c_int), ("path", C.c_int), ("cluster", C.c_int)]
 
 
 class fh_result(C.Structure):
     _fields_ = [("iterations", C.c_int * FH_MAX_LOADS), ("residual", C.c_double * FH_MAX_LOADS),
                 ("status", C.c_int * FH_MAX_LOADS), ("mean_stress", C.c_double * (FH_MAX_LOADS * 6)),
-                ("elapsed_ms", C.c_double), ("kernel_launches", C.c_longlong)]
+                ("elapsed_ms", C.c_double), ("kernel_launches", C.c_longlong), ("path", C.c_int),
+                ("cluster", C.c_int)]
 
 
 _lib = None
@@ -248,9 +249,11 @@ class Solver:
             C0 = np.ascontiguousarray(np.asarray(C0, dtype=np.float64))
             _check(library().fh_set_reference(self._h, _ptr(C0)))
 
-    def solve(self, eps0, tol=1e-8, max_iter=1000, precision=FH_PREC_FP64, init=0, chunk=0):
+    def solve(self, eps0, tol=1e-8, max_iter=1000, precision=FH_PREC_FP64, init=0, chunk=0, path=0, cluster=0):
+        """path: 0 automatic, 1 whole-GPU passes, 2 cluster-resident (2-axis grids)."""
         eps0 = np.ascontiguousarray(np.atleast_2d(np.asarray(eps0, dtype=np.float64)))
-        opts = fh_solve_opts(float(tol), int(max_iter), int(precision), int(init), int(chunk))
+        opts = fh_solve_opts(float(tol), int(max_iter), int(precision), int(init), int(chunk), int(path),
+                             int(cluster))
         res = fh_result()
         rc = library().fh_solve(self._h, eps0.shape[0], _ptr(eps0), C.byref(opts), C.byref(res))
         _check(rc, ok=(FH_OK, FH_NOT_CONVERGED, FH_DIVERGED, FH_NONFINITE))
@@ -263,6 +266,8 @@ class Solver:
             "mean_stress": np.array(res.mean_stress[: n * 6]).reshape(n, 6)[:, : self.nv],
             "elapsed_ms": res.elapsed_ms,
             "kernel_launches": res.kernel_launches,
+            "path": res.path,
+            "cluster": res.cluster,
         }
 
     def get_strain(self, load, out=None):

@@ -1,0 +1,319 @@
+// Cluster-resident Basic-Scheme solver for 2-axis Smith grids.
+//
+// One thread-block cluster owns one load case for the whole solve.  The
+// strain E, the half spectrum and the cluster's slice of the Gamma^p table
+// stay in the distributed shared memory of the cluster; only the final strain
+// goes back to global memory.  Each iteration of the paper's fixed point
+// (Eq. (pde_coefficients), Sec. 4) is:
+//
+//   column phase  CTA c gathers its half-spectrum columns [c0, c1) of every row
+//                 from the owning CTAs (DSMEM loads), FFT along axis 0, Green
+//                 step E^ = -Gamma^p tau^ (E^_0 = 0), inverse FFT, scatters
+//                 the columns back (DSMEM stores)
+//   cluster barrier
+//   row phase     CTA c, for its rows [r0, r1): inverse FFT along the
+//                 contiguous axis, E_new, FP64 residual partial sums (sent to
+//                 rank 0), tau = (C - C0):(E_new + eps0), forward FFT
+//   cluster barrier
+//   stop test     every CTA sums the CS partials in the same fixed order and
+//                 takes the same decision; rank 0 records r_n.
+//
+// Cluster barriers are hardware barriers (no spin loops); the iteration count
+// is bounded by max_iter.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "kernels.cuh"
+
+namespace fh {
+
+namespace cg = cooperative_groups;
+
+struct ClusterLayout {
+  // per-CTA shared-memory layout (byte offsets), identical in every CTA
+  int rows_max;   // max rows owned by one CTA
+  int cols_max;   // max half-spectrum columns owned by one CTA
+  int npair_max;  // complex lines of the row phase
+  size_t off_E, off_S, off_G, off_ph, off_tw0, off_tw1, off_dc, off_own, off_loc, off_work, off_part, total;
+};
+
+__host__ __device__ inline int split_lo(int n, int parts, int c) { return (int)(((long long)n * c) / parts); }
+
+template <typename T>
+__host__ __device__ inline ClusterLayout cluster_layout(int N0, int L, int nv, int CS) {
+  ClusterLayout c{};
+  const int H = L / 2 + 1;
+  c.rows_max = 0;
+  c.cols_max = 0;
+  for (int q = 0; q < CS; ++q) {
+    c.rows_max = max(c.rows_max, split_lo(N0, CS, q + 1) - split_lo(N0, CS, q));
+    c.cols_max = max(c.cols_max, split_lo(H, CS, q + 1) - split_lo(H, CS, q));
+  }
+  c.npair_max = (c.rows_max * nv + 1) / 2;
+  const size_t ntri = (size_t)nv * (nv + 1) / 2;
+  const size_t cs = sizeof(T) * 2;
+  auto align = [](size_t x) { return (x + 127) & ~(size_t)127; };
+  size_t o = 0;
+  c.off_E = o;    o = align(o + (size_t)c.rows_max * nv * L * sizeof(T));
+  c.off_S = o;    o = align(o + (size_t)c.rows_max * nv * H * cs);
+  c.off_G = o;    o = align(o + ntri * (size_t)N0 * c.cols_max * sizeof(T));
+  c.off_ph = o;   o = align(o + (size_t)c.rows_max * L);
+  c.off_tw0 = o;  o = align(o + (size_t)N0 * cs);
+  c.off_tw1 = o;  o = align(o + (size_t)L * cs);
+  c.off_dc = o;   o = align(o + (size_t)16 * nv * nv * sizeof(T));
+  c.off_own = o;  o = align(o + (size_t)N0);
+  c.off_loc = o;  o = align(o + (size_t)N0 * sizeof(short));
+  c.off_part = o; o = align(o + (size_t)CS * 2 * sizeof(double));
+  const size_t row_work = (size_t)2 * c.npair_max * L * cs;
+  const size_t col_work = (size_t)2 * nv * c.cols_max * N0 * cs;
+  c.off_work = o; o = align(o + (row_work > col_work ? row_work : col_work));
+  c.total = o;
+  return c;
+}
+
+template <typename T, int NV, int CS>
+__global__ void __launch_bounds__(256, 1)
+cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __restrict__ tw0g,
+                 const cplx<T>* __restrict__ tw1g, T* __restrict__ Eg, const uint8_t* __restrict__ phase,
+                 const T* __restrict__ dC, int nphase, const T* __restrict__ Gt, Control* ctl, LoadState* st,
+                 double* __restrict__ hist) {
+  constexpr int NTRI = NV * (NV + 1) / 2;
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ double red[32];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int load = blockIdx.x / CS;
+  const int N0 = g.dims[0], L = g.L, H = g.H;
+  const int m = (int)g.m;
+  const ClusterLayout lay = cluster_layout<T>(N0, L, NV, CS);
+  const int r0 = split_lo(N0, CS, rank), r1 = split_lo(N0, CS, rank + 1);
+  const int c0 = split_lo(H, CS, rank), c1 = split_lo(H, CS, rank + 1);
+  const int nrow = r1 - r0, ncol = c1 - c0;
+  T* El = reinterpret_cast<T*>(sm + lay.off_E);                  // [row*NV + comp][L]
+  cplx<T>* Sl = reinterpret_cast<cplx<T>*>(sm + lay.off_S);       // [row*NV + comp][H]
+  T* Gl = reinterpret_cast<T*>(sm + lay.off_G);                  // [tri][N0][ncol]
+  uint8_t* phl = sm + lay.off_ph;                                // [row][L]
+  cplx<T>* tw0 = reinterpret_cast<cplx<T>*>(sm + lay.off_tw0);
+  cplx<T>* tw1 = reinterpret_cast<cplx<T>*>(sm + lay.off_tw1);
+  T* dcs = reinterpret_cast<T*>(sm + lay.off_dc);
+  uint8_t* own = sm + lay.off_own;                                // owner rank of row n
+  short* loc = reinterpret_cast<short*>(sm + lay.off_loc);        // local row index in the owner
+  double* part = reinterpret_cast<double*>(sm + lay.off_part);    // [CS][2], used in rank 0
+  cplx<T>* W0 = reinterpret_cast<cplx<T>*>(sm + lay.off_work);
+  cplx<T>* W1 = reinterpret_cast<cplx<T>*>(sm + lay.off_work) + (size_t)lay.npair_max * L;
+  cplx<T>* X0 = W0;
+  cplx<T>* X1 = W0 + (size_t)NV * lay.cols_max * N0;
+  const size_t Ebase = (size_t)load * NV * g.m;
+  const FDiv fL = make_fdiv(L), fH = make_fdiv(H), fN0 = make_fdiv(N0), fnc = make_fdiv(ncol > 0 ? ncol : 1);
+
+  // ---- stage everything this CTA keeps for the whole solve
+  for (int i = threadIdx.x; i < N0; i += blockDim.x) tw0[i] = tw0g[i];
+  for (int i = threadIdx.x; i < L; i += blockDim.x) tw1[i] = tw1g[i];
+  for (int i = threadIdx.x; i < nphase * NV * NV; i += blockDim.x) dcs[i] = dC[i];
+  for (int q = 0; q < CS; ++q) {
+    const int a = split_lo(N0, CS, q), b = split_lo(N0, CS, q + 1);
+    for (int n = a + (int)threadIdx.x; n < b; n += blockDim.x) {
+      own[n] = (uint8_t)q;
+      loc[n] = (short)(n - a);
+    }
+  }
+  for (int i = threadIdx.x; i < nrow * L; i += blockDim.x) {
+    const int r = fdiv(i, fL), x = i - r * L;
+    const int gi = (r0 + r) * L + x;
+    phl[i] = phase[gi];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) El[(r * NV + c) * L + x] = Eg[Ebase + (size_t)c * m + gi];
+  }
+  for (int i = threadIdx.x; i < NTRI * N0 * ncol; i += blockDim.x) {
+    const int t2 = fdiv(i, fnc);
+    const int j = i - t2 * ncol;
+    const int t = fdiv(t2, fN0);
+    const int n = t2 - t * N0;
+    Gl[i] = Gt[(size_t)t * g.nhalf + (size_t)n * H + c0 + j];
+  }
+  T e0[NV];
+#pragma unroll
+  for (int c = 0; c < NV; ++c) e0[c] = (T)ctl->eps0[load][c];
+  LoadState s = st[load];
+  const double tol = ctl->tol;
+  const int max_iter = ctl->max_iter;
+  const T scale = (T)g.inv_m;
+  __syncthreads();
+
+  // ---- row phase: (optional inverse FFT + E update + residual) + stress + forward FFT
+  auto row_phase = [&](bool with_inverse, ResAcc<T>& acc_d, ResAcc<T>& acc_n) {
+    const int nreal = nrow * NV;
+    const int npair = (nreal + 1) >> 1;
+    cplx<T>* Z = W0;
+    cplx<T>* Zo = W1;
+    if (with_inverse) {
+      for (int idx = threadIdx.x; idx < npair * L; idx += blockDim.x) {
+        const int p = fdiv(idx, fL), k = idx - p * L;
+        const int fa = 2 * p, fb = 2 * p + 1;
+        const bool lo = k <= (L >> 1);
+        const int kk = lo ? k : L - k;
+        cplx<T> A = Sl[fa * H + kk];
+        cplx<T> B;
+        B.x = T(0); B.y = T(0);
+        if (fb < nreal) B = Sl[fb * H + kk];
+        if (!lo) { A.y = -A.y; B.y = -B.y; }
+        cplx<T> z;
+        z.x = A.x - B.y;
+        z.y = A.y + B.x;
+        W0[p * L + k] = z;
+      }
+      __syncthreads();
+      Z = fft_lines_pp<+1, T>(W0, W1, npair, L, plan1, tw1);
+      Zo = (Z == W0) ? W1 : W0;
+    }
+    for (int idx = threadIdx.x; idx < nrow * L; idx += blockDim.x) {
+      const int r = fdiv(idx, fL), x = idx - r * L;
+      T en[NV];
+#pragma unroll
+      for (int c = 0; c < NV; ++c) {
+        const int f = r * NV + c;
+        T* ep = &El[f * L + x];
+        if (with_inverse) {
+          const cplx<T> zz = Z[(f >> 1) * L + x];
+          en[c] = ((f & 1) ? zz.y : zz.x) * scale;
+          acc_d.add_sq(en[c] - *ep);
+          acc_n.add_sq(en[c] + e0[c]);
+          *ep = en[c];
+        } else {
+          en[c] = *ep;
+        }
+      }
+      const T* dc = dcs + phl[idx] * NV * NV;
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+        T t = T(0);
+#pragma unroll
+        for (int b = 0; b < NV; ++b) t += dc[a * NV + b] * (en[b] + e0[b]);
+        const int f = r * NV + a;
+        if (f & 1) Z[(f >> 1) * L + x].y = t;
+        else Z[(f >> 1) * L + x].x = t;
+      }
+    }
+    if (nreal & 1)
+      for (int x = threadIdx.x; x < L; x += blockDim.x) Z[(npair - 1) * L + x].y = T(0);
+    __syncthreads();
+    cplx<T>* Zf = fft_lines_pp<-1, T>(Z, Zo, npair, L, plan1, tw1);
+    for (int idx = threadIdx.x; idx < npair * H; idx += blockDim.x) {
+      const int p = fdiv(idx, fH), k = idx - p * H;
+      const cplx<T> zk = Zf[p * L + k];
+      const cplx<T> zm = Zf[p * L + (k == 0 ? 0 : L - k)];
+      cplx<T> A, B;
+      A.x = T(0.5) * (zk.x + zm.x);
+      A.y = T(0.5) * (zk.y - zm.y);
+      B.x = T(0.5) * (zk.y + zm.y);
+      B.y = T(-0.5) * (zk.x - zm.x);
+      Sl[(2 * p) * H + k] = A;
+      if (2 * p + 1 < nreal) Sl[(2 * p + 1) * H + k] = B;
+    }
+  };
+
+  // ---- column phase: gather columns over DSMEM, FFT, Green, inverse FFT, scatter
+  auto col_phase = [&]() {
+    const int nl = NV * ncol;
+    for (int idx = threadIdx.x; idx < NV * N0 * ncol; idx += blockDim.x) {
+      const int t = fdiv(idx, fnc);
+      const int j = idx - t * ncol;
+      const int c = fdiv(t, fN0);
+      const int n = t - c * N0;
+      const cplx<T>* rem = cluster.map_shared_rank(Sl, (int)own[n]);
+      X0[(c * ncol + j) * N0 + n] = rem[((int)loc[n] * NV + c) * H + c0 + j];
+    }
+    __syncthreads();
+    cplx<T>* Xf = fft_lines_pp<-1, T>(X0, X1, nl, N0, plan0, tw0);
+    for (int idx = threadIdx.x; idx < N0 * ncol; idx += blockDim.x) {
+      const int n = fdiv(idx, fnc);
+      const int j = idx - n * ncol;
+      cplx<T> tv[NV];
+#pragma unroll
+      for (int c = 0; c < NV; ++c) tv[c] = Xf[(c * ncol + j) * N0 + n];
+      const bool zero = (n == 0 && c0 + j == 0);
+      T gm[NTRI];
+#pragma unroll
+      for (int t = 0; t < NTRI; ++t) gm[t] = Gl[(t * N0 + n) * ncol + j];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+        T re = T(0), im = T(0);
+#pragma unroll
+        for (int b = 0; b < NV; ++b) {
+          const int lo = a < b ? a : b, hi = a < b ? b : a;
+          const T gv = gm[lo * NV - (lo * (lo - 1)) / 2 + (hi - lo)];
+          re -= gv * tv[b].x;
+          im -= gv * tv[b].y;
+        }
+        cplx<T> e;
+        e.x = zero ? T(0) : re;
+        e.y = zero ? T(0) : im;
+        Xf[(a * ncol + j) * N0 + n] = e;
+      }
+    }
+    __syncthreads();
+    cplx<T>* Xi = fft_lines_pp<+1, T>(Xf, Xf == X0 ? X1 : X0, nl, N0, plan0, tw0);
+    for (int idx = threadIdx.x; idx < NV * N0 * ncol; idx += blockDim.x) {
+      const int t = fdiv(idx, fnc);
+      const int j = idx - t * ncol;
+      const int c = fdiv(t, fN0);
+      const int n = t - c * N0;
+      cplx<T>* rem = cluster.map_shared_rank(Sl, (int)own[n]);
+      rem[((int)loc[n] * NV + c) * H + c0 + j] = Xi[(c * ncol + j) * N0 + n];
+    }
+  };
+
+  // ---- initial stress and forward transform of the rows
+  {
+    ResAcc<T> a, b;
+    row_phase(false, a, b);
+  }
+  cluster.sync();
+  double* part0 = cluster.map_shared_rank(part, 0);
+  for (int it = 0; it < max_iter && !s.done; ++it) {
+    col_phase();
+    cluster.sync();
+    ResAcc<T> acc_d, acc_n;
+    row_phase(true, acc_d, acc_n);
+    const double d2 = block_sum(acc_d.value(), red);
+    const double n2 = block_sum(acc_n.value(), red);
+    if (threadIdx.x == 0) {
+      part0[2 * rank] = d2;
+      part0[2 * rank + 1] = n2;
+    }
+    cluster.sync();
+    // every CTA sums the partials in the same order and takes the same decision
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < CS; ++q) {
+      a += part0[2 * q];
+      b += part0[2 * q + 1];
+    }
+    if (rank == 0 && threadIdx.x == 0) {
+      LoadState t = s;
+      advance_state(t, ctl, hist, load, a, b);
+    }
+    {
+      // the same state update as advance_state, without the history write
+      const double r = (b > 0.0) ? sqrt(a / b) : sqrt(a);
+      s.iter += 1;
+      if (s.iter == 1) s.r_first = r;
+      s.inc = (s.iter > 1 && r > s.r) ? s.inc + 1 : 0;
+      s.r = r;
+      if (!isfinite(r)) { s.status = FH_NONFINITE; s.done = 1; }
+      else if (r <= tol) { s.status = FH_OK; s.done = 1; }
+      else if (s.inc >= 100 || (s.iter > 10 && r > 1e6 * s.r_first && r > 1.0)) { s.status = FH_DIVERGED; s.done = 1; }
+      else if (s.iter >= max_iter) { s.status = FH_NOT_CONVERGED; s.done = 1; }
+    }
+  }
+  // ---- results
+  for (int i = threadIdx.x; i < nrow * L; i += blockDim.x) {
+    const int r = fdiv(i, fL), x = i - r * L;
+#pragma unroll
+    for (int c = 0; c < NV; ++c) Eg[Ebase + (size_t)c * m + (r0 + r) * L + x] = El[(r * NV + c) * L + x];
+  }
+  if (rank == 0 && threadIdx.x == 0) st[load] = s;
+  cluster.sync();  // keep every CTA's shared memory alive until remote accesses are done
+}
+
+}  // namespace fh

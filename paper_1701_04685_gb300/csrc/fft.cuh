@@ -155,6 +155,21 @@ __device__ __forceinline__ void dft_small(cplx<T>* v, const cplx<T>* __restrict_
   else dft_direct<R, DIR, T>(v, tw, L);
 }
 
+// Integer division by a runtime divisor through a float reciprocal: exact for
+// 0 <= n < 2^22 (the product is off by at most one and corrected).
+struct FDiv {
+  int d;
+  float inv;
+};
+__host__ __device__ inline FDiv make_fdiv(int d) { FDiv f; f.d = d; f.inv = 1.0f / (float)d; return f; }
+__device__ __forceinline__ int fdiv(int n, FDiv f) {
+  int q = (int)((float)n * f.inv);
+  const int r = n - q * f.d;
+  if (r < 0) --q;
+  else if (r >= f.d) ++q;
+  return q;
+}
+
 // One Stockham stage of radix R: sub-transforms of size Ns are combined into
 // size Ns*R.  Butterfly j reads in[j + t*L/R] (t < R), applies the twiddles
 // w^{t k}, k = j mod Ns, w = exp(DIR 2 pi i / (Ns R)), does a length-R DFT and
@@ -165,12 +180,14 @@ __device__ __forceinline__ void stockham_stage(const cplx<T>* in, cplx<T>* out, 
   const int nb = L / R;
   const int stride = L / (Ns * R);
   const int total = nlines * nb;
+  const FDiv fnb = make_fdiv(nb), fns = make_fdiv(Ns);
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int line = idx / nb;
+    const int line = fdiv(idx, fnb);
     const int j = idx - line * nb;
     const cplx<T>* li = in + line * ls;
     cplx<T>* lo = out + line * ls;
-    const int k = j % Ns;
+    const int jq = fdiv(j, fns);
+    const int k = j - jq * Ns;
     cplx<T> v[R];
 #pragma unroll
     for (int t = 0; t < R; ++t) v[t] = li[j + t * nb];
@@ -183,19 +200,19 @@ __device__ __forceinline__ void stockham_stage(const cplx<T>* in, cplx<T>* out, 
       }
     }
     dft_small<R, DIR, T>(v, tw, L);
-    const int base = (j / Ns) * Ns * R + k;
+    const int base = jq * Ns * R + k;
 #pragma unroll
     for (int t = 0; t < R; ++t) lo[base + t * Ns] = v[t];
   }
 }
 
-// Transform `nlines` lines of length plan.L in place in shared memory.
-// Line q occupies buf[q*ls .. q*ls + L); tmp has the same shape (ping-pong
-// buffer).  Every thread of the block must call this.  On return the result
-// is in buf.
+// Transform `nlines` lines of length plan.L held in shared memory.  Line q
+// occupies buf[q*ls .. q*ls + L); tmp has the same shape (ping-pong buffer).
+// Every thread of the block must call this.  Returns the buffer (buf or tmp)
+// that holds the result; a __syncthreads() has been executed on return.
 template <int DIR, typename T>
-__device__ void fft_lines(cplx<T>* buf, cplx<T>* tmp, int nlines, int ls, const DevPlan& plan,
-                          const cplx<T>* __restrict__ tw) {
+__device__ cplx<T>* fft_lines_pp(cplx<T>* buf, cplx<T>* tmp, int nlines, int ls, const DevPlan& plan,
+                                 const cplx<T>* __restrict__ tw) {
   const int L = plan.L;
   cplx<T>* in = buf;
   cplx<T>* out = tmp;
@@ -216,10 +233,20 @@ __device__ void fft_lines(cplx<T>* buf, cplx<T>* tmp, int nlines, int ls, const 
     cplx<T>* sw = in; in = out; out = sw;
     Ns *= r;
   }
+  return in;
+}
+
+// As fft_lines_pp, with the result copied back into buf when it ended in tmp.
+template <int DIR, typename T>
+__device__ void fft_lines(cplx<T>* buf, cplx<T>* tmp, int nlines, int ls, const DevPlan& plan,
+                          const cplx<T>* __restrict__ tw) {
+  cplx<T>* in = fft_lines_pp<DIR, T>(buf, tmp, nlines, ls, plan, tw);
   if (in != buf) {
+    const int L = plan.L;
     const int total = nlines * L;
+    const FDiv fl = make_fdiv(L);
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-      const int line = idx / L;
+      const int line = fdiv(idx, fl);
       const int x = idx - line * L;
       buf[line * ls + x] = in[line * ls + x];
     }

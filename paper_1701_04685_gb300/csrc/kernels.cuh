@@ -80,6 +80,33 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;
 }
 
+// Per-thread accumulator of the Cauchy-residual sums.  FP64 kernels add in
+// double.  FP32 kernels keep a double-float pair (hi, lo) built with the exact
+// TwoSum / TwoProduct transformations (Knuth; Dekker), which carries about 48
+// significant bits while using only FP32 instructions: GB300's FP64 pipe is
+// narrow enough that per-point double arithmetic would dominate an FP32
+// iteration.  The pair is rounded to double once per thread, before the FP64
+// block reduction.
+template <typename T> struct ResAcc;
+template <> struct ResAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add_sq(double a) { s = fma(a, a, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct ResAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add_sq(float a) {
+    const float p = a * a;
+    const float e = fmaf(a, a, -p);        // a*a = p + e exactly
+    const float s = hi + p;                 // TwoSum(hi, p)
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (p - bp);
+    hi = s;
+    lo += err + e;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // Advance the per-load state after one iteration's residual is known.
 __device__ void advance_state(LoadState& s, Control* ctl, double* hist, int load, double d2, double n2) {
   const double r = (n2 > 0.0) ? sqrt(d2 / n2) : sqrt(d2);
@@ -98,7 +125,7 @@ __device__ void advance_state(LoadState& s, Control* ctl, double* hist, int load
 // row pass along the contiguous axis (length L), fused with the pointwise
 // constitutive stage and the residual.
 // ---------------------------------------------------------------------------
-template <typename T, bool FIRST>
+template <typename T, int NV, bool FIRST>
 __global__ void __launch_bounds__(256) row_pass(GridInfo g, DevPlan plan, const cplx<T>* __restrict__ tw,
                                                 T* __restrict__ E, cplx<T>* __restrict__ S,
                                                 const uint8_t* __restrict__ phase, const T* __restrict__ dC,
@@ -111,106 +138,113 @@ __global__ void __launch_bounds__(256) row_pass(GridInfo g, DevPlan plan, const 
   const int rb = blockIdx.x - load * blocks_per_load;
   const long long row0 = (long long)rb * rpb;
   const int nrow = (int)min((long long)rpb, g.nrows - row0);
-  const int L = g.L, H = g.H, nv = g.nv;
-  const int nreal = nrow * nv;
+  const int L = g.L, H = g.H;
+  const int nreal = nrow * NV;
   const int npair = (nreal + 1) >> 1;
-  cplx<T>* Z = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* tmp = Z + (size_t)((rpb * nv + 1) >> 1) * L;
+  cplx<T>* W0 = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* W1 = W0 + (size_t)((rpb * NV + 1) >> 1) * L;
+  const FDiv fL = make_fdiv(L), fH = make_fdiv(H);
 
   if (threadIdx.x == 0) s_skip = st[load].done;
   __syncthreads();
-  double d2 = 0.0, n2 = 0.0;
+  ResAcc<T> acc_d, acc_n;
   if (!s_skip) {
-    T e0[MAXV];
-    for (int c = 0; c < nv; ++c) e0[c] = (T)ctl->eps0[load][c];
-    const size_t Ebase = (size_t)load * nv * g.m;
-    const size_t Sbase = (size_t)load * nv * g.nrows * H;
+    T e0[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) e0[c] = (T)ctl->eps0[load][c];
+    T* Eb = E + (size_t)load * NV * g.m + row0 * L;              // row0 of component 0
+    const cplx<T>* Sr = S + ((size_t)load * NV * g.nrows + row0) * H;  // row0 of component 0
+    cplx<T>* Sw = S + ((size_t)load * NV * g.nrows + row0) * H;
+    const size_t cstrE = (size_t)g.m, cstrS = (size_t)g.nrows * H;
+    cplx<T>* Z = W0;
+    cplx<T>* Zo = W1;
     if (!FIRST) {
       // 1. rebuild the two-real-lines-in-one complex spectrum Z = A + i B
       for (int idx = threadIdx.x; idx < npair * L; idx += blockDim.x) {
-        const int p = idx / L, k = idx - p * L;
+        const int p = fdiv(idx, fL), k = idx - p * L;
         const int fa = 2 * p, fb = 2 * p + 1;
-        const int kk = k <= L / 2 ? k : L - k;
-        const T sg = k <= L / 2 ? T(1) : T(-1);  // conjugate for k > L/2
-        const int ra = fa / nv, ca = fa - ra * nv;
-        cplx<T> A = S[Sbase + ((size_t)ca * g.nrows + row0 + ra) * H + kk];
+        const bool lo = k <= (L >> 1);
+        const int kk = lo ? k : L - k;
+        const int ra = fa / NV, ca = fa - ra * NV;
+        cplx<T> A = Sr[ca * cstrS + ra * H + kk];
         cplx<T> B;
         B.x = T(0); B.y = T(0);
         if (fb < nreal) {
-          const int rbb = fb / nv, cb = fb - rbb * nv;
-          B = S[Sbase + ((size_t)cb * g.nrows + row0 + rbb) * H + kk];
+          const int rbb = fb / NV, cb = fb - rbb * NV;
+          B = Sr[cb * cstrS + rbb * H + kk];
         }
-        A.y *= sg;
-        B.y *= sg;
+        if (!lo) { A.y = -A.y; B.y = -B.y; }
         cplx<T> z;
         z.x = A.x - B.y;
         z.y = A.y + B.x;
-        Z[(size_t)p * L + k] = z;
+        W0[p * L + k] = z;
       }
       __syncthreads();
       // 2. inverse FFT (unnormalised)
-      fft_lines<+1, T>(Z, tmp, npair, L, plan, tw);
+      Z = fft_lines_pp<+1, T>(W0, W1, npair, L, plan, tw);
+      Zo = (Z == W0) ? W1 : W0;
     }
     // 3. pointwise: E_new, residual sums, tau = (C - C0):(E_new + eps0)
     const T scale = (T)g.inv_m;
     for (int idx = threadIdx.x; idx < nrow * L; idx += blockDim.x) {
-      const int r = idx / L, x = idx - r * L;
-      const size_t gi = (size_t)(row0 + r) * L + x;
-      T en[MAXV];
-      for (int c = 0; c < nv; ++c) {
-        const int f = r * nv + c;
+      const int r = fdiv(idx, fL), x = idx - r * L;
+      T* ep = Eb + r * L + x;
+      T en[NV];
+#pragma unroll
+      for (int c = 0; c < NV; ++c) {
+        const int f = r * NV + c;
         if (FIRST) {
-          en[c] = E[Ebase + (size_t)c * g.m + gi];
+          en[c] = ep[c * cstrE];
         } else {
-          const cplx<T> zz = Z[(size_t)(f >> 1) * L + x];
+          const cplx<T> zz = Z[(f >> 1) * L + x];
           en[c] = ((f & 1) ? zz.y : zz.x) * scale;
-          const T eo = E[Ebase + (size_t)c * g.m + gi];
-          const double df = (double)en[c] - (double)eo;
-          const double tf = (double)en[c] + (double)e0[c];
-          d2 += df * df;
-          n2 += tf * tf;
-          E[Ebase + (size_t)c * g.m + gi] = en[c];
+          const T eo = ep[c * cstrE];
+          acc_d.add_sq(en[c] - eo);
+          acc_n.add_sq(en[c] + e0[c]);
+          ep[c * cstrE] = en[c];
         }
       }
-      const T* dc = dC + (size_t)phase[gi] * nv * nv;
-      for (int a = 0; a < nv; ++a) {
+      const T* dc = dC + (size_t)phase[(row0 + r) * L + x] * NV * NV;
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
         T t = T(0);
-        for (int b = 0; b < nv; ++b) t += dc[a * nv + b] * (en[b] + e0[b]);
-        const int f = r * nv + a;
-        if (f & 1) Z[(size_t)(f >> 1) * L + x].y = t;
-        else Z[(size_t)(f >> 1) * L + x].x = t;
+#pragma unroll
+        for (int b = 0; b < NV; ++b) t += dc[a * NV + b] * (en[b] + e0[b]);
+        const int f = r * NV + a;
+        if (f & 1) Z[(f >> 1) * L + x].y = t;
+        else Z[(f >> 1) * L + x].x = t;
       }
     }
     // odd number of real lines: the last pair's imaginary part is zero
     if (nreal & 1) {
-      for (int x = threadIdx.x; x < L; x += blockDim.x) Z[(size_t)(npair - 1) * L + x].y = T(0);
+      for (int x = threadIdx.x; x < L; x += blockDim.x) Z[(npair - 1) * L + x].y = T(0);
     }
     __syncthreads();
     // 4. forward FFT
-    fft_lines<-1, T>(Z, tmp, npair, L, plan, tw);
+    cplx<T>* Zf = fft_lines_pp<-1, T>(Z, Zo, npair, L, plan, tw);
     // 5. split into the two half spectra A = (Z_k + conj Z_{L-k})/2, B = (Z_k - conj Z_{L-k})/(2i)
     for (int idx = threadIdx.x; idx < npair * H; idx += blockDim.x) {
-      const int p = idx / H, k = idx - p * H;
-      const cplx<T> zk = Z[(size_t)p * L + k];
-      const cplx<T> zm = Z[(size_t)p * L + (k == 0 ? 0 : L - k)];
+      const int p = fdiv(idx, fH), k = idx - p * H;
+      const cplx<T> zk = Zf[p * L + k];
+      const cplx<T> zm = Zf[p * L + (k == 0 ? 0 : L - k)];
       cplx<T> A, B;
       A.x = T(0.5) * (zk.x + zm.x);
       A.y = T(0.5) * (zk.y - zm.y);
       B.x = T(0.5) * (zk.y + zm.y);
       B.y = T(-0.5) * (zk.x - zm.x);
       const int fa = 2 * p, fb = 2 * p + 1;
-      const int ra = fa / nv, ca = fa - ra * nv;
-      S[Sbase + ((size_t)ca * g.nrows + row0 + ra) * H + k] = A;
+      const int ra = fa / NV, ca = fa - ra * NV;
+      Sw[ca * cstrS + ra * H + k] = A;
       if (fb < nreal) {
-        const int rbb = fb / nv, cb = fb - rbb * nv;
-        S[Sbase + ((size_t)cb * g.nrows + row0 + rbb) * H + k] = B;
+        const int rbb = fb / NV, cb = fb - rbb * NV;
+        Sw[cb * cstrS + rbb * H + k] = B;
       }
     }
   }
   if (FIRST) return;
   // 6. partial sums of this block
-  d2 = block_sum(d2, red);
-  n2 = block_sum(n2, red);
+  const double d2 = block_sum(acc_d.value(), red);
+  const double n2 = block_sum(acc_n.value(), red);
   __shared__ unsigned int s_ticket;
   if (threadIdx.x == 0) {
     partials[2 * (size_t)blockIdx.x] = d2;
@@ -245,13 +279,15 @@ __global__ void __launch_bounds__(256) row_pass(GridInfo g, DevPlan plan, const 
 // ---------------------------------------------------------------------------
 // line pass along a non-contiguous axis `ax` of the half spectrum.
 // MODE 0: forward FFT; MODE 1: inverse FFT; MODE 2 (ax = 0 only): forward,
-// Green step, inverse.
+// Green step, inverse.  Lines sit in shared memory with stride N + 1 (odd,
+// against bank conflicts).
 // ---------------------------------------------------------------------------
-template <typename T, int MODE>
+template <typename T, int NV, int MODE>
 __global__ void __launch_bounds__(256) line_pass(GridInfo g, DevPlan plan, const cplx<T>* __restrict__ tw,
                                                  cplx<T>* __restrict__ S, const T* __restrict__ Gt,
                                                  const LoadState* st, int ax, int W, int ntiles,
                                                  int n_outer, int n_inner) {
+  constexpr int NTRI = NV * (NV + 1) / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int b = blockIdx.x;
   const int tile = b % ntiles; b /= ntiles;
@@ -260,67 +296,72 @@ __global__ void __launch_bounds__(256) line_pass(GridInfo g, DevPlan plan, const
   const int load = b;
   if (st[load].done) return;
   const int N = g.dims[ax];
-  const int nv = g.nv, H = g.H;
+  const int ls = N + 1;
+  const int H = g.H;
   // element stride of axis ax inside one component's half spectrum
   long long stride = H;
   for (int k = ax + 1; k < g.nd - 1; ++k) stride *= g.dims[k];
   const long long base = (long long)outer * N * stride + (long long)inner * H;
   const int w0 = tile * W;
-  const int nl = nv * W;
-  cplx<T>* X = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* tmp = X + (size_t)nl * N;
+  const int nl = NV * W;
+  cplx<T>* X0 = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* X1 = X0 + (size_t)nl * ls;
   const size_t comp_stride = (size_t)g.nhalf;
-  const size_t Sbase = (size_t)load * nv * comp_stride;
+  cplx<T>* Sb = S + (size_t)load * NV * comp_stride + base + w0;
+  const FDiv fW = make_fdiv(W), fN = make_fdiv(N);
+  const int wlim = min(W, H - w0);
 
-  for (int idx = threadIdx.x; idx < nv * N * W; idx += blockDim.x) {
-    const int w = idx % W;
-    const int t = idx / W;
-    const int n = t % N;
-    const int c = t / N;
+  for (int idx = threadIdx.x; idx < NV * N * W; idx += blockDim.x) {
+    const int t = fdiv(idx, fW);
+    const int w = idx - t * W;
+    const int c = fdiv(t, fN);
+    const int n = t - c * N;
     cplx<T> v;
     v.x = T(0); v.y = T(0);
-    if (w0 + w < H) v = S[Sbase + c * comp_stride + base + n * stride + w0 + w];
-    X[(size_t)(c * W + w) * N + n] = v;
+    if (w < wlim) v = Sb[c * comp_stride + n * stride + w];
+    X0[(c * W + w) * ls + n] = v;
   }
   __syncthreads();
-  if (MODE == 0 || MODE == 2) fft_lines<-1, T>(X, tmp, nl, N, plan, tw);
+  cplx<T>* X = X0;
+  if (MODE == 0 || MODE == 2) X = fft_lines_pp<-1, T>(X0, X1, nl, ls, plan, tw);
   if (MODE == 2) {
     // Green step at frequency (l_0 = n, inner axes, l_last = w0 + w)
     for (int idx = threadIdx.x; idx < N * W; idx += blockDim.x) {
-      const int w = idx % W;
-      const int n = idx / W;
-      if (w0 + w >= H) continue;
+      const int n = fdiv(idx, fW);
+      const int w = idx - n * W;
+      if (w >= wlim) continue;
       const long long f = (long long)n * stride + (long long)inner * H + w0 + w;
-      cplx<T> tv[MAXV], ev[MAXV];
-      for (int c = 0; c < nv; ++c) tv[c] = X[(size_t)(c * W + w) * N + n];
-      T Gm[MAXV][MAXV];
-      int t = 0;
-      for (int a = 0; a < nv; ++a)
-        for (int bb = a; bb < nv; ++bb) {
-          const T v = Gt[(size_t)t * g.nhalf + f];
-          Gm[a][bb] = v;
-          Gm[bb][a] = v;
-          ++t;
-        }
-      for (int a = 0; a < nv; ++a) {
+      cplx<T> tv[NV];
+#pragma unroll
+      for (int c = 0; c < NV; ++c) tv[c] = X[(c * W + w) * ls + n];
+      T gm[NTRI];
+#pragma unroll
+      for (int t = 0; t < NTRI; ++t) gm[t] = Gt[(size_t)t * g.nhalf + f];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
         T re = T(0), im = T(0);
-        for (int bb = 0; bb < nv; ++bb) { re -= Gm[a][bb] * tv[bb].x; im -= Gm[a][bb] * tv[bb].y; }
-        ev[a].x = re;
-        ev[a].y = im;
+#pragma unroll
+        for (int bb = 0; bb < NV; ++bb) {
+          const int lo = a < bb ? a : bb, hi = a < bb ? bb : a;
+          const T gv = gm[lo * NV - (lo * (lo - 1)) / 2 + (hi - lo)];
+          re -= gv * tv[bb].x;
+          im -= gv * tv[bb].y;
+        }
+        cplx<T> e;
+        e.x = (f == 0) ? T(0) : re;
+        e.y = (f == 0) ? T(0) : im;
+        X[(a * W + w) * ls + n] = e;
       }
-      if (f == 0)
-        for (int a = 0; a < nv; ++a) { ev[a].x = T(0); ev[a].y = T(0); }
-      for (int c = 0; c < nv; ++c) X[(size_t)(c * W + w) * N + n] = ev[c];
     }
     __syncthreads();
   }
-  if (MODE == 1 || MODE == 2) fft_lines<+1, T>(X, tmp, nl, N, plan, tw);
-  for (int idx = threadIdx.x; idx < nv * N * W; idx += blockDim.x) {
-    const int w = idx % W;
-    const int t = idx / W;
-    const int n = t % N;
-    const int c = t / N;
-    if (w0 + w < H) S[Sbase + c * comp_stride + base + n * stride + w0 + w] = X[(size_t)(c * W + w) * N + n];
+  if (MODE == 1 || MODE == 2) X = fft_lines_pp<+1, T>(X, X == X0 ? X1 : X0, nl, ls, plan, tw);
+  for (int idx = threadIdx.x; idx < NV * N * W; idx += blockDim.x) {
+    const int t = fdiv(idx, fW);
+    const int w = idx - t * W;
+    const int c = fdiv(t, fN);
+    const int n = t - c * N;
+    if (w < wlim) Sb[c * comp_stride + n * stride + w] = X[(c * W + w) * ls + n];
   }
 }
 

@@ -17,6 +17,7 @@
 
 #include "internal.hpp"
 #include "kernels.cuh"
+#include "cluster.cuh"
 
 namespace fh {
 static thread_local std::string g_err;
@@ -129,7 +130,7 @@ void choose_shapes(fh_solver* s, int prec) {
     for (int k = 0; k + 1 < g.nd; ++k)
       if (k != a) others *= g.dims[k];
     int W = 16;
-    auto smem = [&](int w) { return (size_t)2 * g.nv * w * N * csize(prec); };
+    auto smem = [&](int w) { return (size_t)2 * g.nv * w * (N + 1) * csize(prec); };
     auto blocks = [&](int w) { return (long long)nl * others * ((g.H + w - 1) / w); };
     const int wmin = prec == FH_PREC_FP64 ? 2 : 4;
     while (W > wmin && (smem(W) > 96 * 1024 || blocks(W) < 2 * sms)) W /= 2;
@@ -168,6 +169,26 @@ const double* Gptr<double>(fh_solver* s) { return s->G64; }
 template <>
 const float* Gptr<float>(fh_solver* s) { return s->G32; }
 
+template <typename T, int NV>
+void launch_line_nv(fh_solver* s, int prec, int a, int mode, unsigned blocks, int n_outer, int n_inner) {
+  using C = typename fh::cplx_t<T>::type;
+  C* S = reinterpret_cast<C*>(s->S);
+  const size_t sm = s->line_smem[prec][a];
+  const int W = s->lineW[prec][a], nt = s->ntiles[prec][a];
+  if (mode == 0)
+    fh::line_pass<T, NV, 0><<<blocks, kThreads, sm, s->work>>>(s->g, s->ax[a].plan, twp<T>(s->ax[a]), S, Gptr<T>(s), s->st, a, W, nt, n_outer, n_inner);
+  else if (mode == 1)
+    fh::line_pass<T, NV, 1><<<blocks, kThreads, sm, s->work>>>(s->g, s->ax[a].plan, twp<T>(s->ax[a]), S, Gptr<T>(s), s->st, a, W, nt, n_outer, n_inner);
+  else
+    fh::line_pass<T, NV, 2><<<blocks, kThreads, sm, s->work>>>(s->g, s->ax[a].plan, twp<T>(s->ax[a]), S, Gptr<T>(s), s->st, a, W, nt, n_outer, n_inner);
+}
+
+template <typename T>
+void launch_line(fh_solver* s, int prec, int a, int mode, unsigned blocks, int n_outer, int n_inner) {
+  if (s->g.nv == 3) launch_line_nv<T, 3>(s, prec, a, mode, blocks, n_outer, n_inner);
+  else launch_line_nv<T, 6>(s, prec, a, mode, blocks, n_outer, n_inner);
+}
+
 // Enqueue the line passes of one iteration (everything between two row passes).
 template <typename T>
 void enqueue_line_passes(fh_solver* s, int prec, int nload) {
@@ -185,16 +206,7 @@ void enqueue_line_passes(fh_solver* s, int prec, int nload) {
     for (int k = 0; k < a; ++k) n_outer *= g.dims[k];
     for (int k = a + 1; k + 1 < g.nd; ++k) n_inner *= g.dims[k];
     const long long blocks = (long long)nload * n_outer * n_inner * s->ntiles[prec][a];
-    const size_t sm = s->line_smem[prec][a];
-    if (mode == 0)
-      fh::line_pass<T, 0><<<(unsigned)blocks, kThreads, sm, s->work>>>(g, s->ax[a].plan, twp<T>(s->ax[a]), S, Gptr<T>(s), s->st, a,
-                                                                       s->lineW[prec][a], s->ntiles[prec][a], (int)n_outer, (int)n_inner);
-    else if (mode == 1)
-      fh::line_pass<T, 1><<<(unsigned)blocks, kThreads, sm, s->work>>>(g, s->ax[a].plan, twp<T>(s->ax[a]), S, Gptr<T>(s), s->st, a,
-                                                                       s->lineW[prec][a], s->ntiles[prec][a], (int)n_outer, (int)n_inner);
-    else
-      fh::line_pass<T, 2><<<(unsigned)blocks, kThreads, sm, s->work>>>(g, s->ax[a].plan, twp<T>(s->ax[a]), S, Gptr<T>(s), s->st, a,
-                                                                       s->lineW[prec][a], s->ntiles[prec][a], (int)n_outer, (int)n_inner);
+    launch_line<T>(s, prec, a, mode, (unsigned)blocks, (int)n_outer, (int)n_inner);
   };
   // forward along axes nd-2 .. 1, then axis 0 with the Green step, then inverse 1 .. nd-2
   for (int a = g.nd - 2; a >= 1; --a) launch(a, 0);
@@ -202,26 +214,32 @@ void enqueue_line_passes(fh_solver* s, int prec, int nload) {
   for (int a = 1; a <= g.nd - 2; ++a) launch(a, 1);
 }
 
-template <typename T, bool FIRST>
-void enqueue_row_pass(fh_solver* s, int prec, int nload) {
+template <typename T, int NV, bool FIRST>
+void enqueue_row_pass_nv(fh_solver* s, int prec, int nload) {
   const GridInfo& g = s->g;
   using C = typename fh::cplx_t<T>::type;
   const int last = g.nd - 1;
   const int blocks = nload * s->row_bpl[prec];
-  fh::row_pass<T, FIRST><<<blocks, kThreads, s->row_smem[prec], s->work>>>(
-      g, s->ax[last].plan, twp<T>(s->ax[last]), Eptr<T>(s), reinterpret_cast<C*>(s->S), s->phase, dCptr<T>(s), s->ctl, s->st,
-      s->partials, s->hist, s->rpb[prec], s->row_bpl[prec]);
+  fh::row_pass<T, NV, FIRST><<<blocks, kThreads, s->row_smem[prec], s->work>>>(
+      g, s->ax[last].plan, twp<T>(s->ax[last]), Eptr<T>(s), reinterpret_cast<C*>(s->S), s->phase, dCptr<T>(s), s->ctl,
+      s->st, s->partials, s->hist, s->rpb[prec], s->row_bpl[prec]);
 }
 
-template <typename T>
-fh_status set_smem_attrs(fh_solver* s, int prec) {
+template <typename T, bool FIRST>
+void enqueue_row_pass(fh_solver* s, int prec, int nload) {
+  if (s->g.nv == 3) enqueue_row_pass_nv<T, 3, FIRST>(s, prec, nload);
+  else enqueue_row_pass_nv<T, 6, FIRST>(s, prec, nload);
+}
+
+template <typename T, int NV>
+fh_status set_smem_attrs_nv(fh_solver* s, int prec) {
   const size_t rs = s->row_smem[prec];
   if (rs > kMaxSmem) {
     fh::set_error("contiguous axis too long for this precision (shared memory)");
     return FH_ERR_UNSUPPORTED;
   }
-  CK(cudaFuncSetAttribute(fh::row_pass<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
-  CK(cudaFuncSetAttribute(fh::row_pass<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
+  CK(cudaFuncSetAttribute(fh::row_pass<T, NV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
+  CK(cudaFuncSetAttribute(fh::row_pass<T, NV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
   size_t lm = 0;
   for (int a = 0; a + 1 < s->g.nd; ++a) lm = std::max(lm, s->line_smem[prec][a]);
   if (lm > kMaxSmem) {
@@ -229,11 +247,16 @@ fh_status set_smem_attrs(fh_solver* s, int prec) {
     return FH_ERR_UNSUPPORTED;
   }
   if (lm > 0) {
-    CK(cudaFuncSetAttribute(fh::line_pass<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lm));
-    CK(cudaFuncSetAttribute(fh::line_pass<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lm));
-    CK(cudaFuncSetAttribute(fh::line_pass<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lm));
+    CK(cudaFuncSetAttribute(fh::line_pass<T, NV, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lm));
+    CK(cudaFuncSetAttribute(fh::line_pass<T, NV, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lm));
+    CK(cudaFuncSetAttribute(fh::line_pass<T, NV, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lm));
   }
   return FH_OK;
+}
+
+template <typename T>
+fh_status set_smem_attrs(fh_solver* s, int prec) {
+  return s->g.nv == 3 ? set_smem_attrs_nv<T, 3>(s, prec) : set_smem_attrs_nv<T, 6>(s, prec);
 }
 
 template <typename T>
@@ -292,6 +315,109 @@ fh_status run_solve(fh_solver* s, int prec, int nload, int chunk, int max_iter, 
   CK(cudaGetLastError());
   CK(cudaEventRecord(s->ev1, s->work));
   *launches = 2 + launched * (1 + line_launches_per_iter(s->g));
+  return FH_OK;
+}
+
+// Cluster-resident path (2-axis grids): one cluster of CS CTAs per load case.
+template <typename T, int NV, int CS>
+fh_status cluster_fits_nv(fh_solver* s, bool* ok) {
+  *ok = false;
+  const GridInfo& g = s->g;
+  if (g.nd != 2) return FH_OK;
+  const fh::ClusterLayout lay = fh::cluster_layout<T>(g.dims[0], g.L, g.nv, CS);
+  if (lay.total + 1024 > kMaxSmem) return FH_OK;
+  auto kern = fh::cluster_solve_2d<T, NV, CS>;
+  CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total));
+  if (CS > 8) CK(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CS);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = lay.total;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return FH_OK;
+  }
+  *ok = n >= 1;
+  return FH_OK;
+}
+
+template <typename T, int CS>
+fh_status cluster_fits(fh_solver* s, bool* ok) {
+  return s->g.nv == 3 ? cluster_fits_nv<T, 3, CS>(s, ok) : cluster_fits_nv<T, 6, CS>(s, ok);
+}
+
+template <typename T, int NV, int CS>
+fh_status launch_cluster_nv(fh_solver* s, int nload) {
+  const GridInfo& g = s->g;
+  const fh::ClusterLayout lay = fh::cluster_layout<T>(g.dims[0], g.L, g.nv, CS);
+  auto kern = fh::cluster_solve_2d<T, NV, CS>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nload * CS);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = lay.total;
+  cfg.stream = s->work;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  using C = typename fh::cplx_t<T>::type;
+  CK(cudaLaunchKernelEx(&cfg, kern, g, s->ax[0].plan, s->ax[1].plan, (const C*)twp<T>(s->ax[0]),
+                        (const C*)twp<T>(s->ax[1]), Eptr<T>(s), (const uint8_t*)s->phase, dCptr<T>(s), s->nphase,
+                        Gptr<T>(s), s->ctl, s->st, s->hist));
+  return FH_OK;
+}
+
+template <typename T, int CS>
+fh_status launch_cluster(fh_solver* s, int nload) {
+  return s->g.nv == 3 ? launch_cluster_nv<T, 3, CS>(s, nload) : launch_cluster_nv<T, 6, CS>(s, nload);
+}
+
+// Pick path and cluster size; returns 1 (passes) or 2 (cluster) in *path.
+template <typename T>
+fh_status choose_path(fh_solver* s, int want_path, int want_cs, int* path, int* cs) {
+  *path = 1;
+  *cs = 0;
+  if (want_path == 1) return FH_OK;
+  bool ok8 = false, ok16 = false;
+  if (want_cs == 0 || want_cs == 16) {
+    fh_status rc = cluster_fits<T, 16>(s, &ok16);
+    if (rc != FH_OK) return rc;
+  }
+  if (want_cs == 0 || want_cs == 8) {
+    fh_status rc = cluster_fits<T, 8>(s, &ok8);
+    if (rc != FH_OK) return rc;
+  }
+  if (ok16 && (want_cs == 16 || want_cs == 0)) { *path = 2; *cs = 16; }
+  else if (ok8) { *path = 2; *cs = 8; }
+  if (want_path == 2 && *path != 2) {
+    fh::set_error("cluster-resident path unavailable for this grid (needs 2 axes and fields that fit in a cluster)");
+    return FH_ERR_UNSUPPORTED;
+  }
+  return FH_OK;
+}
+
+template <typename T>
+fh_status run_solve_cluster(fh_solver* s, int nload, int cs, long long* launches) {
+  CK(cudaEventRecord(s->ev0, s->work));
+  fh_status rc = cs == 16 ? launch_cluster<T, 16>(s, nload) : launch_cluster<T, 8>(s, nload);
+  if (rc != FH_OK) return rc;
+  const int bpl = std::max(1, (int)std::min<long long>((s->g.m + kThreads - 1) / kThreads, 64));
+  fh::mean_stress<T><<<nload * bpl, kThreads, 0, s->work>>>(s->g, Eptr<T>(s), s->phase, s->Cp64, s->ctl, s->partials2,
+                                                            s->mstress, bpl);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(s->ev1, s->work));
+  *launches = 2;
   return FH_OK;
 }
 
@@ -393,14 +519,7 @@ fh_status profile_passes(fh_solver* s, int prec, int nload, int reps, double* ms
     for (int k = 0; k < a; ++k) n_outer *= g.dims[k];
     for (int k = a + 1; k + 1 < g.nd; ++k) n_inner *= g.dims[k];
     const unsigned blocks = (unsigned)((long long)nload * n_outer * n_inner * s->ntiles[prec][a]);
-    const size_t sm = s->line_smem[prec][a];
-    const int W = s->lineW[prec][a], nt = s->ntiles[prec][a];
-    if (mode == 0)
-      fh::line_pass<T, 0><<<blocks, kThreads, sm, s->work>>>(g, s->ax[a].plan, twp<T>(s->ax[a]), S, Gptr<T>(s), s->st, a, W, nt, (int)n_outer, (int)n_inner);
-    else if (mode == 1)
-      fh::line_pass<T, 1><<<blocks, kThreads, sm, s->work>>>(g, s->ax[a].plan, twp<T>(s->ax[a]), S, Gptr<T>(s), s->st, a, W, nt, (int)n_outer, (int)n_inner);
-    else
-      fh::line_pass<T, 2><<<blocks, kThreads, sm, s->work>>>(g, s->ax[a].plan, twp<T>(s->ax[a]), S, Gptr<T>(s), s->st, a, W, nt, (int)n_outer, (int)n_inner);
+    launch_line<T>(s, prec, a, mode, blocks, (int)n_outer, (int)n_inner);
   };
   if (g.nd == 1) {
     rc = timed(1, [&] {
@@ -706,32 +825,36 @@ fh_status fh_set_reference(fh_solver* s, const double* C0) {
   return FH_OK;
 }
 
-fh_status fh_solve(fh_solver* s, int nload, const double* eps0, const fh_solve_opts* opts, fh_result* res) {
-  if (!s || !eps0 || !opts) { fh::set_error("null argument"); return FH_ERR_ARG; }
-  if (!s->have_table) { fh::set_error("set stiffness and reference medium first"); return FH_ERR_STATE; }
-  if (nload < 1 || nload > s->nload_max) { fh::set_error("nload out of range"); return FH_ERR_ARG; }
-  if (opts->max_iter < 1 || opts->max_iter > 10000000 || !(opts->tol >= 0.0)) { fh::set_error("bad tol/max_iter"); return FH_ERR_ARG; }
-  if (opts->precision != FH_PREC_FP64 && opts->precision != FH_PREC_FP32) { fh::set_error("unknown precision"); return FH_ERR_ARG; }
-  if (opts->init != 0 && opts->init != 1) { fh::set_error("init must be 0 or 1"); return FH_ERR_ARG; }
+}  // extern "C"
+
+namespace {
+
+struct PhaseOut {
+  LoadState hs[FH_MAX_LOADS];
+  double ms[FH_MAX_LOADS * fh::MAXV];
+  float elapsed = 0.f;
+  long long launches = 0;
+  int path = 1, cs = 0;
+};
+
+// One run of the fixed point in one precision.  `start` (may be null) gives the
+// per-load state to continue from; otherwise every load starts at iteration 0.
+fh_status solve_phase(fh_solver* s, int nload, const double* eps0, double tol, int max_iter, int prec, int init,
+                      int chunk, int want_path, int want_cs, const LoadState* start, PhaseOut* out) {
   const int nv = s->g.nv;
-  for (int i = 0; i < nload * nv; ++i)
-    if (!std::isfinite(eps0[i])) { fh::set_error("non-finite eps0"); return FH_ERR_ARG; }
-  const int prec = opts->precision;
-  const int chunk = opts->chunk > 0 ? std::min(opts->chunk, 1024) : 32;
   Control h{};
   for (int l = 0; l < nload; ++l)
     for (int c = 0; c < nv; ++c) h.eps0[l][c] = eps0[l * nv + c];
-  h.tol = opts->tol;
-  h.max_iter = opts->max_iter;
+  h.tol = tol;
+  h.max_iter = max_iter;
   h.nload = nload;
   h.hist_cap = kHistCap;
-  fh_status rc = join_user(s);
-  if (rc != FH_OK) return rc;
   CK(cudaMemcpyAsync(s->ctl, &h, sizeof(Control), cudaMemcpyHostToDevice, s->work));
-  CK(cudaMemsetAsync(s->st, 0, FH_MAX_LOADS * sizeof(LoadState), s->work));
+  if (start) CK(cudaMemcpyAsync(s->st, start, nload * sizeof(LoadState), cudaMemcpyHostToDevice, s->work));
+  else CK(cudaMemsetAsync(s->st, 0, FH_MAX_LOADS * sizeof(LoadState), s->work));
   const size_t nfield = (size_t)nload * nv * s->g.m;
   const unsigned conv_blocks = 1024;
-  if (opts->init == 0) {
+  if (init == 0) {
     if (prec == FH_PREC_FP64) CK(cudaMemsetAsync(s->E64, 0, nfield * sizeof(double), s->work));
     else CK(cudaMemsetAsync(s->E32, 0, nfield * sizeof(float), s->work));
   } else if (s->E_prec != prec) {
@@ -740,37 +863,93 @@ fh_status fh_solve(fh_solver* s, int nload, const double* eps0, const fh_solve_o
     CK(cudaGetLastError());
   }
   s->E_prec = prec;
-  long long launches = 0;
-  rc = prec == FH_PREC_FP64 ? run_solve<double>(s, prec, nload, chunk, opts->max_iter, &launches)
-                            : run_solve<float>(s, prec, nload, chunk, opts->max_iter, &launches);
+  fh_status rc = prec == FH_PREC_FP64 ? choose_path<double>(s, want_path, want_cs, &out->path, &out->cs)
+                                      : choose_path<float>(s, want_path, want_cs, &out->path, &out->cs);
   if (rc != FH_OK) return rc;
-  LoadState hs[FH_MAX_LOADS];
-  double ms[FH_MAX_LOADS * fh::MAXV];
-  CK(cudaMemcpyAsync(hs, s->st, sizeof(LoadState) * nload, cudaMemcpyDeviceToHost, s->work));
-  CK(cudaMemcpyAsync(ms, s->mstress, sizeof(double) * nload * fh::MAXV, cudaMemcpyDeviceToHost, s->work));
+  if (out->path == 2)
+    rc = prec == FH_PREC_FP64 ? run_solve_cluster<double>(s, nload, out->cs, &out->launches)
+                              : run_solve_cluster<float>(s, nload, out->cs, &out->launches);
+  else
+    rc = prec == FH_PREC_FP64 ? run_solve<double>(s, prec, nload, chunk, max_iter, &out->launches)
+                              : run_solve<float>(s, prec, nload, chunk, max_iter, &out->launches);
+  if (rc != FH_OK) return rc;
+  CK(cudaMemcpyAsync(out->hs, s->st, sizeof(LoadState) * nload, cudaMemcpyDeviceToHost, s->work));
+  CK(cudaMemcpyAsync(out->ms, s->mstress, sizeof(double) * nload * fh::MAXV, cudaMemcpyDeviceToHost, s->work));
   CK(cudaStreamSynchronize(s->work));
-  float ms_elapsed = 0.f;
-  CK(cudaEventElapsedTime(&ms_elapsed, s->ev0, s->ev1));
+  CK(cudaEventElapsedTime(&out->elapsed, s->ev0, s->ev1));
+  return FH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fh_status fh_solve(fh_solver* s, int nload, const double* eps0, const fh_solve_opts* opts, fh_result* res) {
+  if (!s || !eps0 || !opts) { fh::set_error("null argument"); return FH_ERR_ARG; }
+  if (!s->have_table) { fh::set_error("set stiffness and reference medium first"); return FH_ERR_STATE; }
+  if (nload < 1 || nload > s->nload_max) { fh::set_error("nload out of range"); return FH_ERR_ARG; }
+  if (opts->max_iter < 1 || opts->max_iter > 10000000 || !(opts->tol >= 0.0)) { fh::set_error("bad tol/max_iter"); return FH_ERR_ARG; }
+  if (opts->precision != FH_PREC_FP64 && opts->precision != FH_PREC_FP32 && opts->precision != FH_PREC_MIXED) {
+    fh::set_error("unknown precision");
+    return FH_ERR_ARG;
+  }
+  if (opts->init != 0 && opts->init != 1) { fh::set_error("init must be 0 or 1"); return FH_ERR_ARG; }
+  if (opts->path < 0 || opts->path > 2 || (opts->cluster != 0 && opts->cluster != 8 && opts->cluster != 16)) {
+    fh::set_error("path must be 0..2 and cluster 0, 8 or 16");
+    return FH_ERR_ARG;
+  }
+  const int nv = s->g.nv;
+  for (int i = 0; i < nload * nv; ++i)
+    if (!std::isfinite(eps0[i])) { fh::set_error("non-finite eps0"); return FH_ERR_ARG; }
+  const int chunk = opts->chunk > 0 ? std::min(opts->chunk, 1024) : 32;
+  fh_status rc = join_user(s);
+  if (rc != FH_OK) return rc;
+  PhaseOut A;
+  const int prec1 = opts->precision == FH_PREC_FP64 ? FH_PREC_FP64 : FH_PREC_FP32;
+  rc = solve_phase(s, nload, eps0, opts->tol, opts->max_iter, prec1, opts->init, chunk, opts->path, opts->cluster,
+                   nullptr, &A);
+  if (rc != FH_OK) return rc;
+  PhaseOut* fin = &A;
+  PhaseOut B;
+  if (opts->precision == FH_PREC_MIXED) {
+    // one FP64 iteration from the FP32 iterate: every load continues its count
+    // and stops after exactly one step (tolerance set to +inf for this phase)
+    LoadState st0[FH_MAX_LOADS];
+    for (int l = 0; l < nload; ++l) {
+      st0[l] = A.hs[l];
+      st0[l].done = 0;
+      st0[l].inc = 0;
+    }
+    rc = solve_phase(s, nload, eps0, HUGE_VAL, 0x7fffffff, FH_PREC_FP64, 1, chunk, opts->path, opts->cluster, st0, &B);
+    if (rc != FH_OK) return rc;
+    for (int l = 0; l < nload; ++l) B.hs[l].status = A.hs[l].status;
+    B.elapsed += A.elapsed;
+    B.launches += A.launches;
+    fin = &B;
+  }
   fh_status worst = FH_OK;
   auto rank = [](int st) { return st == FH_NONFINITE ? 3 : st == FH_DIVERGED ? 2 : st == FH_NOT_CONVERGED ? 1 : 0; };
   if (res) std::memset(res, 0, sizeof(*res));
   for (int l = 0; l < nload; ++l) {
-    if (rank(hs[l].status) > rank(worst)) worst = (fh_status)hs[l].status;
-    s->last_iters[l] = hs[l].iter;
+    const LoadState& hs = fin->hs[l];
+    if (rank(hs.status) > rank(worst)) worst = (fh_status)hs.status;
+    s->last_iters[l] = hs.iter;
     if (res) {
-      res->iterations[l] = hs[l].iter;
-      res->residual[l] = hs[l].r;
-      res->status[l] = hs[l].status;
-      for (int c = 0; c < nv; ++c) res->mean_stress[l * 6 + c] = ms[l * fh::MAXV + c];
+      res->iterations[l] = hs.iter;
+      res->residual[l] = hs.r;
+      res->status[l] = hs.status;
+      for (int c = 0; c < nv; ++c) res->mean_stress[l * 6 + c] = fin->ms[l * fh::MAXV + c];
     }
     for (int c = 0; c < nv; ++c) {
-      s->last_ms[l * 6 + c] = ms[l * fh::MAXV + c];
+      s->last_ms[l * 6 + c] = fin->ms[l * fh::MAXV + c];
       s->last_eps0[l * 6 + c] = eps0[l * nv + c];
     }
   }
   if (res) {
-    res->elapsed_ms = ms_elapsed;
-    res->kernel_launches = launches;
+    res->elapsed_ms = fin->elapsed;
+    res->kernel_launches = fin->launches;
+    res->path = A.path;
+    res->cluster = A.cs;
   }
   s->last_nload = nload;
   s->have_solution = true;

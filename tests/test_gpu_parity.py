@@ -60,18 +60,58 @@ def test_green_table_matches_oracle(fh, spec):
     assert rel(Gg, Go) < 1e-12
 
 
+PATHS = [(1, 0), (2, 8), (2, 16)]   # (path, cluster size)
+
+
+def _solve_or_skip(fh, s, eps0, n, prec, path):
+    """Solve with a forced path; a cluster size whose fields do not fit is skipped."""
+    try:
+        return s.solve(eps0, tol=0.0, max_iter=n, precision=prec, path=path[0], cluster=path[1])
+    except fh.FhError as e:
+        if e.status == -8 and path[0] == 2:
+            pytest.skip("fields do not fit in a cluster of this size")
+        raise
+
+
+@pytest.mark.parametrize("path", PATHS, ids=["passes", "cluster8", "cluster16"])
 @pytest.mark.parametrize("spec", CASES, ids=[c[0] for c in CASES])
-def test_fixed_iterations_match_oracle(fh, spec):
+def test_fixed_iterations_match_oracle(fh, spec, path):
     case = _case(spec)
     s = case.product(fh)
     n = 25
-    out = s.solve(case.eps0, tol=0.0, max_iter=n)
+    two_axes = len(case.pattern.dims) == 2
+    if path[0] == 2 and not two_axes:
+        with pytest.raises(fh.FhError) as e:
+            s.solve(case.eps0, tol=0.0, max_iter=n, path=path[0], cluster=path[1])
+        assert e.value.status == -8
+        return
+    out = _solve_or_skip(fh, s, case.eps0, n, fh.FH_PREC_FP64, path)
+    assert out["path"] == path[0]
     ref = case.oracle_solve(tol=0.0, max_iter=n)
     assert list(out["iterations"]) == [n] * case.nload
     assert case.strain_error(s, ref["E"]) < TOL64
     for L in range(case.nload):
         assert rel(s.get_residuals(L), ref["resid"][L]) < 1e-9
     assert rel(out["mean_stress"], ref["mean_stress"]) < TOL64
+
+
+# FP32 bulk stages: each iteration adds rounding of order eps32 * log2(m) ~ 1e-6
+# relative, damped by the contraction; 25 iterations stay below 5e-5.
+TOL32 = 5e-5
+
+
+@pytest.mark.parametrize("path", PATHS, ids=["passes", "cluster8", "cluster16"])
+@pytest.mark.parametrize("spec", CASES[:5], ids=[c[0] for c in CASES[:5]])
+def test_fp32_stages_track_fp64_oracle(fh, spec, path):
+    case = _case(spec)
+    s = case.product(fh)
+    if path[0] == 2 and len(case.pattern.dims) != 2:
+        pytest.skip("cluster path needs two axes")
+    n = 25
+    out = _solve_or_skip(fh, s, case.eps0, n, fh.FH_PREC_FP32, path)
+    ref = case.oracle_solve(tol=0.0, max_iter=n)
+    assert case.strain_error(s, ref["E"]) < TOL32
+    assert rel(out["mean_stress"], ref["mean_stress"]) < TOL32
 
 
 def test_config_disk32_to_tolerance(fh):
@@ -99,17 +139,28 @@ def test_config_disk32_to_tolerance(fh):
     assert rel(Cg, Cg.T) < 1e-6
 
 
-def test_config_dlvp_sheared_full_size(fh):
+@pytest.mark.parametrize("path", PATHS, ids=["passes", "cluster8", "cluster16"])
+def test_config_dlvp_sheared_full_size(fh, path):
     """M = [[128,32],[0,128]] (grid 32 x 512), dlVP, 20 disks at contrast 100: the
-    benchmark workload, FP64, 200 iterations element by element against the oracle."""
+    benchmark workload, FP64, 200 iterations element by element against the oracle,
+    in every launch configuration the benchmark can take."""
     w = W.dlvp_sheared()
     case = Case.from_workload(w)
     s = case.product(fh)
     n = 200
-    out = s.solve(case.eps0, tol=0.0, max_iter=n)
+    out = _solve_or_skip(fh, s, case.eps0, n, fh.FH_PREC_FP64, path)
     ref = case.oracle_solve(tol=0.0, max_iter=n)
     assert case.strain_error(s, ref["E"]) < TOL64
     assert rel(out["mean_stress"], ref["mean_stress"]) < TOL64
+
+
+def test_benchmark_workload_takes_the_cluster_path(fh):
+    """The benchmark workload runs cluster-resident in both precisions (automatic choice)."""
+    case = Case.from_workload(W.dlvp_sheared())
+    s = case.product(fh)
+    for prec in (fh.FH_PREC_FP64, fh.FH_PREC_FP32):
+        out = s.solve(case.eps0, tol=0.0, max_iter=3, precision=prec)
+        assert out["path"] == 2 and out["cluster"] in (8, 16)
 
 
 def test_homogeneous_medium_stops_after_one_iteration(fh):
@@ -122,13 +173,14 @@ def test_homogeneous_medium_stops_after_one_iteration(fh):
         assert np.abs(s.get_strain(L)).max() < 1e-14
 
 
-def test_resume_is_bitwise_identical(fh):
+@pytest.mark.parametrize("path", [1, 2])
+def test_resume_is_bitwise_identical(fh, path):
     case = _case(CASES[1])
     s = case.product(fh)
-    s.solve(case.eps0, tol=0.0, max_iter=20)
+    s.solve(case.eps0, tol=0.0, max_iter=20, path=path)
     E20 = [s.get_strain(L).copy() for L in range(3)]
-    s.solve(case.eps0, tol=0.0, max_iter=12)
-    s.solve(case.eps0, tol=0.0, max_iter=8, init=1)
+    s.solve(case.eps0, tol=0.0, max_iter=12, path=path)
+    s.solve(case.eps0, tol=0.0, max_iter=8, init=1, path=path)
     for L in range(3):
         assert np.array_equal(s.get_strain(L), E20[L])
 
@@ -188,3 +240,36 @@ def test_nonfinite_stiffness_is_reported(fh):
     with pytest.raises(fh.FhError) as e:
         s.set_stiffness_phases(np.zeros(64, np.uint8), Cp)
     assert e.value.status == -1
+
+
+def _ceff_reference():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "ceff_dlvp_sheared.txt")
+    return np.loadtxt(path)
+
+
+@pytest.mark.parametrize("prec,bound", [("fp64", 1e-6), ("mixed", 1e-6), ("fp32", 5e-6)])
+def test_benchmark_workload_ceff_accuracy(fh, prec, bound):
+    """C_eff at the benchmark tolerance (Cauchy r <= 1e-6) against the converged FP64
+    oracle (golden file): plain FP64 and the mixed mode (FP32 iterations + one FP64
+    step) meet 1e-6 relative; FP32 alone is reported with its own, looser bound."""
+    P = {"fp64": fh.FH_PREC_FP64, "mixed": fh.FH_PREC_MIXED, "fp32": fh.FH_PREC_FP32}[prec]
+    case = Case.from_workload(W.dlvp_sheared())
+    s = case.product(fh)
+    out = s.solve(case.eps0, tol=1e-6, max_iter=20000, precision=P)
+    assert out["status"] == 0
+    C = s.get_ceff()
+    Cref = _ceff_reference()
+    err = np.linalg.norm(C - Cref) / np.linalg.norm(Cref)
+    print(f"{prec}: C_eff relative error {err:.3e}, iterations {out['iterations']}")
+    assert err < bound
+
+
+def test_mixed_mode_continues_the_iteration_count(fh):
+    case = _case(CASES[0])
+    s = case.product(fh)
+    a = s.solve(case.eps0, tol=1e-5, max_iter=5000, precision=fh.FH_PREC_FP32)
+    b = s.solve(case.eps0, tol=1e-5, max_iter=5000, precision=fh.FH_PREC_MIXED)
+    assert list(b["iterations"]) == [i + 1 for i in a["iterations"]]
+    h = s.get_residuals(0)
+    assert len(h) == b["iterations"][0]
