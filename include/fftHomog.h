@@ -87,10 +87,13 @@ typedef struct {
 
 /* FH_PREC_FP64: every stage in FP64.  FH_PREC_FP32: FFT, stress and Green
  * stages in FP32 (table built in FP64 and rounded; residual sums carried with
- * about 48 bits; mean stress in FP64).  FH_PREC_MIXED: the FP32 iteration to
- * the tolerance, then one FP64 iteration from its iterate, which removes most
- * of the FP32 rounding from E and C_eff; the reported residual of each load is
- * that FP64 step's Cauchy residual and the iteration count includes it. */
+ * about 48 bits; mean stress in FP64).  FH_PREC_MIXED: FP32 iterations until a
+ * load meets the tolerance or its residual stops improving (no 1% progress in
+ * 50 iterations: the FP32 rounding floor), then FP64 iterations from that
+ * iterate until the FP64 Cauchy residual meets the tolerance (at least one),
+ * which removes the FP32 rounding from E and C_eff.  Iteration counts and the
+ * residual history cover both phases; status and residual are the FP64
+ * phase's. */
 typedef enum { FH_PREC_FP64 = 0, FH_PREC_FP32 = 1, FH_PREC_MIXED = 2 } fh_precision;
 
 typedef struct {
@@ -192,6 +195,17 @@ fh_status fh_set_reference(fh_solver* s, const double* C0);
  * FH_DIVERGED > FH_NOT_CONVERGED), or an error code. */
 fh_status fh_solve(fh_solver* s, int nload, const double* eps0,
                    const fh_solve_opts* opts, fh_result* res);
+
+/* Batched solve: runs fh_solve on n distinct solvers (patterns of any sizes)
+ * with one shared set of options; nload[i] and eps0[i] are solver i's load
+ * count and strains, res[i] (host, may be NULL) its result.  Every solver's
+ * work is enqueued on its own stream before any is waited for, so cluster-
+ * resident solves of different patterns run concurrently on the GPU; solvers
+ * that need the whole-GPU pass path run their host-driven loops in turn while
+ * the others proceed.  Returns the worst per-load status over the batch or an
+ * error code (nothing is run when an argument check fails). */
+fh_status fh_solve_batch(fh_solver* const* solvers, int n, const int* nload, const double* const* eps0,
+                         const fh_solve_opts* opts, fh_result* res);
 
 /* Copy the strain fluctuation E of one load (component-major: E[c*m + i] is
  * component c at stored point i) into host or device memory, as doubles. */

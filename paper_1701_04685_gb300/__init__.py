@@ -83,6 +83,7 @@ def library():
             "fh_get_green": (I, [P, P]),
             "fh_get_residuals": (I, [P, I, P, P]),
             "fh_profile_passes": (I, [P, I, I, I, P]),
+            "fh_solve_batch": (I, [P, I, P, P, C.POINTER(fh_solve_opts), P]),
             "fh_status_string": (C.c_char_p, [I]),
             "fh_last_error": (C.c_char_p, []),
         }
@@ -100,7 +101,7 @@ def exported_symbols():
             "fh_pattern_numerators", "fh_pattern_half_freqs", "fh_solver_create", "fh_solver_destroy",
             "fh_set_stiffness_phases", "fh_set_reference", "fh_solve", "fh_get_strain", "fh_set_strain",
             "fh_get_ceff", "fh_get_green", "fh_get_residuals", "fh_profile_passes", "fh_status_string",
-            "fh_last_error", "fh_mean_stress_noalloc"]
+            "fh_last_error", "fh_mean_stress_noalloc", "fh_solve_batch"]
 
 
 def _check(rc, ok=(FH_OK,)):
@@ -306,3 +307,26 @@ class Solver:
         ms = np.zeros(4)
         _check(library().fh_profile_passes(self._h, int(nload), int(precision), int(reps), _ptr(ms)))
         return ms
+
+
+def solve_batch(solvers, eps0s, tol=1e-6, max_iter=20000, precision=FH_PREC_MIXED, init=0, chunk=0, path=0,
+                cluster=0):
+    """fh_solve_batch over a list of Solver objects; eps0s[i] is solver i's (n_L, n_v) strains."""
+    n = len(solvers)
+    hs = (C.c_void_p * n)(*[sv._h.value for sv in solvers])
+    e0 = [np.ascontiguousarray(np.atleast_2d(np.asarray(e, dtype=np.float64))) for e in eps0s]
+    nl = (C.c_int * n)(*[e.shape[0] for e in e0])
+    ptrs = (C.c_void_p * n)(*[e.ctypes.data for e in e0])
+    opts = fh_solve_opts(float(tol), int(max_iter), int(precision), int(init), int(chunk), int(path), int(cluster))
+    res = (fh_result * n)()
+    rc = library().fh_solve_batch(hs, n, nl, ptrs, C.byref(opts), res)
+    _check(rc, ok=(FH_OK, FH_NOT_CONVERGED, FH_DIVERGED, FH_NONFINITE))
+    out = []
+    for i, sv in enumerate(solvers):
+        k = e0[i].shape[0]
+        out.append({"iterations": np.array(res[i].iterations[:k]), "residual": np.array(res[i].residual[:k]),
+                    "load_status": np.array(res[i].status[:k]),
+                    "mean_stress": np.array(res[i].mean_stress[: k * 6]).reshape(k, 6)[:, : sv.nv],
+                    "elapsed_ms": res[i].elapsed_ms, "kernel_launches": res[i].kernel_launches,
+                    "path": res[i].path, "cluster": res[i].cluster})
+    return rc, out

@@ -40,8 +40,13 @@ struct ClusterLayout {
 
 __host__ __device__ inline int split_lo(int n, int parts, int c) { return (int)(((long long)n * c) / parts); }
 
+// shift of the row-line padding: one spare slot per 128-byte wavefront
+template <typename T> struct RowPad { static constexpr int SH = sizeof(T) == 4 ? 4 : 3; };
+
+// g_smem = false keeps the Gamma^p slice in global memory (L2) instead of
+// shared memory, for grids whose fields fill the cluster otherwise.
 template <typename T>
-__host__ __device__ inline ClusterLayout cluster_layout(int N0, int L, int nv, int CS) {
+__host__ __device__ inline ClusterLayout cluster_layout(int N0, int L, int nv, int CS, bool g_smem = true) {
   ClusterLayout c{};
   const int H = L / 2 + 1;
   c.rows_max = 0;
@@ -57,7 +62,7 @@ __host__ __device__ inline ClusterLayout cluster_layout(int N0, int L, int nv, i
   size_t o = 0;
   c.off_E = o;    o = align(o + (size_t)c.rows_max * nv * L * sizeof(T));
   c.off_S = o;    o = align(o + (size_t)c.rows_max * nv * H * cs);
-  c.off_G = o;    o = align(o + ntri * (size_t)N0 * c.cols_max * sizeof(T));
+  c.off_G = o;    o = align(o + (g_smem ? ntri * (size_t)N0 * c.cols_max * sizeof(T) : 0));
   c.off_ph = o;   o = align(o + (size_t)c.rows_max * L);
   c.off_tw0 = o;  o = align(o + (size_t)N0 * cs);
   c.off_tw1 = o;  o = align(o + (size_t)L * cs);
@@ -65,8 +70,8 @@ __host__ __device__ inline ClusterLayout cluster_layout(int N0, int L, int nv, i
   c.off_own = o;  o = align(o + (size_t)N0);
   c.off_loc = o;  o = align(o + (size_t)N0 * sizeof(short));
   c.off_part = o; o = align(o + (size_t)CS * 2 * sizeof(double));
-  const size_t row_work = (size_t)2 * c.npair_max * L * cs;
-  const size_t col_work = (size_t)2 * nv * c.cols_max * N0 * cs;
+  const size_t row_work = (size_t)2 * c.npair_max * padded_len<RowPad<T>::SH>(L) * cs;
+  const size_t col_work = (size_t)2 * nv * c.cols_max * (N0 + 1) * cs;
   c.off_work = o; o = align(o + (row_work > col_work ? row_work : col_work));
   c.total = o;
   return c;
@@ -77,7 +82,7 @@ __global__ void __launch_bounds__(256, 1)
 cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __restrict__ tw0g,
                  const cplx<T>* __restrict__ tw1g, T* __restrict__ Eg, const uint8_t* __restrict__ phase,
                  const T* __restrict__ dC, int nphase, const T* __restrict__ Gt, Control* ctl, LoadState* st,
-                 double* __restrict__ hist) {
+                 double* __restrict__ hist, int g_smem) {
   constexpr int NTRI = NV * (NV + 1) / 2;
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ double red[32];
@@ -86,7 +91,7 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
   const int load = blockIdx.x / CS;
   const int N0 = g.dims[0], L = g.L, H = g.H;
   const int m = (int)g.m;
-  const ClusterLayout lay = cluster_layout<T>(N0, L, NV, CS);
+  const ClusterLayout lay = cluster_layout<T>(N0, L, NV, CS, g_smem != 0);
   const int r0 = split_lo(N0, CS, rank), r1 = split_lo(N0, CS, rank + 1);
   const int c0 = split_lo(H, CS, rank), c1 = split_lo(H, CS, rank + 1);
   const int nrow = r1 - r0, ncol = c1 - c0;
@@ -100,10 +105,13 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
   uint8_t* own = sm + lay.off_own;                                // owner rank of row n
   short* loc = reinterpret_cast<short*>(sm + lay.off_loc);        // local row index in the owner
   double* part = reinterpret_cast<double*>(sm + lay.off_part);    // [CS][2], used in rank 0
+  constexpr int PS = RowPad<T>::SH;
+  const int Lp = padded_len<PS>(L);      // padded row-line stride
+  const int N0p = N0 + 1;                // odd column-line stride
   cplx<T>* W0 = reinterpret_cast<cplx<T>*>(sm + lay.off_work);
-  cplx<T>* W1 = reinterpret_cast<cplx<T>*>(sm + lay.off_work) + (size_t)lay.npair_max * L;
+  cplx<T>* W1 = reinterpret_cast<cplx<T>*>(sm + lay.off_work) + (size_t)lay.npair_max * Lp;
   cplx<T>* X0 = W0;
-  cplx<T>* X1 = W0 + (size_t)NV * lay.cols_max * N0;
+  cplx<T>* X1 = W0 + (size_t)NV * lay.cols_max * N0p;
   const size_t Ebase = (size_t)load * NV * g.m;
   const FDiv fL = make_fdiv(L), fH = make_fdiv(H), fN0 = make_fdiv(N0), fnc = make_fdiv(ncol > 0 ? ncol : 1);
 
@@ -125,7 +133,7 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
 #pragma unroll
     for (int c = 0; c < NV; ++c) El[(r * NV + c) * L + x] = Eg[Ebase + (size_t)c * m + gi];
   }
-  for (int i = threadIdx.x; i < NTRI * N0 * ncol; i += blockDim.x) {
+  for (int i = threadIdx.x; g_smem && i < NTRI * N0 * ncol; i += blockDim.x) {
     const int t2 = fdiv(i, fnc);
     const int j = i - t2 * ncol;
     const int t = fdiv(t2, fN0);
@@ -138,6 +146,7 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
   LoadState s = st[load];
   const double tol = ctl->tol;
   const int max_iter = ctl->max_iter;
+  const int stall_window = ctl->stall_window;
   const T scale = (T)g.inv_m;
   __syncthreads();
 
@@ -161,10 +170,10 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
         cplx<T> z;
         z.x = A.x - B.y;
         z.y = A.y + B.x;
-        W0[p * L + k] = z;
+        W0[p * Lp + padi<PS>(k)] = z;
       }
       __syncthreads();
-      Z = fft_lines_pp<+1, T>(W0, W1, npair, L, plan1, tw1);
+      Z = fft_lines_pp<+1, T, PS>(W0, W1, npair, Lp, plan1, tw1);
       Zo = (Z == W0) ? W1 : W0;
     }
     for (int idx = threadIdx.x; idx < nrow * L; idx += blockDim.x) {
@@ -175,7 +184,7 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
         const int f = r * NV + c;
         T* ep = &El[f * L + x];
         if (with_inverse) {
-          const cplx<T> zz = Z[(f >> 1) * L + x];
+          const cplx<T> zz = Z[(f >> 1) * Lp + padi<PS>(x)];
           en[c] = ((f & 1) ? zz.y : zz.x) * scale;
           acc_d.add_sq(en[c] - *ep);
           acc_n.add_sq(en[c] + e0[c]);
@@ -191,18 +200,18 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
 #pragma unroll
         for (int b = 0; b < NV; ++b) t += dc[a * NV + b] * (en[b] + e0[b]);
         const int f = r * NV + a;
-        if (f & 1) Z[(f >> 1) * L + x].y = t;
-        else Z[(f >> 1) * L + x].x = t;
+        if (f & 1) Z[(f >> 1) * Lp + padi<PS>(x)].y = t;
+        else Z[(f >> 1) * Lp + padi<PS>(x)].x = t;
       }
     }
     if (nreal & 1)
-      for (int x = threadIdx.x; x < L; x += blockDim.x) Z[(npair - 1) * L + x].y = T(0);
+      for (int x = threadIdx.x; x < L; x += blockDim.x) Z[(npair - 1) * Lp + padi<PS>(x)].y = T(0);
     __syncthreads();
-    cplx<T>* Zf = fft_lines_pp<-1, T>(Z, Zo, npair, L, plan1, tw1);
+    cplx<T>* Zf = fft_lines_pp<-1, T, PS>(Z, Zo, npair, Lp, plan1, tw1);
     for (int idx = threadIdx.x; idx < npair * H; idx += blockDim.x) {
       const int p = fdiv(idx, fH), k = idx - p * H;
-      const cplx<T> zk = Zf[p * L + k];
-      const cplx<T> zm = Zf[p * L + (k == 0 ? 0 : L - k)];
+      const cplx<T> zk = Zf[p * Lp + padi<PS>(k)];
+      const cplx<T> zm = Zf[p * Lp + padi<PS>(k == 0 ? 0 : L - k)];
       cplx<T> A, B;
       A.x = T(0.5) * (zk.x + zm.x);
       A.y = T(0.5) * (zk.y - zm.y);
@@ -222,20 +231,21 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
       const int c = fdiv(t, fN0);
       const int n = t - c * N0;
       const cplx<T>* rem = cluster.map_shared_rank(Sl, (int)own[n]);
-      X0[(c * ncol + j) * N0 + n] = rem[((int)loc[n] * NV + c) * H + c0 + j];
+      X0[(c * ncol + j) * N0p + n] = rem[((int)loc[n] * NV + c) * H + c0 + j];
     }
     __syncthreads();
-    cplx<T>* Xf = fft_lines_pp<-1, T>(X0, X1, nl, N0, plan0, tw0);
+    cplx<T>* Xf = fft_lines_pp<-1, T>(X0, X1, nl, N0p, plan0, tw0);
     for (int idx = threadIdx.x; idx < N0 * ncol; idx += blockDim.x) {
       const int n = fdiv(idx, fnc);
       const int j = idx - n * ncol;
       cplx<T> tv[NV];
 #pragma unroll
-      for (int c = 0; c < NV; ++c) tv[c] = Xf[(c * ncol + j) * N0 + n];
+      for (int c = 0; c < NV; ++c) tv[c] = Xf[(c * ncol + j) * N0p + n];
       const bool zero = (n == 0 && c0 + j == 0);
       T gm[NTRI];
 #pragma unroll
-      for (int t = 0; t < NTRI; ++t) gm[t] = Gl[(t * N0 + n) * ncol + j];
+      for (int t = 0; t < NTRI; ++t)
+        gm[t] = g_smem ? Gl[(t * N0 + n) * ncol + j] : Gt[(size_t)t * g.nhalf + (size_t)n * H + c0 + j];
 #pragma unroll
       for (int a = 0; a < NV; ++a) {
         T re = T(0), im = T(0);
@@ -249,18 +259,18 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
         cplx<T> e;
         e.x = zero ? T(0) : re;
         e.y = zero ? T(0) : im;
-        Xf[(a * ncol + j) * N0 + n] = e;
+        Xf[(a * ncol + j) * N0p + n] = e;
       }
     }
     __syncthreads();
-    cplx<T>* Xi = fft_lines_pp<+1, T>(Xf, Xf == X0 ? X1 : X0, nl, N0, plan0, tw0);
+    cplx<T>* Xi = fft_lines_pp<+1, T>(Xf, Xf == X0 ? X1 : X0, nl, N0p, plan0, tw0);
     for (int idx = threadIdx.x; idx < NV * N0 * ncol; idx += blockDim.x) {
       const int t = fdiv(idx, fnc);
       const int j = idx - t * ncol;
       const int c = fdiv(t, fN0);
       const int n = t - c * N0;
       cplx<T>* rem = cluster.map_shared_rank(Sl, (int)own[n]);
-      rem[((int)loc[n] * NV + c) * H + c0 + j] = Xi[(c * ncol + j) * N0 + n];
+      rem[((int)loc[n] * NV + c) * H + c0 + j] = Xi[(c * ncol + j) * N0p + n];
     }
   };
 
@@ -293,18 +303,7 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
       LoadState t = s;
       advance_state(t, ctl, hist, load, a, b);
     }
-    {
-      // the same state update as advance_state, without the history write
-      const double r = (b > 0.0) ? sqrt(a / b) : sqrt(a);
-      s.iter += 1;
-      if (s.iter == 1) s.r_first = r;
-      s.inc = (s.iter > 1 && r > s.r) ? s.inc + 1 : 0;
-      s.r = r;
-      if (!isfinite(r)) { s.status = FH_NONFINITE; s.done = 1; }
-      else if (r <= tol) { s.status = FH_OK; s.done = 1; }
-      else if (s.inc >= 100 || (s.iter > 10 && r > 1e6 * s.r_first && r > 1.0)) { s.status = FH_DIVERGED; s.done = 1; }
-      else if (s.iter >= max_iter) { s.status = FH_NOT_CONVERGED; s.done = 1; }
-    }
+    update_state(s, a, b, tol, max_iter, stall_window);   // the same update in every thread
   }
   // ---- results
   for (int i = threadIdx.x; i < nrow * L; i += blockDim.x) {

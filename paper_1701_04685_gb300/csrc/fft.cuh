@@ -174,7 +174,14 @@ __device__ __forceinline__ int fdiv(int n, FDiv f) {
 // size Ns*R.  Butterfly j reads in[j + t*L/R] (t < R), applies the twiddles
 // w^{t k}, k = j mod Ns, w = exp(DIR 2 pi i / (Ns R)), does a length-R DFT and
 // writes out[(j / Ns) * Ns * R + k + t*Ns].
-template <int R, int DIR, typename T>
+// Position of element i inside a padded line: one spare slot after every
+// 2^PADSH elements (PADSH = 0: no padding).  With 2^PADSH elements per 128-byte
+// shared-memory wavefront, the strided writes of the early Stockham stages
+// (stride R) then spread over all banks.
+template <int PADSH> __device__ __forceinline__ int padi(int i) { return PADSH ? i + (i >> PADSH) : i; }
+template <int PADSH> __host__ __device__ inline int padded_len(int L) { return PADSH ? L + (L >> PADSH) + 1 : L; }
+
+template <int R, int DIR, typename T, int PADSH = 0>
 __device__ __forceinline__ void stockham_stage(const cplx<T>* in, cplx<T>* out, int nlines, int ls, int L, int Ns,
                                                const cplx<T>* __restrict__ tw) {
   const int nb = L / R;
@@ -190,7 +197,7 @@ __device__ __forceinline__ void stockham_stage(const cplx<T>* in, cplx<T>* out, 
     const int k = j - jq * Ns;
     cplx<T> v[R];
 #pragma unroll
-    for (int t = 0; t < R; ++t) v[t] = li[j + t * nb];
+    for (int t = 0; t < R; ++t) v[t] = li[padi<PADSH>(j + t * nb)];
     if (k != 0) {
 #pragma unroll
       for (int t = 1; t < R; ++t) {
@@ -202,7 +209,7 @@ __device__ __forceinline__ void stockham_stage(const cplx<T>* in, cplx<T>* out, 
     dft_small<R, DIR, T>(v, tw, L);
     const int base = jq * Ns * R + k;
 #pragma unroll
-    for (int t = 0; t < R; ++t) lo[base + t * Ns] = v[t];
+    for (int t = 0; t < R; ++t) lo[padi<PADSH>(base + t * Ns)] = v[t];
   }
 }
 
@@ -210,7 +217,7 @@ __device__ __forceinline__ void stockham_stage(const cplx<T>* in, cplx<T>* out, 
 // occupies buf[q*ls .. q*ls + L); tmp has the same shape (ping-pong buffer).
 // Every thread of the block must call this.  Returns the buffer (buf or tmp)
 // that holds the result; a __syncthreads() has been executed on return.
-template <int DIR, typename T>
+template <int DIR, typename T, int PADSH = 0>
 __device__ cplx<T>* fft_lines_pp(cplx<T>* buf, cplx<T>* tmp, int nlines, int ls, const DevPlan& plan,
                                  const cplx<T>* __restrict__ tw) {
   const int L = plan.L;
@@ -220,14 +227,14 @@ __device__ cplx<T>* fft_lines_pp(cplx<T>* buf, cplx<T>* tmp, int nlines, int ls,
   for (int s = 0; s < plan.np; ++s) {
     const int r = plan.r[s];
     switch (r) {
-      case 2: stockham_stage<2, DIR, T>(in, out, nlines, ls, L, Ns, tw); break;
-      case 3: stockham_stage<3, DIR, T>(in, out, nlines, ls, L, Ns, tw); break;
-      case 4: stockham_stage<4, DIR, T>(in, out, nlines, ls, L, Ns, tw); break;
-      case 5: stockham_stage<5, DIR, T>(in, out, nlines, ls, L, Ns, tw); break;
-      case 7: stockham_stage<7, DIR, T>(in, out, nlines, ls, L, Ns, tw); break;
-      case 8: stockham_stage<8, DIR, T>(in, out, nlines, ls, L, Ns, tw); break;
-      case 11: stockham_stage<11, DIR, T>(in, out, nlines, ls, L, Ns, tw); break;
-      default: stockham_stage<13, DIR, T>(in, out, nlines, ls, L, Ns, tw); break;
+      case 2: stockham_stage<2, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
+      case 3: stockham_stage<3, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
+      case 4: stockham_stage<4, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
+      case 5: stockham_stage<5, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
+      case 7: stockham_stage<7, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
+      case 8: stockham_stage<8, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
+      case 11: stockham_stage<11, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
+      default: stockham_stage<13, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
     }
     __syncthreads();
     cplx<T>* sw = in; in = out; out = sw;

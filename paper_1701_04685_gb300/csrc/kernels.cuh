@@ -41,7 +41,14 @@ struct LoadState {
   int inc;          // consecutive growing residuals
   double r;         // last residual
   double r_first;
+  double r_best;    // smallest residual so far
+  int since_best;   // iterations since r_best last improved by 1%
+  int pad_;
 };
+
+// internal status: the residual stopped improving (FP32 rounding floor); the
+// mixed mode then continues in FP64
+constexpr int kStatusStalled = 4;
 
 struct Control {
   double eps0[16][6];
@@ -53,7 +60,7 @@ struct Control {
   unsigned int ticket;
   unsigned int ticket2;
   int err;
-  int pad;
+  int stall_window;  // > 0: stop a load whose residual has not improved by 1% for this many iterations
 };
 
 // ---------------------------------------------------------------------------
@@ -107,18 +114,28 @@ template <> struct ResAcc<float> {
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
-// Advance the per-load state after one iteration's residual is known.
-__device__ void advance_state(LoadState& s, Control* ctl, double* hist, int load, double d2, double n2) {
+// Advance the per-load state after one iteration's residual is known:
+// r_n = sqrt(d2 / n2) (Sec. 4's Cauchy criterion), then the stop tests.
+__device__ __forceinline__ void update_state(LoadState& s, double d2, double n2, double tol, int max_iter,
+                                             int stall_window) {
   const double r = (n2 > 0.0) ? sqrt(d2 / n2) : sqrt(d2);
   s.iter += 1;
-  if (s.iter <= ctl->hist_cap) hist[(size_t)load * ctl->hist_cap + (s.iter - 1)] = r;
   if (s.iter == 1) s.r_first = r;
   s.inc = (s.iter > 1 && r > s.r) ? s.inc + 1 : 0;
   s.r = r;
+  if (s.since_best == 0 && s.r_best == 0.0) s.r_best = r;  // first step of this phase
+  if (r < 0.99 * s.r_best) { s.r_best = r; s.since_best = 0; }
+  else s.since_best += 1;
   if (!isfinite(r)) { s.status = FH_NONFINITE; s.done = 1; }
-  else if (r <= ctl->tol) { s.status = FH_OK; s.done = 1; }
+  else if (r <= tol) { s.status = FH_OK; s.done = 1; }
   else if (s.inc >= 100 || (s.iter > 10 && r > 1e6 * s.r_first && r > 1.0)) { s.status = FH_DIVERGED; s.done = 1; }
-  else if (s.iter >= ctl->max_iter) { s.status = FH_NOT_CONVERGED; s.done = 1; }
+  else if (stall_window > 0 && s.since_best >= stall_window) { s.status = kStatusStalled; s.done = 1; }
+  else if (s.iter >= max_iter) { s.status = FH_NOT_CONVERGED; s.done = 1; }
+}
+
+__device__ void advance_state(LoadState& s, Control* ctl, double* hist, int load, double d2, double n2) {
+  update_state(s, d2, n2, ctl->tol, ctl->max_iter, ctl->stall_window);
+  if (s.iter <= ctl->hist_cap) hist[(size_t)load * ctl->hist_cap + (s.iter - 1)] = s.r;
 }
 
 // ---------------------------------------------------------------------------
@@ -141,8 +158,10 @@ __global__ void __launch_bounds__(256) row_pass(GridInfo g, DevPlan plan, const 
   const int L = g.L, H = g.H;
   const int nreal = nrow * NV;
   const int npair = (nreal + 1) >> 1;
+  constexpr int PS = sizeof(T) == 4 ? 4 : 3;   // one spare slot per 128-byte wavefront
+  const int Lp = padded_len<PS>(L);
   cplx<T>* W0 = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* W1 = W0 + (size_t)((rpb * NV + 1) >> 1) * L;
+  cplx<T>* W1 = W0 + (size_t)((rpb * NV + 1) >> 1) * Lp;
   const FDiv fL = make_fdiv(L), fH = make_fdiv(H);
 
   if (threadIdx.x == 0) s_skip = st[load].done;
@@ -160,28 +179,44 @@ __global__ void __launch_bounds__(256) row_pass(GridInfo g, DevPlan plan, const 
     cplx<T>* Zo = W1;
     if (!FIRST) {
       // 1. rebuild the two-real-lines-in-one complex spectrum Z = A + i B
-      for (int idx = threadIdx.x; idx < npair * L; idx += blockDim.x) {
-        const int p = fdiv(idx, fL), k = idx - p * L;
-        const int fa = 2 * p, fb = 2 * p + 1;
-        const bool lo = k <= (L >> 1);
-        const int kk = lo ? k : L - k;
-        const int ra = fa / NV, ca = fa - ra * NV;
-        cplx<T> A = Sr[ca * cstrS + ra * H + kk];
-        cplx<T> B;
-        B.x = T(0); B.y = T(0);
-        if (fb < nreal) {
-          const int rbb = fb / NV, cb = fb - rbb * NV;
-          B = Sr[cb * cstrS + rbb * H + kk];
+      // four independent element pairs per thread are loaded before any is
+      // stored, to keep enough global loads in flight
+      constexpr int U = 4;
+      const int total = npair * L;
+      for (int base = threadIdx.x; base < total; base += U * blockDim.x) {
+        cplx<T> A[U], B[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int idx = base + u * blockDim.x;
+          A[u].x = A[u].y = B[u].x = B[u].y = T(0);
+          if (idx < total) {
+            const int p = fdiv(idx, fL), k = idx - p * L;
+            const int fa = 2 * p, fb = 2 * p + 1;
+            const int kk = k <= (L >> 1) ? k : L - k;
+            const int ra = fa / NV, ca = fa - ra * NV;
+            A[u] = Sr[ca * cstrS + ra * H + kk];
+            if (fb < nreal) {
+              const int rbb = fb / NV, cb = fb - rbb * NV;
+              B[u] = Sr[cb * cstrS + rbb * H + kk];
+            }
+          }
         }
-        if (!lo) { A.y = -A.y; B.y = -B.y; }
-        cplx<T> z;
-        z.x = A.x - B.y;
-        z.y = A.y + B.x;
-        W0[p * L + k] = z;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int idx = base + u * blockDim.x;
+          if (idx < total) {
+            const int p = fdiv(idx, fL), k = idx - p * L;
+            if (k > (L >> 1)) { A[u].y = -A[u].y; B[u].y = -B[u].y; }
+            cplx<T> z;
+            z.x = A[u].x - B[u].y;
+            z.y = A[u].y + B[u].x;
+            W0[p * Lp + padi<PS>(k)] = z;
+          }
+        }
       }
       __syncthreads();
       // 2. inverse FFT (unnormalised)
-      Z = fft_lines_pp<+1, T>(W0, W1, npair, L, plan, tw);
+      Z = fft_lines_pp<+1, T, PS>(W0, W1, npair, Lp, plan, tw);
       Zo = (Z == W0) ? W1 : W0;
     }
     // 3. pointwise: E_new, residual sums, tau = (C - C0):(E_new + eps0)
@@ -196,7 +231,7 @@ __global__ void __launch_bounds__(256) row_pass(GridInfo g, DevPlan plan, const 
         if (FIRST) {
           en[c] = ep[c * cstrE];
         } else {
-          const cplx<T> zz = Z[(f >> 1) * L + x];
+          const cplx<T> zz = Z[(f >> 1) * Lp + padi<PS>(x)];
           en[c] = ((f & 1) ? zz.y : zz.x) * scale;
           const T eo = ep[c * cstrE];
           acc_d.add_sq(en[c] - eo);
@@ -211,22 +246,22 @@ __global__ void __launch_bounds__(256) row_pass(GridInfo g, DevPlan plan, const 
 #pragma unroll
         for (int b = 0; b < NV; ++b) t += dc[a * NV + b] * (en[b] + e0[b]);
         const int f = r * NV + a;
-        if (f & 1) Z[(f >> 1) * L + x].y = t;
-        else Z[(f >> 1) * L + x].x = t;
+        if (f & 1) Z[(f >> 1) * Lp + padi<PS>(x)].y = t;
+        else Z[(f >> 1) * Lp + padi<PS>(x)].x = t;
       }
     }
     // odd number of real lines: the last pair's imaginary part is zero
     if (nreal & 1) {
-      for (int x = threadIdx.x; x < L; x += blockDim.x) Z[(npair - 1) * L + x].y = T(0);
+      for (int x = threadIdx.x; x < L; x += blockDim.x) Z[(npair - 1) * Lp + padi<PS>(x)].y = T(0);
     }
     __syncthreads();
     // 4. forward FFT
-    cplx<T>* Zf = fft_lines_pp<-1, T>(Z, Zo, npair, L, plan, tw);
+    cplx<T>* Zf = fft_lines_pp<-1, T, PS>(Z, Zo, npair, Lp, plan, tw);
     // 5. split into the two half spectra A = (Z_k + conj Z_{L-k})/2, B = (Z_k - conj Z_{L-k})/(2i)
     for (int idx = threadIdx.x; idx < npair * H; idx += blockDim.x) {
       const int p = fdiv(idx, fH), k = idx - p * H;
-      const cplx<T> zk = Zf[p * L + k];
-      const cplx<T> zm = Zf[p * L + (k == 0 ? 0 : L - k)];
+      const cplx<T> zk = Zf[p * Lp + padi<PS>(k)];
+      const cplx<T> zm = Zf[p * Lp + padi<PS>(k == 0 ? 0 : L - k)];
       cplx<T> A, B;
       A.x = T(0.5) * (zk.x + zm.x);
       A.y = T(0.5) * (zk.y - zm.y);
@@ -311,15 +346,35 @@ __global__ void __launch_bounds__(256) line_pass(GridInfo g, DevPlan plan, const
   const FDiv fW = make_fdiv(W), fN = make_fdiv(N);
   const int wlim = min(W, H - w0);
 
-  for (int idx = threadIdx.x; idx < NV * N * W; idx += blockDim.x) {
-    const int t = fdiv(idx, fW);
-    const int w = idx - t * W;
-    const int c = fdiv(t, fN);
-    const int n = t - c * N;
-    cplx<T> v;
-    v.x = T(0); v.y = T(0);
-    if (w < wlim) v = Sb[c * comp_stride + n * stride + w];
-    X0[(c * W + w) * ls + n] = v;
+  {
+    constexpr int U = 4;   // loads in flight per thread
+    const int total = NV * N * W;
+    for (int base0 = threadIdx.x; base0 < total; base0 += U * blockDim.x) {
+      cplx<T> v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = base0 + u * blockDim.x;
+        v[u].x = v[u].y = T(0);
+        if (idx < total) {
+          const int t = fdiv(idx, fW);
+          const int w = idx - t * W;
+          const int c = fdiv(t, fN);
+          const int n = t - c * N;
+          if (w < wlim) v[u] = Sb[c * comp_stride + n * stride + w];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = base0 + u * blockDim.x;
+        if (idx < total) {
+          const int t = fdiv(idx, fW);
+          const int w = idx - t * W;
+          const int c = fdiv(t, fN);
+          const int n = t - c * N;
+          X0[(c * W + w) * ls + n] = v[u];
+        }
+      }
+    }
   }
   __syncthreads();
   cplx<T>* X = X0;

@@ -108,6 +108,9 @@ struct fh_solver {
   int ntiles[2][3] = {};
   size_t line_smem[2][3] = {};
   std::vector<GraphEntry> graphs;
+  bool cl_gsmem[2][2] = {{true, true}, {true, true}};  // [fp64/fp32][cluster 8/16]: table slice in smem
+  LoadState* h_states = nullptr;                       // pinned copies read back after a phase
+  double* h_ms = nullptr;
 };
 
 namespace {
@@ -118,7 +121,8 @@ void choose_shapes(fh_solver* s, int prec) {
   const GridInfo& g = s->g;
   const int sms = 152;
   const int nl = s->nload_max;
-  auto row_smem = [&](int rpb) { return (size_t)2 * ((rpb * g.nv + 1) / 2) * g.L * csize(prec); };
+  const int Lp = prec == FH_PREC_FP64 ? fh::padded_len<3>(g.L) : fh::padded_len<4>(g.L);
+  auto row_smem = [&](int rpb) { return (size_t)2 * ((rpb * g.nv + 1) / 2) * Lp * csize(prec); };
   int rpb = 1;
   while (rpb * 2 <= g.nrows && (g.nrows * nl) / (rpb * 2) >= 2 * sms && row_smem(rpb * 2) <= 96 * 1024) rpb *= 2;
   s->rpb[prec] = rpb;
@@ -324,8 +328,14 @@ fh_status cluster_fits_nv(fh_solver* s, bool* ok) {
   *ok = false;
   const GridInfo& g = s->g;
   if (g.nd != 2) return FH_OK;
-  const fh::ClusterLayout lay = fh::cluster_layout<T>(g.dims[0], g.L, g.nv, CS);
+  bool gs = true;
+  fh::ClusterLayout lay = fh::cluster_layout<T>(g.dims[0], g.L, g.nv, CS, true);
+  if (lay.total + 1024 > kMaxSmem) {
+    gs = false;
+    lay = fh::cluster_layout<T>(g.dims[0], g.L, g.nv, CS, false);
+  }
   if (lay.total + 1024 > kMaxSmem) return FH_OK;
+  s->cl_gsmem[sizeof(T) == 8 ? 0 : 1][CS == 16 ? 1 : 0] = gs;
   auto kern = fh::cluster_solve_2d<T, NV, CS>;
   CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total));
   if (CS > 8) CK(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
@@ -357,7 +367,8 @@ fh_status cluster_fits(fh_solver* s, bool* ok) {
 template <typename T, int NV, int CS>
 fh_status launch_cluster_nv(fh_solver* s, int nload) {
   const GridInfo& g = s->g;
-  const fh::ClusterLayout lay = fh::cluster_layout<T>(g.dims[0], g.L, g.nv, CS);
+  const bool gs = s->cl_gsmem[sizeof(T) == 8 ? 0 : 1][CS == 16 ? 1 : 0];
+  const fh::ClusterLayout lay = fh::cluster_layout<T>(g.dims[0], g.L, g.nv, CS, gs);
   auto kern = fh::cluster_solve_2d<T, NV, CS>;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nload * CS);
@@ -374,7 +385,7 @@ fh_status launch_cluster_nv(fh_solver* s, int nload) {
   using C = typename fh::cplx_t<T>::type;
   CK(cudaLaunchKernelEx(&cfg, kern, g, s->ax[0].plan, s->ax[1].plan, (const C*)twp<T>(s->ax[0]),
                         (const C*)twp<T>(s->ax[1]), Eptr<T>(s), (const uint8_t*)s->phase, dCptr<T>(s), s->nphase,
-                        Gptr<T>(s), s->ctl, s->st, s->hist));
+                        Gptr<T>(s), s->ctl, s->st, s->hist, gs ? 1 : 0));
   return FH_OK;
 }
 
@@ -433,6 +444,8 @@ void free_all(fh_solver* s) {
     if (a.tw32) cudaFree(a.tw32);
   }
   if (s->h_flag) cudaFreeHost(s->h_flag);
+  if (s->h_states) cudaFreeHost(s->h_states);
+  if (s->h_ms) cudaFreeHost(s->h_ms);
   if (s->ev0) cudaEventDestroy(s->ev0);
   if (s->ev1) cudaEventDestroy(s->ev1);
   if (s->ev_user) cudaEventDestroy(s->ev_user);
@@ -496,6 +509,8 @@ fh_status profile_passes(fh_solver* s, int prec, int nload, int reps, double* ms
   CK(cudaMemcpyAsync(&s->ctl->tol, &zero, sizeof(double), cudaMemcpyHostToDevice, s->work));
   CK(cudaMemcpyAsync(&s->ctl->max_iter, &big, sizeof(int), cudaMemcpyHostToDevice, s->work));
   CK(cudaMemcpyAsync(&s->ctl->nload, &nload, sizeof(int), cudaMemcpyHostToDevice, s->work));
+  const int no_stall = 0;
+  CK(cudaMemcpyAsync(&s->ctl->stall_window, &no_stall, sizeof(int), cudaMemcpyHostToDevice, s->work));
   const GridInfo& g = s->g;
   using C = typename fh::cplx_t<T>::type;
   C* S = reinterpret_cast<C*>(s->S);
@@ -687,6 +702,8 @@ fh_status fh_solver_create(const fh_pattern* p, const fh_generator* gen, int nlo
   CKS(cudaMalloc(&s->mstress, FH_MAX_LOADS * fh::MAXV * sizeof(double)));
   CKS(cudaMalloc(&s->err, sizeof(int)));
   CKS(cudaMallocHost(&s->h_flag, sizeof(int)));
+  CKS(cudaMallocHost(&s->h_states, FH_MAX_LOADS * sizeof(LoadState)));
+  CKS(cudaMallocHost(&s->h_ms, FH_MAX_LOADS * fh::MAXV * sizeof(double)));
   CKS(cudaMemset(s->ctl, 0, sizeof(Control)));
   CKS(cudaMemset(s->st, 0, FH_MAX_LOADS * sizeof(LoadState)));
   CKS(cudaMemset(s->err, 0, sizeof(int)));
@@ -830,6 +847,7 @@ fh_status fh_set_reference(fh_solver* s, const double* C0) {
 namespace {
 
 struct PhaseOut {
+  int nload = 0;
   LoadState hs[FH_MAX_LOADS];
   double ms[FH_MAX_LOADS * fh::MAXV];
   float elapsed = 0.f;
@@ -837,12 +855,19 @@ struct PhaseOut {
   int path = 1, cs = 0;
 };
 
-// One run of the fixed point in one precision.  `start` (may be null) gives the
-// per-load state to continue from; otherwise every load starts at iteration 0.
-fh_status solve_phase(fh_solver* s, int nload, const double* eps0, double tol, int max_iter, int prec, int init,
-                      int chunk, int want_path, int want_cs, const LoadState* start, PhaseOut* out) {
+// One run of the fixed point in one precision, in two halves so that a batch
+// of solvers can have their cluster-resident solves in flight together.
+// begin_phase enqueues the work; for the cluster path it returns without
+// waiting (the results are copied to pinned host memory on the solver's
+// stream), for the pass path it runs the host-driven loop to completion.
+// end_phase waits for the solver's stream and collects the results.
+// `start` (may be null) gives the per-load state to continue from.
+fh_status begin_phase(fh_solver* s, int nload, const double* eps0, double tol, int max_iter, int prec, int init,
+                      int chunk, int want_path, int want_cs, const LoadState* start, PhaseOut* out,
+                      int stall_window = 0) {
   const int nv = s->g.nv;
   Control h{};
+  h.stall_window = stall_window;
   for (int l = 0; l < nload; ++l)
     for (int c = 0; c < nv; ++c) h.eps0[l][c] = eps0[l * nv + c];
   h.tol = tol;
@@ -873,18 +898,38 @@ fh_status solve_phase(fh_solver* s, int nload, const double* eps0, double tol, i
     rc = prec == FH_PREC_FP64 ? run_solve<double>(s, prec, nload, chunk, max_iter, &out->launches)
                               : run_solve<float>(s, prec, nload, chunk, max_iter, &out->launches);
   if (rc != FH_OK) return rc;
-  CK(cudaMemcpyAsync(out->hs, s->st, sizeof(LoadState) * nload, cudaMemcpyDeviceToHost, s->work));
-  CK(cudaMemcpyAsync(out->ms, s->mstress, sizeof(double) * nload * fh::MAXV, cudaMemcpyDeviceToHost, s->work));
+  CK(cudaMemcpyAsync(s->h_states, s->st, sizeof(LoadState) * nload, cudaMemcpyDeviceToHost, s->work));
+  CK(cudaMemcpyAsync(s->h_ms, s->mstress, sizeof(double) * nload * fh::MAXV, cudaMemcpyDeviceToHost, s->work));
+  out->nload = nload;
+  return FH_OK;
+}
+
+fh_status end_phase(fh_solver* s, PhaseOut* out) {
   CK(cudaStreamSynchronize(s->work));
+  std::memcpy(out->hs, s->h_states, sizeof(LoadState) * out->nload);
+  std::memcpy(out->ms, s->h_ms, sizeof(double) * out->nload * fh::MAXV);
   CK(cudaEventElapsedTime(&out->elapsed, s->ev0, s->ev1));
   return FH_OK;
+}
+
+fh_status solve_phase(fh_solver* s, int nload, const double* eps0, double tol, int max_iter, int prec, int init,
+                      int chunk, int want_path, int want_cs, const LoadState* start, PhaseOut* out,
+                      int stall_window = 0) {
+  fh_status rc = begin_phase(s, nload, eps0, tol, max_iter, prec, init, chunk, want_path, want_cs, start, out,
+                             stall_window);
+  if (rc != FH_OK) return rc;
+  return end_phase(s, out);
 }
 
 }  // namespace
 
 extern "C" {
 
-fh_status fh_solve(fh_solver* s, int nload, const double* eps0, const fh_solve_opts* opts, fh_result* res) {
+}  // extern "C"
+
+namespace {
+
+fh_status validate_solve(fh_solver* s, int nload, const double* eps0, const fh_solve_opts* opts) {
   if (!s || !eps0 || !opts) { fh::set_error("null argument"); return FH_ERR_ARG; }
   if (!s->have_table) { fh::set_error("set stiffness and reference medium first"); return FH_ERR_STATE; }
   if (nload < 1 || nload > s->nload_max) { fh::set_error("nload out of range"); return FH_ERR_ARG; }
@@ -898,34 +943,38 @@ fh_status fh_solve(fh_solver* s, int nload, const double* eps0, const fh_solve_o
     fh::set_error("path must be 0..2 and cluster 0, 8 or 16");
     return FH_ERR_ARG;
   }
-  const int nv = s->g.nv;
-  for (int i = 0; i < nload * nv; ++i)
+  for (int i = 0; i < nload * s->g.nv; ++i)
     if (!std::isfinite(eps0[i])) { fh::set_error("non-finite eps0"); return FH_ERR_ARG; }
-  const int chunk = opts->chunk > 0 ? std::min(opts->chunk, 1024) : 32;
-  fh_status rc = join_user(s);
-  if (rc != FH_OK) return rc;
-  PhaseOut A;
-  const int prec1 = opts->precision == FH_PREC_FP64 ? FH_PREC_FP64 : FH_PREC_FP32;
-  rc = solve_phase(s, nload, eps0, opts->tol, opts->max_iter, prec1, opts->init, chunk, opts->path, opts->cluster,
-                   nullptr, &A);
-  if (rc != FH_OK) return rc;
-  PhaseOut* fin = &A;
-  PhaseOut B;
-  if (opts->precision == FH_PREC_MIXED) {
-    // one FP64 iteration from the FP32 iterate: every load continues its count
-    // and stops after exactly one step (tolerance set to +inf for this phase)
-    LoadState st0[FH_MAX_LOADS];
-    for (int l = 0; l < nload; ++l) {
-      st0[l] = A.hs[l];
-      st0[l].done = 0;
-      st0[l].inc = 0;
-    }
-    rc = solve_phase(s, nload, eps0, HUGE_VAL, 0x7fffffff, FH_PREC_FP64, 1, chunk, opts->path, opts->cluster, st0, &B);
-    if (rc != FH_OK) return rc;
-    for (int l = 0; l < nload; ++l) B.hs[l].status = A.hs[l].status;
-    B.elapsed += A.elapsed;
-    B.launches += A.launches;
-    fin = &B;
+  return FH_OK;
+}
+
+int chunk_of(const fh_solve_opts* opts) { return opts->chunk > 0 ? std::min(opts->chunk, 1024) : 32; }
+
+// start states of the FP64 step of the mixed mode: continue every load's count
+void polish_start(const PhaseOut& A, LoadState* st0) {
+  for (int l = 0; l < A.nload; ++l) {
+    st0[l] = A.hs[l];
+    st0[l].done = 0;
+    st0[l].inc = 0;
+    st0[l].r_best = 0.0;
+    st0[l].since_best = 0;
+    st0[l].status = 0;
+  }
+}
+
+// mixed mode: the FP32 phase stops a load whose residual has not improved by 1%
+// for this many iterations (its FP32 rounding floor), and the FP64 phase
+// continues every load until its FP64 Cauchy residual meets the tolerance
+constexpr int kStallWindow = 50;
+
+fh_status finish_solve(fh_solver* s, int nload, const double* eps0, const PhaseOut& A, PhaseOut* B, bool mixed,
+                       fh_result* res) {
+  const int nv = s->g.nv;
+  const PhaseOut* fin = &A;
+  if (mixed) {
+    B->elapsed += A.elapsed;
+    B->launches += A.launches;
+    fin = B;
   }
   fh_status worst = FH_OK;
   auto rank = [](int st) { return st == FH_NONFINITE ? 3 : st == FH_DIVERGED ? 2 : st == FH_NOT_CONVERGED ? 1 : 0; };
@@ -953,6 +1002,82 @@ fh_status fh_solve(fh_solver* s, int nload, const double* eps0, const fh_solve_o
   }
   s->last_nload = nload;
   s->have_solution = true;
+  return worst;
+}
+
+int status_rank(fh_status st) {
+  return st == FH_NONFINITE ? 3 : st == FH_DIVERGED ? 2 : st == FH_NOT_CONVERGED ? 1 : 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+fh_status fh_solve(fh_solver* s, int nload, const double* eps0, const fh_solve_opts* opts, fh_result* res) {
+  fh_status rc = validate_solve(s, nload, eps0, opts);
+  if (rc != FH_OK) return rc;
+  rc = join_user(s);
+  if (rc != FH_OK) return rc;
+  const int chunk = chunk_of(opts);
+  const bool mixed = opts->precision == FH_PREC_MIXED;
+  const int prec1 = opts->precision == FH_PREC_FP64 ? FH_PREC_FP64 : FH_PREC_FP32;
+  PhaseOut A, B;
+  rc = solve_phase(s, nload, eps0, opts->tol, opts->max_iter, prec1, opts->init, chunk, opts->path, opts->cluster,
+                   nullptr, &A, mixed ? kStallWindow : 0);
+  if (rc != FH_OK) return rc;
+  if (mixed) {
+    LoadState st0[FH_MAX_LOADS];
+    polish_start(A, st0);
+    rc = solve_phase(s, nload, eps0, opts->tol, opts->max_iter, FH_PREC_FP64, 1, chunk, opts->path, opts->cluster,
+                     st0, &B);
+    if (rc != FH_OK) return rc;
+  }
+  return finish_solve(s, nload, eps0, A, &B, mixed, res);
+}
+
+fh_status fh_solve_batch(fh_solver* const* solvers, int n, const int* nload, const double* const* eps0,
+                         const fh_solve_opts* opts, fh_result* res) {
+  if (!solvers || !nload || !eps0 || !opts || n < 1) { fh::set_error("null argument or empty batch"); return FH_ERR_ARG; }
+  for (int i = 0; i < n; ++i) {
+    fh_status rc = validate_solve(solvers[i], nload[i], eps0[i], opts);
+    if (rc != FH_OK) return rc;
+    for (int j = 0; j < i; ++j)
+      if (solvers[j] == solvers[i]) { fh::set_error("a solver appears twice in the batch"); return FH_ERR_ARG; }
+  }
+  const int chunk = chunk_of(opts);
+  const bool mixed = opts->precision == FH_PREC_MIXED;
+  const int prec1 = opts->precision == FH_PREC_FP64 ? FH_PREC_FP64 : FH_PREC_FP32;
+  std::vector<PhaseOut> A(n), B(n);
+  // phase 1: every solver's work is enqueued before any is waited for
+  for (int i = 0; i < n; ++i) {
+    fh_status rc = join_user(solvers[i]);
+    if (rc != FH_OK) return rc;
+    rc = begin_phase(solvers[i], nload[i], eps0[i], opts->tol, opts->max_iter, prec1, opts->init, chunk, opts->path,
+                     opts->cluster, nullptr, &A[i], mixed ? kStallWindow : 0);
+    if (rc != FH_OK) return rc;
+  }
+  for (int i = 0; i < n; ++i) {
+    fh_status rc = end_phase(solvers[i], &A[i]);
+    if (rc != FH_OK) return rc;
+  }
+  if (mixed) {
+    for (int i = 0; i < n; ++i) {
+      LoadState st0[FH_MAX_LOADS];
+      polish_start(A[i], st0);
+      fh_status rc = begin_phase(solvers[i], nload[i], eps0[i], opts->tol, opts->max_iter, FH_PREC_FP64, 1, chunk,
+                                 opts->path, opts->cluster, st0, &B[i]);
+      if (rc != FH_OK) return rc;
+    }
+    for (int i = 0; i < n; ++i) {
+      fh_status rc = end_phase(solvers[i], &B[i]);
+      if (rc != FH_OK) return rc;
+    }
+  }
+  fh_status worst = FH_OK;
+  for (int i = 0; i < n; ++i) {
+    fh_status st = finish_solve(solvers[i], nload[i], eps0[i], A[i], &B[i], mixed, res ? &res[i] : nullptr);
+    if (status_rank(st) > status_rank(worst)) worst = st;
+  }
   return worst;
 }
 

@@ -273,3 +273,71 @@ def test_mixed_mode_continues_the_iteration_count(fh):
     assert list(b["iterations"]) == [i + 1 for i in a["iterations"]]
     h = s.get_residuals(0)
     assert len(h) == b["iterations"][0]
+
+
+def _sampled_iteration_check(fh, w, loads, n_prev, nsample, seed, tol):
+    """One GPU iteration checked at sampled frequencies against the oracle.
+
+    The GPU runs n_prev iterations (E_prev), then one more (E_next).  On the CPU,
+    tau = (C - C0):(E_prev + eps0) is built with the oracle's own materials,
+    transformed with numpy's FFT on the oracle's Smith grid, and the oracle's
+    Gamma^p evaluated one frequency at a time at `nsample` random frequencies h
+    predicts E^_next(h) = -Gamma^p_h tau^(h) (Eq. (pde_coefficients)), compared
+    with the FFT of the GPU's E_next there."""
+    from oracle import green as OGr, scheme as OS
+    case = Case.from_workload(w)   # oracle-side materials, generator, SNF grid (no table)
+    s = case.product(fh)
+    T = case.T
+    rng = np.random.default_rng(seed)
+    picks = rng.choice(T.m, size=nsample, replace=False)
+    picks = picks[np.any(T.freqs[picks] != 0, axis=1)]
+    Gp = np.stack([OGr.gamma_p(case.M, case.gen_o, case.C0_o, T.freqs[f]) for f in picks])
+    dC = case.Cp_o[case.ids] - case.C0_o[None]
+    inv = np.argsort(case.perm)            # oracle index -> product index
+    worst = 0.0
+    s.solve(case.eps0, tol=0.0, max_iter=n_prev)
+    prev = {L: s.get_strain(L)[:, inv].T.copy() for L in loads}   # (m, nv) oracle order
+    s.solve(case.eps0, tol=0.0, max_iter=1, init=1)
+    for L in loads:
+        nxt = s.get_strain(L)[:, inv].T
+        tau = np.einsum("mab,mb->ma", dC, prev[L] + case.eps0[L][None])
+        tau_h = T.fwd(tau.astype(complex))[picks]
+        pred = -np.einsum("hab,hb->ha", Gp, tau_h)
+        got = T.fwd(nxt.astype(complex))[picks]
+        worst = max(worst, np.abs(pred - got).max() / np.abs(got).max())
+    assert worst < tol, worst
+
+
+def test_full_size_box3d_iteration_sampled(fh):
+    """M = diag(128,128,128), box spline of order 2 with alias radius 4 (729 aliases),
+    50 spheres at contrast 50, 6 loads: one FP64 iteration at 300 sampled frequencies."""
+    _sampled_iteration_check(fh, W.box3d(), loads=[0, 4], n_prev=3, nsample=300, seed=7, tol=1e-10)
+
+
+def test_full_size_fno3d_iteration_sampled(fh):
+    """M = diag(64,64,64), Dirichlet kernel, random spheres: one FP64 iteration sampled."""
+    _sampled_iteration_check(fh, W.fno3d_item(100000), loads=[1, 5], n_prev=4, nsample=300, seed=8,
+                             tol=1e-10)
+
+
+def test_full_size_box3d_properties(fh):
+    """Converged (mixed mode, r <= 1e-6) 128^3 solve: zero-mean strain fluctuation,
+    symmetric C_eff, positive definite C_eff between Reuss and Voigt bounds of the
+    sampled phases within the discretisation's tolerance."""
+    w = W.box3d()
+    case = Case.from_workload(w)
+    s = case.product(fh)
+    out = s.solve(case.eps0, tol=1e-6, max_iter=5000, precision=fh.FH_PREC_MIXED)
+    assert out["status"] == 0
+    for L in (0, 3):
+        E = s.get_strain(L)
+        assert np.abs(E.mean(axis=1)).max() < 1e-9
+    C = s.get_ceff()
+    assert rel(C, C.T) < 1e-6
+    assert np.linalg.eigvalsh(0.5 * (C + C.T)).min() > 0
+    Cp = case.Cp_o[case.ids]
+    voigt = Cp.mean(axis=0)
+    reuss = np.linalg.inv(np.linalg.inv(Cp).mean(axis=0))
+    Cs = 0.5 * (C + C.T)
+    assert np.linalg.eigvalsh(voigt - Cs).min() > -1e-3 * np.abs(voigt).max()
+    assert np.linalg.eigvalsh(Cs - reuss).min() > -1e-3 * np.abs(voigt).max()
