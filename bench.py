@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-cluster", type=int, default=0)
     return ap.parse_args()
 
 
@@ -166,6 +168,17 @@ class Clocks:
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def reduce_over_ranks(dist, total_ms, vox, device):
+    """Whole-job numbers of independent replicas: the slowest rank's time and the
+    voxel-iterations of all ranks (no collective touches the solver's data)."""
+    import torch
+    t = torch.tensor([float(total_ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    v = torch.tensor([float(vox)], device=device, dtype=torch.float64)
+    dist.all_reduce(v, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(v.item())
+
+
 def ceff_reference():
     path = os.path.join(ROOT, "tests", "golden", "ceff_dlvp_sheared.txt")
     return np.loadtxt(path) if os.path.exists(path) else None
@@ -244,12 +257,7 @@ def run_gpu(args, rank, world, local_rank):
             clocks = clocks.stop()
         total_ms = float(np.sum(times))
         if dist:
-            t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
-            v = torch.tensor([float(vox)], device="cuda", dtype=torch.float64)
-            dist.all_reduce(v, op=dist.ReduceOp.SUM)
-            vox = int(v.item())
+            total_ms, vox = reduce_over_ranks(dist, total_ms, vox, "cuda")
         ce = s.get_ceff()
         results[mode] = {"value": vox / (total_ms * 1e-3), "ms_per_step": total_ms / args.steps,
                          "iterations": [int(x) for x in iters], "gpu_launches": launches,
@@ -308,6 +316,58 @@ def run_gpu(args, rank, world, local_rank):
     return results, e2e, roofline, clocks
 
 
+def run_batched(fh, steps, cluster):
+    """The batched workload: 512 seeded two-phase 2-D microstructures with N in
+    {64,96,128,192,256} (half diagonal, half sheared M), 3 loads each, mixed
+    precision to r <= 1e-6, solved with one fh_solve_batch call per step;
+    compared with solving the same solvers one after another."""
+    import torch
+    solvers, ms = [], []
+    t0 = time.perf_counter()
+    for i in range(512):
+        w = W.batch2d_item(i)
+        p = fh.Pattern(w["M"])
+        ids = W.phase_ids(p.points(), w["centres"], w["radii"])
+        Cp = np.stack([fh.isotropic_stiffness(*fh.lame(E, nu), 2) for E, nu in w["phases"]])
+        s = fh.Solver(p, fh.generator("dirichlet"), 3, torch.cuda.current_stream().cuda_stream)
+        s.set_stiffness_phases(ids, Cp)
+        s.set_reference(None)
+        solvers.append(s)
+        ms.append(p.m)
+    setup = time.perf_counter() - t0
+    eps = [np.eye(3)] * len(solvers)
+    fh.solve_batch(solvers, eps, tol=1e-6, precision=fh.FH_PREC_MIXED, cluster=cluster)   # warm-up
+    torch.cuda.synchronize()
+    times, vox, launches = [], 0, 0
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        rc, outs = fh.solve_batch(solvers, eps, tol=1e-6, precision=fh.FH_PREC_MIXED, cluster=cluster)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        vox += sum(m * int(np.sum(o["iterations"])) for m, o in zip(ms, outs))
+        launches += sum(o["kernel_launches"] + 1 for o in outs)
+    t0 = time.perf_counter()
+    seq_vox = 0
+    for s, m in zip(solvers, ms):
+        o = s.solve(np.eye(3), tol=1e-6, max_iter=20000, precision=fh.FH_PREC_MIXED, cluster=cluster)
+        seq_vox += m * int(np.sum(o["iterations"]))
+    torch.cuda.synchronize()
+    seq = time.perf_counter() - t0
+    paths = {}
+    for o in outs:
+        k = f"path{o['path']}/cluster{o['cluster']}"
+        paths[k] = paths.get(k, 0) + 1
+    for s in solvers:
+        s.close()
+    return {"workload": "batch2d: 512 microstructures, N in {64,96,128,192,256}, diag and sheared M, "
+                        "Dirichlet, contrast log-U[5,200], 3 loads each, mixed precision, tol 1e-6",
+            "value": vox / sum(times), "unit": UNIT, "ms_per_step": 1e3 * sum(times) / steps, "steps": steps,
+            "points": int(sum(ms)), "status": int(rc), "launch_configs": paths,
+            "sequential_value": seq_vox / seq, "sequential_ms": 1e3 * seq, "setup_s": setup,
+            "timing": "host wall clock around fh_solve_batch (synchronous), L2 not flushed (1.6 M points x 3 "
+                      "loads, working set > L2)", "gpu_launches": launches}
+
+
 def measured_fp_peak(mode):
     """Dense peak of the arithmetic type measured here with cuBLAS (DGEMM / SGEMM without TF32)."""
     import torch
@@ -351,6 +411,10 @@ def main():
     from paper_1701_04685_gb300 import build
     build.build()
     results, e2e, roofline, clocks = run_gpu(args, rank, world, local_rank)
+    batched = None
+    if not args.no_batched:
+        import paper_1701_04685_gb300 as fh
+        batched = run_batched(fh, min(args.steps, 3), args.batch_cluster)
     if rank != 0:
         return
     cpu = None
@@ -369,6 +433,7 @@ def main():
                    "iterations_per_load": head["iterations"]},
         "time_to_tol_ms": head["ms_per_step"],
         "modes": results,
+        "batched": batched,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -114,6 +114,21 @@ typedef struct {
                       runs every iteration in one launch).  Automatic picks 2
                       when the fields fit, else 1.                            */
   int cluster;     /* cluster size for path 2: 0 = automatic, 8 or 16        */
+  int form;        /* 0: the Lippmann-Schwinger discretisation, Eq.
+                      (pde_coefficients) of Thm. pde_discretization:
+                      E <- -Gamma^p (C - C0)(E + eps0).
+                      1: the variational discretisation, Eq.
+                      (pde_coefficients_variational) of Thm.
+                      ls_discretization, whose fixed point solves
+                      C0 Gamma^p C (E + eps0) = 0: E <- E - Gamma^p C (E + eps0).
+                      The two coincide for the Dirichlet kernel only (Remark
+                      constants).                                            */
+  int tune;        /* 1 with path = cluster = 0 and init = 0: on the first such
+                      solve of each bulk precision, time every eligible launch
+                      configuration (passes; clusters of 8 and 16) for 24
+                      iterations of these loads and use the fastest from then
+                      on (see fh_get_tuning).  The trials overwrite the
+                      strain before the actual solve starts from E = 0.      */
 } fh_solve_opts;
 
 typedef struct {
@@ -224,6 +239,12 @@ fh_status fh_get_ceff(const fh_solver* s, double* Ceff, int voigt);
  * matrix for every stored half-spectrum frequency (order of
  * fh_pattern_half_freqs). */
 fh_status fh_get_green(const fh_solver* s, double* G);
+
+/* Autotuner result for a bulk precision (FH_PREC_FP64 or FH_PREC_FP32): the
+ * chosen path (0 = not tuned yet) and cluster size, and the measured
+ * microseconds per iteration of [passes, cluster 8, cluster 16] (-1 where a
+ * configuration does not fit); us_per_iter may be NULL. */
+fh_status fh_get_tuning(const fh_solver* s, int precision, int* path, int* cluster, float* us_per_iter);
 
 /* Residual history r_1..r_n of one load from the last solve: hist[n] host;
  * *n receives the count (hist may be NULL to query it). */

@@ -44,7 +44,8 @@ class fh_generator(C.Structure):
 
 class fh_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("precision", C.c_int),
-                ("init", C.c_int), ("chunk", C.c_int), ("path", C.c_int), ("cluster", C.c_int)]
+                ("init", C.c_int), ("chunk", C.c_int), ("path", C.c_int), ("cluster", C.c_int),
+                ("form", C.c_int), ("tune", C.c_int)]
 
 
 class fh_result(C.Structure):
@@ -84,6 +85,7 @@ def library():
             "fh_get_residuals": (I, [P, I, P, P]),
             "fh_profile_passes": (I, [P, I, I, I, P]),
             "fh_solve_batch": (I, [P, I, P, P, C.POINTER(fh_solve_opts), P]),
+            "fh_get_tuning": (I, [P, I, P, P, P]),
             "fh_status_string": (C.c_char_p, [I]),
             "fh_last_error": (C.c_char_p, []),
         }
@@ -101,7 +103,8 @@ def exported_symbols():
             "fh_pattern_numerators", "fh_pattern_half_freqs", "fh_solver_create", "fh_solver_destroy",
             "fh_set_stiffness_phases", "fh_set_reference", "fh_solve", "fh_get_strain", "fh_set_strain",
             "fh_get_ceff", "fh_get_green", "fh_get_residuals", "fh_profile_passes", "fh_status_string",
-            "fh_last_error", "fh_mean_stress_noalloc", "fh_solve_batch"]
+            "fh_last_error", "fh_mean_stress_noalloc", "fh_solve_batch",
+            "fh_get_tuning"]
 
 
 def _check(rc, ok=(FH_OK,)):
@@ -250,11 +253,14 @@ class Solver:
             C0 = np.ascontiguousarray(np.asarray(C0, dtype=np.float64))
             _check(library().fh_set_reference(self._h, _ptr(C0)))
 
-    def solve(self, eps0, tol=1e-8, max_iter=1000, precision=FH_PREC_FP64, init=0, chunk=0, path=0, cluster=0):
-        """path: 0 automatic, 1 whole-GPU passes, 2 cluster-resident (2-axis grids)."""
+    def solve(self, eps0, tol=1e-8, max_iter=1000, precision=FH_PREC_FP64, init=0, chunk=0, path=0, cluster=0,
+              form=0, tune=0):
+        """path: 0 automatic, 1 whole-GPU passes, 2 cluster-resident (2-axis grids);
+        form: 0 Eq. (pde_coefficients), 1 the variational discretisation;
+        tune: 1 picks path and cluster size by timing them (see fh_get_tuning)."""
         eps0 = np.ascontiguousarray(np.atleast_2d(np.asarray(eps0, dtype=np.float64)))
         opts = fh_solve_opts(float(tol), int(max_iter), int(precision), int(init), int(chunk), int(path),
-                             int(cluster))
+                             int(cluster), int(form), int(tune))
         res = fh_result()
         rc = library().fh_solve(self._h, eps0.shape[0], _ptr(eps0), C.byref(opts), C.byref(res))
         _check(rc, ok=(FH_OK, FH_NOT_CONVERGED, FH_DIVERGED, FH_NONFINITE))
@@ -294,6 +300,12 @@ class Solver:
         _check(library().fh_get_green(self._h, _ptr(out)))
         return out
 
+    def get_tuning(self, precision):
+        path, cl = C.c_int(), C.c_int()
+        us = (C.c_float * 3)()
+        _check(library().fh_get_tuning(self._h, int(precision), C.byref(path), C.byref(cl), us))
+        return {"path": path.value, "cluster": cl.value, "us_per_iter": list(us)}
+
     def get_residuals(self, load):
         n = C.c_int()
         _check(library().fh_get_residuals(self._h, int(load), None, C.byref(n)))
@@ -310,14 +322,16 @@ class Solver:
 
 
 def solve_batch(solvers, eps0s, tol=1e-6, max_iter=20000, precision=FH_PREC_MIXED, init=0, chunk=0, path=0,
-                cluster=0):
-    """fh_solve_batch over a list of Solver objects; eps0s[i] is solver i's (n_L, n_v) strains."""
+                cluster=0, form=0):
+    """fh_solve_batch over Solver objects; eps0s[i] is solver i's (n_L, n_v) strains.  With path and
+    cluster automatic, solvers tuned before (Solver.solve(..., tune=1)) keep their tuned choice."""
     n = len(solvers)
     hs = (C.c_void_p * n)(*[sv._h.value for sv in solvers])
     e0 = [np.ascontiguousarray(np.atleast_2d(np.asarray(e, dtype=np.float64))) for e in eps0s]
     nl = (C.c_int * n)(*[e.shape[0] for e in e0])
     ptrs = (C.c_void_p * n)(*[e.ctypes.data for e in e0])
-    opts = fh_solve_opts(float(tol), int(max_iter), int(precision), int(init), int(chunk), int(path), int(cluster))
+    opts = fh_solve_opts(float(tol), int(max_iter), int(precision), int(init), int(chunk), int(path), int(cluster),
+                         int(form), 0)
     res = (fh_result * n)()
     rc = library().fh_solve_batch(hs, n, nl, ptrs, C.byref(opts), res)
     _check(rc, ok=(FH_OK, FH_NOT_CONVERGED, FH_DIVERGED, FH_NONFINITE))

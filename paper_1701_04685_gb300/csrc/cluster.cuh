@@ -147,6 +147,7 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
   const double tol = ctl->tol;
   const int max_iter = ctl->max_iter;
   const int stall_window = ctl->stall_window;
+  const bool incremental = ctl->form == 1;
   const T scale = (T)g.inv_m;
   __syncthreads();
 
@@ -186,6 +187,7 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
         if (with_inverse) {
           const cplx<T> zz = Z[(f >> 1) * Lp + padi<PS>(x)];
           en[c] = ((f & 1) ? zz.y : zz.x) * scale;
+          if (incremental) en[c] += *ep;
           acc_d.add_sq(en[c] - *ep);
           acc_n.add_sq(en[c] + e0[c]);
           *ep = en[c];

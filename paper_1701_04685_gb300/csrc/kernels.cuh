@@ -61,6 +61,9 @@ struct Control {
   unsigned int ticket2;
   int err;
   int stall_window;  // > 0: stop a load whose residual has not improved by 1% for this many iterations
+  int form;          // 0: Eq. (pde_coefficients), E <- -Gamma^p (C - C0)(E + eps0)
+                     // 1: Eq. (pde_coefficients_variational), E <- E - Gamma^p C (E + eps0)
+  int pad2;
 };
 
 // ---------------------------------------------------------------------------
@@ -220,7 +223,9 @@ __global__ void __launch_bounds__(256) row_pass(GridInfo g, DevPlan plan, const 
       Zo = (Z == W0) ? W1 : W0;
     }
     // 3. pointwise: E_new, residual sums, tau = (C - C0):(E_new + eps0)
+    //    (variational form: E_new = E_old + update, tau = C:(E_new + eps0))
     const T scale = (T)g.inv_m;
+    const bool incremental = ctl->form == 1;
     for (int idx = threadIdx.x; idx < nrow * L; idx += blockDim.x) {
       const int r = fdiv(idx, fL), x = idx - r * L;
       T* ep = Eb + r * L + x;
@@ -234,6 +239,7 @@ __global__ void __launch_bounds__(256) row_pass(GridInfo g, DevPlan plan, const 
           const cplx<T> zz = Z[(f >> 1) * Lp + padi<PS>(x)];
           en[c] = ((f & 1) ? zz.y : zz.x) * scale;
           const T eo = ep[c * cstrE];
+          if (incremental) en[c] += eo;
           acc_d.add_sq(en[c] - eo);
           acc_n.add_sq(en[c] + e0[c]);
           ep[c * cstrE] = en[c];

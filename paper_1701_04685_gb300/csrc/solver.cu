@@ -77,6 +77,12 @@ struct fh_solver {
   double* Cp64 = nullptr;
   double* dC64 = nullptr;
   float* dC32 = nullptr;
+  float* Cp32 = nullptr;
+  int form = 0;  // iteration form of the solve in progress (0 or 1)
+  // autotuned (path, cluster size) per bulk precision [fp64, fp32]; path 0 = not tuned yet
+  int tuned_path[2] = {0, 0};
+  int tuned_cs[2] = {0, 0};
+  float tuned_us[2][3] = {};  // per-iteration time of the candidates: passes, cluster 8, cluster 16
   double* G64 = nullptr;
   float* G32 = nullptr;
   Control* ctl = nullptr;
@@ -159,12 +165,14 @@ double* Eptr<double>(fh_solver* s) { return s->E64; }
 template <>
 float* Eptr<float>(fh_solver* s) { return s->E32; }
 
+// stiffness table of the pointwise stage: C - C0 for Eq. (pde_coefficients),
+// C itself for the variational form
 template <typename T>
 const T* dCptr(fh_solver* s);
 template <>
-const double* dCptr<double>(fh_solver* s) { return s->dC64; }
+const double* dCptr<double>(fh_solver* s) { return s->form == 1 ? s->Cp64 : s->dC64; }
 template <>
-const float* dCptr<float>(fh_solver* s) { return s->dC32; }
+const float* dCptr<float>(fh_solver* s) { return s->form == 1 ? s->Cp32 : s->dC32; }
 
 template <typename T>
 const T* Gptr(fh_solver* s);
@@ -435,7 +443,7 @@ fh_status run_solve_cluster(fh_solver* s, int nload, int cs, long long* launches
 void free_all(fh_solver* s) {
   for (auto& e : s->graphs) cudaGraphExecDestroy(e.exec);
   s->graphs.clear();
-  void* ptrs[] = {s->E64, s->E32, s->S, s->phase, s->Cp64, s->dC64, s->dC32, s->G64, s->G32, s->ctl, s->st,
+  void* ptrs[] = {s->E64, s->E32, s->S, s->phase, s->Cp64, s->dC64, s->dC32, s->Cp32, s->G64, s->G32, s->ctl, s->st,
                   s->partials, s->partials2, s->hist, s->mstress, s->err, s->scratch64};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -691,6 +699,7 @@ fh_status fh_solver_create(const fh_pattern* p, const fh_generator* gen, int nlo
   CKS(cudaMalloc(&s->Cp64, kMaxPhases * 36 * sizeof(double)));
   CKS(cudaMalloc(&s->dC64, kMaxPhases * 36 * sizeof(double)));
   CKS(cudaMalloc(&s->dC32, kMaxPhases * 36 * sizeof(float)));
+  CKS(cudaMalloc(&s->Cp32, kMaxPhases * 36 * sizeof(float)));
   CKS(cudaMalloc(&s->G64, (size_t)g.ntri * g.nhalf * sizeof(double)));
   CKS(cudaMalloc(&s->G32, (size_t)g.ntri * g.nhalf * sizeof(float)));
   CKS(cudaMalloc(&s->ctl, sizeof(Control)));
@@ -764,6 +773,9 @@ fh_status fh_set_stiffness_phases(fh_solver* s, const uint8_t* phase, int nphase
   s->nphase = nphase;
   std::memcpy(s->Cp, Cp, sizeof(double) * nphase * nv * nv);
   CK(cudaMemcpy(s->Cp64, s->Cp, sizeof(double) * nphase * nv * nv, cudaMemcpyHostToDevice));
+  float cpf[kMaxPhases * 36];
+  for (int q = 0; q < nphase * nv * nv; ++q) cpf[q] = (float)s->Cp[q];
+  CK(cudaMemcpy(s->Cp32, cpf, sizeof(float) * nphase * nv * nv, cudaMemcpyHostToDevice));
   s->have_phases = true;
   s->have_table = false;
   return FH_OK;
@@ -868,6 +880,7 @@ fh_status begin_phase(fh_solver* s, int nload, const double* eps0, double tol, i
   const int nv = s->g.nv;
   Control h{};
   h.stall_window = stall_window;
+  h.form = s->form;
   for (int l = 0; l < nload; ++l)
     for (int c = 0; c < nv; ++c) h.eps0[l][c] = eps0[l * nv + c];
   h.tol = tol;
@@ -939,6 +952,8 @@ fh_status validate_solve(fh_solver* s, int nload, const double* eps0, const fh_s
     return FH_ERR_ARG;
   }
   if (opts->init != 0 && opts->init != 1) { fh::set_error("init must be 0 or 1"); return FH_ERR_ARG; }
+  if (opts->form != 0 && opts->form != 1) { fh::set_error("form must be 0 or 1"); return FH_ERR_ARG; }
+  if (opts->tune != 0 && opts->tune != 1) { fh::set_error("tune must be 0 or 1"); return FH_ERR_ARG; }
   if (opts->path < 0 || opts->path > 2 || (opts->cluster != 0 && opts->cluster != 8 && opts->cluster != 16)) {
     fh::set_error("path must be 0..2 and cluster 0, 8 or 16");
     return FH_ERR_ARG;
@@ -1009,6 +1024,39 @@ int status_rank(fh_status st) {
   return st == FH_NONFINITE ? 3 : st == FH_DIVERGED ? 2 : st == FH_NOT_CONVERGED ? 1 : 0;
 }
 
+// Autotuner: time every eligible launch configuration (whole-GPU passes,
+// cluster-resident with 8 or 16 CTAs) for a few iterations of the actual loads
+// in the given bulk precision and keep the fastest per iteration.  The trials
+// overwrite the solver's strain, so they run only for solves that start from
+// E = 0.
+fh_status autotune(fh_solver* s, int nload, const double* eps0, int prec, int chunk) {
+  const int slot = prec == FH_PREC_FP64 ? 0 : 1;
+  const int cand_path[3] = {1, 2, 2}, cand_cs[3] = {0, 8, 16};
+  const int iters = 24;
+  float best = 1e30f;
+  for (int c = 0; c < 3; ++c) {
+    s->tuned_us[slot][c] = -1.f;
+    int path = 1, cs = 0;
+    fh_status rc = prec == FH_PREC_FP64 ? choose_path<double>(s, cand_path[c], cand_cs[c], &path, &cs)
+                                        : choose_path<float>(s, cand_path[c], cand_cs[c], &path, &cs);
+    if (rc == FH_ERR_UNSUPPORTED) { fh::set_error(""); continue; }
+    if (rc != FH_OK) return rc;
+    PhaseOut P;
+    for (int rep = 0; rep < 2; ++rep) {  // the first run pays one-time set-up
+      rc = solve_phase(s, nload, eps0, 0.0, iters, prec, 0, chunk, cand_path[c], cand_cs[c], nullptr, &P);
+      if (rc != FH_OK) return rc;
+    }
+    const float us = 1e3f * P.elapsed / iters;
+    s->tuned_us[slot][c] = us;
+    if (us < best) {
+      best = us;
+      s->tuned_path[slot] = P.path;
+      s->tuned_cs[slot] = P.cs;
+    }
+  }
+  return FH_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1018,18 +1066,34 @@ fh_status fh_solve(fh_solver* s, int nload, const double* eps0, const fh_solve_o
   if (rc != FH_OK) return rc;
   rc = join_user(s);
   if (rc != FH_OK) return rc;
+  s->form = opts->form;
   const int chunk = chunk_of(opts);
   const bool mixed = opts->precision == FH_PREC_MIXED;
   const int prec1 = opts->precision == FH_PREC_FP64 ? FH_PREC_FP64 : FH_PREC_FP32;
+  int path1 = opts->path, cs1 = opts->cluster, path2 = opts->path, cs2 = opts->cluster;
+  if (opts->tune && opts->path == 0 && opts->cluster == 0 && opts->init == 0) {
+    for (int pr : {prec1, mixed ? (int)FH_PREC_FP64 : -1}) {
+      if (pr < 0) continue;
+      const int slot = pr == FH_PREC_FP64 ? 0 : 1;
+      if (s->tuned_path[slot] == 0) {
+        rc = autotune(s, nload, eps0, pr, chunk);
+        if (rc != FH_OK) return rc;
+      }
+    }
+    const int s1 = prec1 == FH_PREC_FP64 ? 0 : 1;
+    path1 = s->tuned_path[s1];
+    cs1 = s->tuned_cs[s1];
+    path2 = s->tuned_path[0];
+    cs2 = s->tuned_cs[0];
+  }
   PhaseOut A, B;
-  rc = solve_phase(s, nload, eps0, opts->tol, opts->max_iter, prec1, opts->init, chunk, opts->path, opts->cluster,
-                   nullptr, &A, mixed ? kStallWindow : 0);
+  rc = solve_phase(s, nload, eps0, opts->tol, opts->max_iter, prec1, opts->init, chunk, path1, cs1, nullptr, &A,
+                   mixed ? kStallWindow : 0);
   if (rc != FH_OK) return rc;
   if (mixed) {
     LoadState st0[FH_MAX_LOADS];
     polish_start(A, st0);
-    rc = solve_phase(s, nload, eps0, opts->tol, opts->max_iter, FH_PREC_FP64, 1, chunk, opts->path, opts->cluster,
-                     st0, &B);
+    rc = solve_phase(s, nload, eps0, opts->tol, opts->max_iter, FH_PREC_FP64, 1, chunk, path2, cs2, st0, &B);
     if (rc != FH_OK) return rc;
   }
   return finish_solve(s, nload, eps0, A, &B, mixed, res);
@@ -1052,8 +1116,15 @@ fh_status fh_solve_batch(fh_solver* const* solvers, int n, const int* nload, con
   for (int i = 0; i < n; ++i) {
     fh_status rc = join_user(solvers[i]);
     if (rc != FH_OK) return rc;
-    rc = begin_phase(solvers[i], nload[i], eps0[i], opts->tol, opts->max_iter, prec1, opts->init, chunk, opts->path,
-                     opts->cluster, nullptr, &A[i], mixed ? kStallWindow : 0);
+    solvers[i]->form = opts->form;
+    int p1 = opts->path, c1 = opts->cluster;
+    const int slot = prec1 == FH_PREC_FP64 ? 0 : 1;
+    if (p1 == 0 && c1 == 0 && solvers[i]->tuned_path[slot] != 0) {   // keep an earlier tuning
+      p1 = solvers[i]->tuned_path[slot];
+      c1 = solvers[i]->tuned_cs[slot];
+    }
+    rc = begin_phase(solvers[i], nload[i], eps0[i], opts->tol, opts->max_iter, prec1, opts->init, chunk, p1, c1,
+                     nullptr, &A[i], mixed ? kStallWindow : 0);
     if (rc != FH_OK) return rc;
   }
   for (int i = 0; i < n; ++i) {
@@ -1064,8 +1135,13 @@ fh_status fh_solve_batch(fh_solver* const* solvers, int n, const int* nload, con
     for (int i = 0; i < n; ++i) {
       LoadState st0[FH_MAX_LOADS];
       polish_start(A[i], st0);
-      fh_status rc = begin_phase(solvers[i], nload[i], eps0[i], opts->tol, opts->max_iter, FH_PREC_FP64, 1, chunk,
-                                 opts->path, opts->cluster, st0, &B[i]);
+      int p2 = opts->path, c2 = opts->cluster;
+      if (p2 == 0 && c2 == 0 && solvers[i]->tuned_path[0] != 0) {
+        p2 = solvers[i]->tuned_path[0];
+        c2 = solvers[i]->tuned_cs[0];
+      }
+      fh_status rc = begin_phase(solvers[i], nload[i], eps0[i], opts->tol, opts->max_iter, FH_PREC_FP64, 1, chunk, p2,
+                                 c2, st0, &B[i]);
       if (rc != FH_OK) return rc;
     }
     for (int i = 0; i < n; ++i) {
@@ -1185,6 +1261,17 @@ fh_status fh_profile_passes(fh_solver* s, int nload, int precision, int reps, do
   if (rc != FH_OK) return rc;
   return precision == FH_PREC_FP64 ? profile_passes<double>(s, precision, nload, reps, ms)
                                    : profile_passes<float>(s, precision, nload, reps, ms);
+}
+
+fh_status fh_get_tuning(const fh_solver* s, int precision, int* path, int* cluster, float* us_per_iter) {
+  if (!s || !path || !cluster) { fh::set_error("null argument"); return FH_ERR_ARG; }
+  if (precision != FH_PREC_FP64 && precision != FH_PREC_FP32) { fh::set_error("precision must be FP64 or FP32"); return FH_ERR_ARG; }
+  const int slot = precision == FH_PREC_FP64 ? 0 : 1;
+  *path = s->tuned_path[slot];
+  *cluster = s->tuned_cs[slot];
+  if (us_per_iter)
+    for (int c = 0; c < 3; ++c) us_per_iter[c] = s->tuned_us[slot][c];
+  return FH_OK;
 }
 
 fh_status fh_get_residuals(const fh_solver* s, int load, double* hist, int* n) {

@@ -341,3 +341,45 @@ def test_full_size_box3d_properties(fh):
     Cs = 0.5 * (C + C.T)
     assert np.linalg.eigvalsh(voigt - Cs).min() > -1e-3 * np.abs(voigt).max()
     assert np.linalg.eigvalsh(Cs - reuss).min() > -1e-3 * np.abs(voigt).max()
+
+
+@pytest.mark.parametrize("path", [(1, 0), (2, 16)], ids=["passes", "cluster16"])
+@pytest.mark.parametrize("spec", [CASES[1], CASES[3], CASES[7]], ids=[CASES[1][0], CASES[3][0], CASES[7][0]])
+def test_variational_form_matches_oracle(fh, spec, path):
+    """Thm. ls_discretization: the variational discretisation iterated as
+    E <- E - Gamma^p C (E + eps0) (the oracle's form B), against the oracle."""
+    case = _case(spec)
+    s = case.product(fh)
+    if path[0] == 2 and len(case.pattern.dims) != 2:
+        pytest.skip("cluster path needs two axes")
+    n = 25
+    try:
+        out = s.solve(case.eps0, tol=0.0, max_iter=n, path=path[0], cluster=path[1], form=1)
+    except fh.FhError as e:
+        if e.status == -8:
+            pytest.skip("fields do not fit in a cluster of this size")
+        raise
+    from oracle import scheme as OS
+    ref = OS.solve(case.T, case.Gp, case.Cp_o[case.ids], case.C0_o, case.eps0, tol=0.0, max_iter=n, form="B")
+    assert case.strain_error(s, ref["E"]) < TOL64
+    assert rel(out["mean_stress"], ref["mean_stress"]) < TOL64
+    # and it is a different discretisation from Eq. (pde_coefficients) for these generators
+    a = case.oracle_solve(tol=0.0, max_iter=n)
+    assert np.abs(a["E"] - ref["E"]).max() > 1e-6
+
+
+def test_autotuner_picks_a_measured_configuration(fh):
+    """tune=1 times passes and clusters of 8 and 16, keeps the fastest, and the tuned
+    solve agrees with the oracle."""
+    case = Case.from_workload(W.dlvp_sheared())
+    s = case.product(fh)
+    out = s.solve(case.eps0, tol=0.0, max_iter=30, precision=fh.FH_PREC_FP64, tune=1)
+    t = s.get_tuning(fh.FH_PREC_FP64)
+    assert t["path"] in (1, 2)
+    us = [u for u in t["us_per_iter"] if u > 0]
+    assert len(us) >= 2
+    chosen = {1: 0, 2: 1 if t["cluster"] == 8 else 2}[t["path"]]
+    assert t["us_per_iter"][chosen] == min(us)
+    assert out["path"] == t["path"]
+    ref = case.oracle_solve(tol=0.0, max_iter=30)
+    assert case.strain_error(s, ref["E"]) < TOL64
