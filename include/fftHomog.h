@@ -229,6 +229,12 @@ fh_status fh_get_strain(const fh_solver* s, int load, double* E);
  * device, layout of fh_get_strain). */
 fh_status fh_set_strain(fh_solver* s, int load, const double* E);
 
+/* FP32 variants of fh_get_strain / fh_set_strain (same layout), for starting
+ * strains produced in FP32 (e.g. by the FNO below).  Setting an FP32 strain
+ * makes the next init = 1 solve start from it in either precision. */
+fh_status fh_get_strain_f32(const fh_solver* s, int load, float* E);
+fh_status fh_set_strain_f32(fh_solver* s, int load, const float* E);
+
 /* Effective stiffness C_eff (Sec. 3.1, read as <C:(E+eps0)> = C_eff eps0)
  * from the last solve, which must have had nload = n_v linearly independent
  * eps0.  Ceff[n_v*n_v] host, row-major; voigt != 0 converts Mandel to Voigt
@@ -287,6 +293,44 @@ fh_status fh_profile_passes(fh_solver* s, int nload, int precision, int reps, do
 fh_status fh_mean_stress_noalloc(int d, long long m, int nload, const double* E, const uint8_t* phase,
                                  int nphase, const double* Cp, const double* eps0, double* mean_stress,
                                  void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Learned start: a Fourier neural operator (FNO) that predicts the starting
+ * strain fluctuation E of fh_solve from the microstructure and eps0.  The
+ * paper has no counterpart; the Basic Scheme started from the prediction
+ * still iterates to the same tolerance, so the network only saves iterations.
+ * Network on an n^3 grid (z fastest, the storage order of a diagonal M):
+ *   v0 = P x + p;  u_l = W_l v_l + w_l + K_l v_l,  v_{l+1} = gelu(u_l);  y = Q v_L + q,
+ *   K_l v = n^-3 Re sum_k w(kz) R_l(k) v^(k) e^{+2 pi i k.x/n},  v^ = truncated DFT,
+ *   kx, ky in {-modes..modes-1}, kz in {0..modes-1}, w(0) = 1, w(kz>0) = 2.
+ * R_l and W_l are applied in BF16 (from FP32 master weights), all sums FP32.
+ * Arrays x [batch][cin][n^3], y and targets [batch][cout][n^3] are device FP32.
+ * The parameter vector (host FP32) is, in order: P[width][cin], p[width],
+ * W[layers][width][width], w[layers][width], Re R[layers][2m][2m][m][width][width],
+ * Im R[...], Q[cout][width], q[cout]. */
+typedef struct fh_fno fh_fno;
+fh_status fh_fno_create(int n, int cin, int cout, int width, int modes, int layers, int max_batch,
+                        void* cuda_stream, fh_fno** out);
+void fh_fno_destroy(fh_fno* f);
+fh_status fh_fno_param_count(const fh_fno* f, long long* count);
+fh_status fh_fno_set_params(fh_fno* f, const float* params);
+fh_status fh_fno_get_params(const fh_fno* f, float* params);
+fh_status fh_fno_get_grads(const fh_fno* f, float* grads);
+fh_status fh_fno_zero_grad(fh_fno* f);
+/* y = network(x) for `batch` samples (x, y device). */
+fh_status fh_fno_forward(fh_fno* f, int batch, const float* x, float* y);
+/* Forward and backward of the mean squared error against `target`
+ * (mean over samples, channels and voxels); the loss goes to *loss (host,
+ * may be NULL) and the gradient is ADDED to the accumulated gradient. */
+fh_status fh_fno_loss_grad(fh_fno* f, int batch, const float* x, const float* target, double* loss);
+/* One Adam update of the master weights with the accumulated gradient
+ * (step counts from 1 for the bias corrections). */
+fh_status fh_fno_adam_step(fh_fno* f, float lr, float beta1, float beta2, float eps, int step);
+/* Input channels of one sample (cin = 7): log10(E(x))/2 from a phase map
+ * (device uint8[n^3]) and per-phase log10 Young moduli (host), then the six
+ * Mandel components of eps0 (host) as constant channels; x device [7][n^3]. */
+fh_status fh_fno_make_input(const fh_fno* f, const uint8_t* phase, int nphase, const double* phase_logE,
+                            const double* eps0, float* x);
 
 const char* fh_status_string(fh_status st);
 const char* fh_last_error(void);

@@ -99,7 +99,7 @@ def library():
 
 def exported_symbols():
     """Names of the C entry points the binding expects (all declared in fftHomog.h)."""
-    return ["fh_pattern_create", "fh_pattern_destroy", "fh_pattern_info", "fh_pattern_points",
+    return FNO_SYMBOLS + ["fh_pattern_create", "fh_pattern_destroy", "fh_pattern_info", "fh_pattern_points",
             "fh_pattern_numerators", "fh_pattern_half_freqs", "fh_solver_create", "fh_solver_destroy",
             "fh_set_stiffness_phases", "fh_set_reference", "fh_solve", "fh_get_strain", "fh_set_strain",
             "fh_get_ceff", "fh_get_green", "fh_get_residuals", "fh_profile_passes", "fh_status_string",
@@ -344,3 +344,103 @@ def solve_batch(solvers, eps0s, tol=1e-6, max_iter=20000, precision=FH_PREC_MIXE
                     "elapsed_ms": res[i].elapsed_ms, "kernel_launches": res[i].kernel_launches,
                     "path": res[i].path, "cluster": res[i].cluster})
     return rc, out
+
+
+# ---------------------------------------------------------------------------
+# learned start (fh_fno_*)
+# ---------------------------------------------------------------------------
+
+def _sig_fno():
+    lib = library()
+    P, I, V = C.c_void_p, C.c_int, None
+    sig = {
+        "fh_fno_create": (I, [I, I, I, I, I, I, I, P, C.POINTER(P)]),
+        "fh_fno_destroy": (V, [P]),
+        "fh_fno_param_count": (I, [P, P]),
+        "fh_fno_set_params": (I, [P, P]),
+        "fh_fno_get_params": (I, [P, P]),
+        "fh_fno_get_grads": (I, [P, P]),
+        "fh_fno_zero_grad": (I, [P]),
+        "fh_fno_forward": (I, [P, I, P, P]),
+        "fh_fno_loss_grad": (I, [P, I, P, P, P]),
+        "fh_fno_adam_step": (I, [P, C.c_float, C.c_float, C.c_float, C.c_float, I]),
+        "fh_fno_make_input": (I, [P, P, I, P, P, P]),
+        "fh_get_strain_f32": (I, [P, I, P]),
+        "fh_set_strain_f32": (I, [P, I, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+FNO_SYMBOLS = ["fh_fno_create", "fh_fno_destroy", "fh_fno_param_count", "fh_fno_set_params", "fh_fno_get_params",
+               "fh_fno_get_grads", "fh_fno_zero_grad", "fh_fno_forward", "fh_fno_loss_grad", "fh_fno_adam_step",
+               "fh_fno_make_input", "fh_get_strain_f32", "fh_set_strain_f32"]
+
+
+class FNO:
+    """Fourier neural operator for the starting strain (fh_fno_*); device tensors in, out."""
+
+    def __init__(self, n, cin=7, cout=6, width=32, modes=12, layers=4, max_batch=4, stream=0):
+        lib = _sig_fno()
+        h = C.c_void_p()
+        _check(lib.fh_fno_create(n, cin, cout, width, modes, layers, max_batch, C.c_void_p(stream), C.byref(h)))
+        self._h = h
+        self.n, self.cin, self.cout, self.width, self.modes, self.layers = n, cin, cout, width, modes, layers
+        cnt = C.c_longlong()
+        _check(lib.fh_fno_param_count(h, C.byref(cnt)))
+        self.nparam = cnt.value
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.fh_fno_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(np.asarray(flat, dtype=np.float32))
+        assert flat.size == self.nparam
+        _check(library().fh_fno_set_params(self._h, _ptr(flat)))
+
+    def get_params(self):
+        out = np.empty(self.nparam, dtype=np.float32)
+        _check(library().fh_fno_get_params(self._h, _ptr(out)))
+        return out
+
+    def get_grads(self):
+        out = np.empty(self.nparam, dtype=np.float32)
+        _check(library().fh_fno_get_grads(self._h, _ptr(out)))
+        return out
+
+    def zero_grad(self):
+        _check(library().fh_fno_zero_grad(self._h))
+
+    def forward(self, x, y):
+        _check(library().fh_fno_forward(self._h, int(x.shape[0]), _ptr(x), _ptr(y)))
+        return y
+
+    def loss_grad(self, x, target):
+        loss = C.c_double()
+        _check(library().fh_fno_loss_grad(self._h, int(x.shape[0]), _ptr(x), _ptr(target), C.byref(loss)))
+        return loss.value
+
+    def adam_step(self, lr, step, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(library().fh_fno_adam_step(self._h, float(lr), float(beta1), float(beta2), float(eps), int(step)))
+
+    def make_input(self, phase, phase_logE, eps0, x):
+        plE = np.ascontiguousarray(np.asarray(phase_logE, dtype=np.float64))
+        e0 = np.ascontiguousarray(np.asarray(eps0, dtype=np.float64))
+        _check(library().fh_fno_make_input(self._h, _ptr(phase), len(plE), _ptr(plE), _ptr(e0), _ptr(x)))
+        return x
+
+
+def get_strain_f32(solver, load, out):
+    _check(_sig_fno().fh_get_strain_f32(solver._h, int(load), _ptr(out)))
+    return out
+
+
+def set_strain_f32(solver, load, E):
+    _check(_sig_fno().fh_set_strain_f32(solver._h, int(load), _ptr(E)))

@@ -17,7 +17,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libffthomog.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["solver.cu", "lattice.cpp", "noalloc.cu"]
+SOURCES = ["solver.cu", "lattice.cpp", "noalloc.cu", "fno.cu"]
 HEADERS = ["internal.hpp", "kernels.cuh", "fft.cuh", "cluster.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

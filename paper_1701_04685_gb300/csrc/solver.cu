@@ -1195,6 +1195,43 @@ fh_status fh_set_strain(fh_solver* s, int load, const double* E) {
   return FH_OK;
 }
 
+fh_status fh_get_strain_f32(const fh_solver* sc, int load, float* E) {
+  fh_solver* s = const_cast<fh_solver*>(sc);
+  if (!s || !E) { fh::set_error("null argument"); return FH_ERR_ARG; }
+  if (load < 0 || load >= s->nload_max) { fh::set_error("load out of range"); return FH_ERR_ARG; }
+  if (s->E_prec < 0) { fh::set_error("no strain available"); return FH_ERR_STATE; }
+  const size_t n = (size_t)s->g.nv * s->g.m;
+  const size_t off = (size_t)load * n;
+  fh_status rc = join_user(s);
+  if (rc != FH_OK) return rc;
+  if (s->E_prec == FH_PREC_FP32) {
+    CK(cudaMemcpyAsync(E, s->E32 + off, n * sizeof(float), cudaMemcpyDefault, s->work));
+  } else {
+    fh::convert_copy<float, double><<<1024, kThreads, 0, s->work>>>(s->E32 + off, s->E64 + off, (long long)n);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(E, s->E32 + off, n * sizeof(float), cudaMemcpyDefault, s->work));
+  }
+  CK(cudaStreamSynchronize(s->work));
+  return FH_OK;
+}
+
+fh_status fh_set_strain_f32(fh_solver* s, int load, const float* E) {
+  if (!s || !E) { fh::set_error("null argument"); return FH_ERR_ARG; }
+  if (load < 0 || load >= s->nload_max) { fh::set_error("load out of range"); return FH_ERR_ARG; }
+  const size_t n = (size_t)s->g.nv * s->g.m;
+  fh_status rc = join_user(s);
+  if (rc != FH_OK) return rc;
+  if (s->E_prec == FH_PREC_FP64) {
+    // keep every load in one precision: bring the others to FP32 first
+    fh::convert_copy<float, double><<<1024, kThreads, 0, s->work>>>(s->E32, s->E64, (long long)(n * s->nload_max));
+    CK(cudaGetLastError());
+  }
+  CK(cudaMemcpyAsync(s->E32 + (size_t)load * n, E, n * sizeof(float), cudaMemcpyDefault, s->work));
+  CK(cudaStreamSynchronize(s->work));
+  s->E_prec = FH_PREC_FP32;
+  return FH_OK;
+}
+
 fh_status fh_get_ceff(const fh_solver* s, double* Ceff, int voigt) {
   if (!s || !Ceff) { fh::set_error("null argument"); return FH_ERR_ARG; }
   const int nv = s->g.nv;

@@ -23,7 +23,7 @@ def fh():
 
 def _declared():
     src = open(os.path.join(ROOT, "include", "fftHomog.h")).read()
-    return sorted(set(re.findall(r"\b(fh_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(fh_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_library_exports_every_declared_symbol(fh):
