@@ -326,9 +326,10 @@ fh_status fh_fno_loss_grad(fh_fno* f, int batch, const float* x, const float* ta
 /* One Adam update of the master weights with the accumulated gradient
  * (step counts from 1 for the bias corrections). */
 fh_status fh_fno_adam_step(fh_fno* f, float lr, float beta1, float beta2, float eps, int step);
-/* Input channels of one sample (cin = 7): log10(E(x))/2 from a phase map
- * (device uint8[n^3]) and per-phase log10 Young moduli (host), then the six
- * Mandel components of eps0 (host) as constant channels; x device [7][n^3]. */
+/* Input channels of one sample: log10(E(x))/2 from a phase map (device
+ * uint8[n^3]) and per-phase log10 Young moduli (host); for cin = 7 followed
+ * by the six Mandel components of eps0 (host) as constant channels (for
+ * cin = 1 eps0 is not used).  x device [cin][n^3]. */
 fh_status fh_fno_make_input(const fh_fno* f, const uint8_t* phase, int nphase, const double* phase_logE,
                             const double* eps0, float* x);
 

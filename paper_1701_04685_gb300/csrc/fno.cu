@@ -430,10 +430,12 @@ struct FeatParams {
   float e0[6];
 };
 
-__global__ void k_features(int N3, FeatParams P, const uint8_t* __restrict__ phase, float* __restrict__ x) {
+__global__ void k_features(int N3, FeatParams P, const uint8_t* __restrict__ phase, float* __restrict__ x,
+                           int with_strain) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N3; i += gridDim.x * blockDim.x) {
     x[i] = P.logE[phase[i] & 15];
-    for (int c = 0; c < 6; ++c) x[(size_t)(c + 1) * N3 + i] = P.e0[c];
+    if (with_strain)
+      for (int c = 0; c < 6; ++c) x[(size_t)(c + 1) * N3 + i] = P.e0[c];
   }
 }
 
@@ -689,11 +691,14 @@ fh_status fh_fno_make_input(const fh_fno* f, const uint8_t* phase, int nphase, c
                             const double* eps0, float* x) {
   if (!f || !phase || !phase_logE || !eps0 || !x) { fh::set_error("null argument"); return FH_ERR_ARG; }
   if (nphase < 1 || nphase > 16) { fh::set_error("nphase must be 1..16"); return FH_ERR_ARG; }
-  if (f->d.cin != 7) { fh::set_error("make_input builds 7 channels (log10 E, 6 strains)"); return FH_ERR_ARG; }
+  if (f->d.cin != 7 && f->d.cin != 1) {
+    fh::set_error("make_input builds 1 channel (log10 E) or 7 (log10 E, 6 strains)");
+    return FH_ERR_ARG;
+  }
   FeatParams P{};
   for (int q = 0; q < nphase; ++q) P.logE[q] = (float)(0.5 * phase_logE[q]);
   for (int c = 0; c < 6; ++c) P.e0[c] = (float)eps0[c];
-  k_features<<<grid_for(f->d.N3), kT, 0, f->stream>>>(f->d.N3, P, phase, x);
+  k_features<<<grid_for(f->d.N3), kT, 0, f->stream>>>(f->d.N3, P, phase, x, f->d.cin == 7);
   FCK(cudaGetLastError());
   FCK(cudaStreamSynchronize(f->stream));
   return FH_OK;
