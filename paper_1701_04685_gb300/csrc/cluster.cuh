@@ -77,8 +77,12 @@ __host__ __device__ inline ClusterLayout cluster_layout(int N0, int L, int nv, i
   return c;
 }
 
+// threads per CTA (8 warps: 16 warps measured slower, the 128-register cap
+// spills the radix-8 butterflies)
+template <typename T> struct ClusterThreads { static constexpr int value = 256; };
+
 template <typename T, int NV, int CS>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(ClusterThreads<T>::value, 1)
 cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __restrict__ tw0g,
                  const cplx<T>* __restrict__ tw1g, T* __restrict__ Eg, const uint8_t* __restrict__ phase,
                  const T* __restrict__ dC, int nphase, const T* __restrict__ Gt, Control* ctl, LoadState* st,

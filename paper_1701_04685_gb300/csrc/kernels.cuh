@@ -101,6 +101,7 @@ template <typename T> struct ResAcc;
 template <> struct ResAcc<double> {
   double s = 0.0;
   __device__ __forceinline__ void add_sq(double a) { s = fma(a, a, s); }
+  __device__ __forceinline__ void add(double v) { s += v; }
   __device__ __forceinline__ double value() const { return s; }
 };
 template <> struct ResAcc<float> {
@@ -113,6 +114,13 @@ template <> struct ResAcc<float> {
     const float err = (hi - (s - bp)) + (p - bp);
     hi = s;
     lo += err + e;
+  }
+  // add a short FP32 partial sum (TwoSum only)
+  __device__ __forceinline__ void add(float v) {
+    const float s = hi + v;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (v - bp);
+    hi = s;
   }
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
@@ -145,8 +153,12 @@ __device__ void advance_state(LoadState& s, Control* ctl, double* hist, int load
 // row pass along the contiguous axis (length L), fused with the pointwise
 // constitutive stage and the residual.
 // ---------------------------------------------------------------------------
+// resident blocks per SM requested from the compiler (more than one capped
+// the registers and spilled, measured slower)
+template <typename T> struct PassOcc { static constexpr int value = 1; };
+
 template <typename T, int NV, bool FIRST>
-__global__ void __launch_bounds__(256) row_pass(GridInfo g, DevPlan plan, const cplx<T>* __restrict__ tw,
+__global__ void __launch_bounds__(256, PassOcc<T>::value) row_pass(GridInfo g, DevPlan plan, const cplx<T>* __restrict__ tw,
                                                 T* __restrict__ E, cplx<T>* __restrict__ S,
                                                 const uint8_t* __restrict__ phase, const T* __restrict__ dC,
                                                 Control* ctl, LoadState* st, double* __restrict__ partials,
@@ -167,6 +179,8 @@ __global__ void __launch_bounds__(256) row_pass(GridInfo g, DevPlan plan, const 
   cplx<T>* W1 = W0 + (size_t)((rpb * NV + 1) >> 1) * Lp;
   const FDiv fL = make_fdiv(L), fH = make_fdiv(H);
 
+  __shared__ T dcs[16 * NV * NV];   // stiffness table of the pointwise stage
+  for (int i = threadIdx.x; i < 16 * NV * NV; i += blockDim.x) dcs[i] = dC[i];
   if (threadIdx.x == 0) s_skip = st[load].done;
   __syncthreads();
   ResAcc<T> acc_d, acc_n;
@@ -245,7 +259,7 @@ __global__ void __launch_bounds__(256) row_pass(GridInfo g, DevPlan plan, const 
           ep[c * cstrE] = en[c];
         }
       }
-      const T* dc = dC + (size_t)phase[(row0 + r) * L + x] * NV * NV;
+      const T* dc = dcs + (size_t)phase[(row0 + r) * L + x] * NV * NV;
 #pragma unroll
       for (int a = 0; a < NV; ++a) {
         T t = T(0);
@@ -324,7 +338,7 @@ __global__ void __launch_bounds__(256) row_pass(GridInfo g, DevPlan plan, const 
 // against bank conflicts).
 // ---------------------------------------------------------------------------
 template <typename T, int NV, int MODE>
-__global__ void __launch_bounds__(256) line_pass(GridInfo g, DevPlan plan, const cplx<T>* __restrict__ tw,
+__global__ void __launch_bounds__(256, PassOcc<T>::value) line_pass(GridInfo g, DevPlan plan, const cplx<T>* __restrict__ tw,
                                                  cplx<T>* __restrict__ S, const T* __restrict__ Gt,
                                                  const LoadState* st, int ax, int W, int ntiles,
                                                  int n_outer, int n_inner) {

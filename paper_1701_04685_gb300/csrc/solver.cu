@@ -18,6 +18,7 @@
 #include "internal.hpp"
 #include "kernels.cuh"
 #include "cluster.cuh"
+#include "warprow.cuh"
 
 namespace fh {
 static thread_local std::string g_err;
@@ -108,6 +109,9 @@ struct fh_solver {
   int last_iters[FH_MAX_LOADS] = {};
   // launch shapes per precision (0: fp64, 1: fp32)
   int rpb[2] = {1, 1};
+  int row_warp[2] = {0, 0};  // > 0: warp-per-row pass with L = 32 * row_warp
+  int warp_res[2] = {0, 0};  // resident blocks per SM of that pass
+  int sms = 0;               // multiprocessors of the device
   int row_bpl[2] = {1, 1};
   size_t row_smem[2] = {0, 0};
   int lineW[2][3] = {};
@@ -129,11 +133,27 @@ void choose_shapes(fh_solver* s, int prec) {
   const int nl = s->nload_max;
   const int Lp = prec == FH_PREC_FP64 ? fh::padded_len<3>(g.L) : fh::padded_len<4>(g.L);
   auto row_smem = [&](int rpb) { return (size_t)2 * ((rpb * g.nv + 1) / 2) * Lp * csize(prec); };
+  // rows per block: grow while the grid keeps >= 2 blocks per SM and a block's
+  // shared memory stays small enough for several resident blocks
+  const size_t row_smem_cap = 96 * 1024;
   int rpb = 1;
-  while (rpb * 2 <= g.nrows && (g.nrows * nl) / (rpb * 2) >= 2 * sms && row_smem(rpb * 2) <= 96 * 1024) rpb *= 2;
+  while (rpb * 2 <= g.nrows && (g.nrows * nl) / (rpb * 2) >= 2 * sms && row_smem(rpb * 2) <= row_smem_cap) rpb *= 2;
   s->rpb[prec] = rpb;
   s->row_bpl[prec] = (int)((g.nrows + rpb - 1) / rpb);
   s->row_smem[prec] = row_smem(rpb);
+  // FP32 3-D grids whose contiguous axis is 32, 64, 128 or 256 points long
+  // take the warp-per-row pass (FP64 keeps the block pass: its radix-8
+  // stages need fewer operations on the narrow FP64 pipe)
+  s->row_warp[prec] = 0;
+  if (prec == FH_PREC_FP32 && g.nv == 6 && g.L % 32 == 0) {
+    const int P = g.L / 32;
+    if (P == 1 || P == 2 || P == 4 || P == 8) {
+      const int nw = fh::kWarpRowThreads / 32;
+      s->row_warp[prec] = P;
+      s->row_bpl[prec] = (int)((g.nrows + nw - 1) / nw);
+      s->row_smem[prec] = fh::warprow_smem<float>(g.L);
+    }
+  }
   for (int a = 0; a + 1 < g.nd; ++a) {
     const int N = g.dims[a];
     long long others = 1;
@@ -143,7 +163,8 @@ void choose_shapes(fh_solver* s, int prec) {
     auto smem = [&](int w) { return (size_t)2 * g.nv * w * (N + 1) * csize(prec); };
     auto blocks = [&](int w) { return (long long)nl * others * ((g.H + w - 1) / w); };
     const int wmin = prec == FH_PREC_FP64 ? 2 : 4;
-    while (W > wmin && (smem(W) > 96 * 1024 || blocks(W) < 2 * sms)) W /= 2;
+    const size_t line_cap = 96 * 1024;
+    while (W > wmin && (smem(W) > line_cap || blocks(W) < 2 * sms)) W /= 2;
     while (W > 1 && smem(W) > kMaxSmem) W /= 2;
     s->lineW[prec][a] = W;
     s->ntiles[prec][a] = (g.H + W - 1) / W;
@@ -237,10 +258,41 @@ void enqueue_row_pass_nv(fh_solver* s, int prec, int nload) {
       s->st, s->partials, s->hist, s->rpb[prec], s->row_bpl[prec]);
 }
 
+template <typename T, int P, bool FIRST>
+void enqueue_row_pass_warp(fh_solver* s, int prec, int nload) {
+  using C = typename fh::cplx_t<T>::type;
+  // at most one wave of resident blocks, split evenly over the loads
+  // (row_bpl, one row per warp, is the bound the partial-sum buffer is sized for)
+  const int resident = std::max(1, s->warp_res[prec]) * std::max(1, s->sms);
+  const int bpl = std::max(1, std::min(s->row_bpl[prec], resident / nload));
+  fh::row_pass_warp6<T, P, FIRST><<<nload * bpl, fh::kWarpRowThreads, s->row_smem[prec], s->work>>>(
+      s->g, twp<T>(s->ax[s->g.nd - 1]), Eptr<T>(s), reinterpret_cast<C*>(s->S), s->phase, dCptr<T>(s), s->ctl, s->st,
+      s->partials, s->hist, bpl);
+}
+
 template <typename T, bool FIRST>
 void enqueue_row_pass(fh_solver* s, int prec, int nload) {
+  if constexpr (sizeof(T) == 4) {
+    switch (s->row_warp[prec]) {
+      case 1: enqueue_row_pass_warp<T, 1, FIRST>(s, prec, nload); return;
+      case 2: enqueue_row_pass_warp<T, 2, FIRST>(s, prec, nload); return;
+      case 4: enqueue_row_pass_warp<T, 4, FIRST>(s, prec, nload); return;
+      case 8: enqueue_row_pass_warp<T, 8, FIRST>(s, prec, nload); return;
+      default: break;
+    }
+  }
   if (s->g.nv == 3) enqueue_row_pass_nv<T, 3, FIRST>(s, prec, nload);
   else enqueue_row_pass_nv<T, 6, FIRST>(s, prec, nload);
+}
+
+template <typename T, int P>
+cudaError_t set_warp_attrs(fh_solver* s, int prec, size_t rs) {
+  cudaError_t e = cudaFuncSetAttribute(fh::row_pass_warp6<T, P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(fh::row_pass_warp6<T, P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s->warp_res[prec], fh::row_pass_warp6<T, P, false>,
+                                                       fh::kWarpRowThreads, rs);
 }
 
 template <typename T, int NV>
@@ -250,8 +302,18 @@ fh_status set_smem_attrs_nv(fh_solver* s, int prec) {
     fh::set_error("contiguous axis too long for this precision (shared memory)");
     return FH_ERR_UNSUPPORTED;
   }
-  CK(cudaFuncSetAttribute(fh::row_pass<T, NV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
-  CK(cudaFuncSetAttribute(fh::row_pass<T, NV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
+  if (s->row_warp[prec] == 0) {
+    CK(cudaFuncSetAttribute(fh::row_pass<T, NV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
+    CK(cudaFuncSetAttribute(fh::row_pass<T, NV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
+  } else if constexpr (sizeof(T) == 4) {
+    switch (s->row_warp[prec]) {
+      case 1: CK((set_warp_attrs<T, 1>(s, prec, rs))); break;
+      case 2: CK((set_warp_attrs<T, 2>(s, prec, rs))); break;
+      case 4: CK((set_warp_attrs<T, 4>(s, prec, rs))); break;
+      case 8: CK((set_warp_attrs<T, 8>(s, prec, rs))); break;
+      default: break;
+    }
+  }
   size_t lm = 0;
   for (int a = 0; a + 1 < s->g.nd; ++a) lm = std::max(lm, s->line_smem[prec][a]);
   if (lm > kMaxSmem) {
@@ -349,7 +411,7 @@ fh_status cluster_fits_nv(fh_solver* s, bool* ok) {
   if (CS > 8) CK(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CS);
-  cfg.blockDim = dim3(kThreads);
+  cfg.blockDim = dim3(fh::ClusterThreads<T>::value);
   cfg.dynamicSmemBytes = lay.total;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -380,7 +442,7 @@ fh_status launch_cluster_nv(fh_solver* s, int nload) {
   auto kern = fh::cluster_solve_2d<T, NV, CS>;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nload * CS);
-  cfg.blockDim = dim3(kThreads);
+  cfg.blockDim = dim3(fh::ClusterThreads<T>::value);
   cfg.dynamicSmemBytes = lay.total;
   cfg.stream = s->work;
   cudaLaunchAttribute attr[1];
@@ -687,6 +749,11 @@ fh_status fh_solver_create(const fh_pattern* p, const fh_generator* gen, int nlo
     }                                                                         \
   } while (0)
   CKS(cudaStreamCreateWithFlags(&s->work, cudaStreamNonBlocking));
+  {
+    int dev = 0;
+    CKS(cudaGetDevice(&dev));
+    CKS(cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev));
+  }
   CKS(cudaEventCreate(&s->ev0));
   CKS(cudaEventCreate(&s->ev1));
   CKS(cudaEventCreateWithFlags(&s->ev_user, cudaEventDisableTiming));

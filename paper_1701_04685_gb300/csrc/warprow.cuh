@@ -1,0 +1,346 @@
+// Warp-per-row variant of the row pass for 3-D grids (n_v = 6) whose
+// contiguous axis has length L = 32 P, P in {1, 2, 4, 8}.
+//
+// One warp owns one grid row of one load at a time.  The six strain
+// components of the row form three complex lines (components 2p and 2p+1 as
+// real and imaginary parts), held in registers with lane l owning the points
+// l + 32 j, j < P.  The line DFT is done without block barriers:
+//   forward  - length-P DFT over j in registers, twiddles w_L^{l q}, then a
+//              32-point decimation-in-frequency DFT across the lanes with
+//              shuffles; lane l ends with frequency q + P * bitrev5(l);
+//   inverse  - the mirror image (decimation in time across lanes from that
+//              bit-reversed layout, twiddles, length-P DFT), ending with the
+//              points back in natural order.
+// Since every lane holds all six components of its points, the pointwise
+// stage (E update, Cauchy-residual sums, tau = (C - C0):(E + eps0)) needs no
+// data exchange.  Half-spectrum rows move between global and a per-warp
+// shared-memory scratch line with coalesced accesses.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace fh {
+
+__device__ __forceinline__ int bitrev5(int v) { return (int)(__brev((unsigned)v) >> 27); }
+
+template <typename T>
+__device__ __forceinline__ cplx<T> shfl_xor_c(cplx<T> v, int m) {
+  cplx<T> r;
+  r.x = __shfl_xor_sync(0xffffffffu, v.x, m);
+  r.y = __shfl_xor_sync(0xffffffffu, v.y, m);
+  return r;
+}
+
+template <int P, int DIR, typename T>
+__device__ __forceinline__ void small_dft(cplx<T>* v) {
+  if (P == 2) dft2<DIR, T>(v);
+  else if (P == 4) dft4<DIR, T>(v);
+  else if (P == 8) dft8<DIR, T>(v);
+}
+
+// w_L^{DIR t} from the table tw[t] = exp(-2 pi i t / L)
+template <int DIR, typename T>
+__device__ __forceinline__ cplx<T> twl(const cplx<T>* tw, int t) {
+  cplx<T> w = tw[t];
+  if (DIR > 0) w.y = -w.y;
+  return w;
+}
+
+// Radix-2 exchange stage h of the 32-point lane DFT, with sgn = -1 on the
+// upper lane of each pair (lane bit h set) and +1 on the lower lane.
+//   forward (decimation in frequency):  lower <- a + b,  upper <- (a - b) w
+//     computed as  t = partner + sgn * own,  then  t * w' (w' = 1 on the lower lane)
+//   inverse (decimation in time):       lower <- a + w b,  upper <- a - w b
+//     computed as  own' = own * w' (w' = 1 on the lower lane), then partner' + sgn * own'
+// where a and b are the lower and upper lane's values.  Every line of the
+// warp takes the same twiddle, loaded once per stage.
+
+// forward: natural (lane l, register j: point l + 32 j) -> bit-reversed
+// frequencies (lane l, register q: frequency q + P * bitrev5(l)), NL lines
+template <int P, int NL, typename T>
+__device__ __forceinline__ void warp_fft_fwd(cplx<T> (&v)[NL][P], const cplx<T>* tw, int lane) {
+  constexpr int L = 32 * P;
+#pragma unroll
+  for (int n = 0; n < NL; ++n) {
+    small_dft<P, -1, T>(v[n]);
+#pragma unroll
+    for (int q = 1; q < P; ++q) v[n][q] = cmul(v[n][q], twl<-1, T>(tw, lane * q));
+  }
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool upper = (lane & h) != 0;
+    const T sgn = upper ? T(-1) : T(1);
+    cplx<T> w;
+    if (h > 1) {
+      w = twl<-1, T>(tw, (lane & (h - 1)) * (L / (2 * h)));
+      if (!upper) { w.x = T(1); w.y = T(0); }
+    }
+#pragma unroll
+    for (int n = 0; n < NL; ++n)
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        const cplx<T> p = shfl_xor_c<T>(v[n][q], h);
+        cplx<T> t;
+        t.x = fma(sgn, v[n][q].x, p.x);
+        t.y = fma(sgn, v[n][q].y, p.y);
+        v[n][q] = h > 1 ? cmul(t, w) : t;
+      }
+  }
+}
+
+// inverse (unnormalised): bit-reversed frequencies -> natural points, NL lines
+template <int P, int NL, typename T>
+__device__ __forceinline__ void warp_fft_inv(cplx<T> (&v)[NL][P], const cplx<T>* tw, int lane) {
+  constexpr int L = 32 * P;
+#pragma unroll
+  for (int h = 1; h <= 16; h <<= 1) {
+    const bool upper = (lane & h) != 0;
+    const T sgn = upper ? T(-1) : T(1);
+    cplx<T> w;
+    if (h > 1) {
+      w = twl<+1, T>(tw, (lane & (h - 1)) * (L / (2 * h)));
+      if (!upper) { w.x = T(1); w.y = T(0); }
+    }
+#pragma unroll
+    for (int n = 0; n < NL; ++n)
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        const cplx<T> o = h > 1 ? cmul(v[n][q], w) : v[n][q];
+        const cplx<T> p = shfl_xor_c<T>(o, h);
+        v[n][q].x = fma(sgn, o.x, p.x);
+        v[n][q].y = fma(sgn, o.y, p.y);
+      }
+  }
+#pragma unroll
+  for (int n = 0; n < NL; ++n) {
+#pragma unroll
+    for (int q = 1; q < P; ++q) v[n][q] = cmul(v[n][q], twl<+1, T>(tw, lane * q));
+    small_dft<P, +1, T>(v[n]);
+  }
+}
+
+// shared-memory index with one spare slot per 16 entries: the stride-P
+// accesses of the bit-reversed layout then spread evenly over the banks
+__device__ __forceinline__ int wpad(int i) { return i + (i >> 4); }
+
+// rows 2a and 2a + 1 of one phase's 6 x 6 stiffness table (12 entries,
+// 16-byte aligned), loaded with 16-byte accesses
+template <typename T>
+__device__ __forceinline__ void load_rows(const T* p, T (&d)[12]);
+template <>
+__device__ __forceinline__ void load_rows<float>(const float* p, float (&d)[12]) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float4 v = q[i];
+    d[4 * i] = v.x; d[4 * i + 1] = v.y; d[4 * i + 2] = v.z; d[4 * i + 3] = v.w;
+  }
+}
+template <>
+__device__ __forceinline__ void load_rows<double>(const double* p, double (&d)[12]) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const double2 v = q[i];
+    d[2 * i] = v.x; d[2 * i + 1] = v.y;
+  }
+}
+
+constexpr int kWarpRowThreads = 256;
+
+// Rows are dealt to the warps of the grid round-robin; a launch sizes its grid
+// to the resident blocks, so every warp handles many rows and the block
+// barrier of the residual reduction is met once per launch.  All global loads
+// of a row (half spectra, old strain, phase indices) are issued together
+// before any of them is used.
+template <typename T, int P, bool FIRST>
+__global__ void __launch_bounds__(kWarpRowThreads, (P <= 4 ? 2 : 1)) row_pass_warp6(GridInfo g, const cplx<T>* __restrict__ twg,
+                                                                  T* __restrict__ E, cplx<T>* __restrict__ S,
+                                                                  const uint8_t* __restrict__ phase,
+                                                                  const T* __restrict__ dC, Control* ctl,
+                                                                  LoadState* st, double* __restrict__ partials,
+                                                                  double* __restrict__ hist, int blocks_per_load) {
+  constexpr int NV = 6, L = 32 * P, H = L / 2 + 1;
+  constexpr int WS = ((6 * H > 3 * L ? 6 * H : 3 * L) * 17 + 15) / 16 + 2;
+  constexpr int NW = kWarpRowThreads / 32;
+  constexpr int KI = (H + 31) / 32;   // half-spectrum entries per lane and component
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);          // L
+  cplx<T>* scratch = tw + L;                                    // NW * WS
+  __shared__ __align__(16) T dcs[16 * NV * NV];
+  __shared__ double red[32];
+  __shared__ int s_skip;
+  const int load = blockIdx.x / blocks_per_load;
+  const int qb = blockIdx.x - load * blocks_per_load;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < 16 * NV * NV; i += blockDim.x) dcs[i] = dC[i];
+  if (threadIdx.x == 0) s_skip = st[load].done;
+  __syncthreads();
+  ResAcc<T> acc_d, acc_n;
+  cplx<T>* ws = scratch + warp * WS;
+  if (!s_skip) {
+    T e0[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) e0[c] = (T)ctl->eps0[load][c];
+    const T scale = (T)g.inv_m;
+    const bool incremental = ctl->form == 1;
+    const size_t cstrS = (size_t)g.nrows * H;
+    const size_t cstrE = (size_t)g.m;
+    const int brev = bitrev5(lane);
+    const T* Eload = E + (size_t)load * NV * cstrE;
+    cplx<T>* Sload = S + (size_t)load * NV * cstrS;
+    for (long long row = (long long)qb * NW + warp; row < g.nrows; row += (long long)blocks_per_load * NW) {
+      T* Er = E + (size_t)load * NV * cstrE + row * L;
+      cplx<T>* Sr = Sload + row * H;
+      // 1. every global load of the row
+      cplx<T> sv[NV][KI];
+      T ev[NV][P];
+      int ph[P];
+      if (!FIRST) {
+#pragma unroll
+        for (int c = 0; c < NV; ++c)
+#pragma unroll
+          for (int i = 0; i < KI; ++i) {
+            const int k = lane + 32 * i;
+            if (k < H) sv[c][i] = Sr[c * cstrS + k];
+          }
+      }
+#pragma unroll
+      for (int c = 0; c < NV; ++c)
+#pragma unroll
+        for (int j = 0; j < P; ++j) ev[c][j] = Eload[c * cstrE + row * L + lane + 32 * j];
+#pragma unroll
+      for (int j = 0; j < P; ++j) ph[j] = phase[row * L + lane + 32 * j];
+      cplx<T> z[3][P];
+      if (!FIRST) {
+        // 2. Z = A + i B per line pair from the half spectra, inverse FFT
+#pragma unroll
+        for (int c = 0; c < NV; ++c)
+#pragma unroll
+          for (int i = 0; i < KI; ++i) {
+            const int k = lane + 32 * i;
+            if (k < H) ws[wpad(c * H + k)] = sv[c][i];
+          }
+        __syncwarp();
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+          for (int q = 0; q < P; ++q) {
+            const int k = q + P * brev;
+            const bool lo = k <= L / 2;
+            const int kk = lo ? k : L - k;
+            cplx<T> A = ws[wpad((2 * p) * H + kk)], B = ws[wpad((2 * p + 1) * H + kk)];
+            if (!lo) { A.y = -A.y; B.y = -B.y; }
+            z[p][q].x = A.x - B.y;
+            z[p][q].y = A.y + B.x;
+          }
+        __syncwarp();
+        warp_fft_inv<P, 3, T>(z, tw, lane);
+      }
+      // 3. pointwise: E_new, residual sums, tau
+      T rd = T(0), rn = T(0);
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        const int x = lane + 32 * j;
+        T en[NV];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+          if (FIRST) {
+            en[c] = ev[c][j];
+          } else {
+            en[c] = ((c & 1) ? z[c >> 1][j].y : z[c >> 1][j].x) * scale;
+            if (incremental) en[c] += ev[c][j];
+            const T dd = en[c] - ev[c][j], nn = en[c] + e0[c];
+            rd = fma(dd, dd, rd);
+            rn = fma(nn, nn, rn);
+            Er[c * cstrE + x] = en[c];
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          T dc[12];
+          load_rows<T>(dcs + ph[j] * NV * NV + 12 * a, dc);
+          T t0 = T(0), t1 = T(0);
+#pragma unroll
+          for (int b = 0; b < NV; ++b) {
+            t0 = fma(dc[b], en[b] + e0[b], t0);
+            t1 = fma(dc[NV + b], en[b] + e0[b], t1);
+          }
+          z[a][j].x = t0;
+          z[a][j].y = t1;
+        }
+      }
+      if (!FIRST) {
+        acc_d.add(rd);
+        acc_n.add(rn);
+      }
+      // 4. forward FFT, then split each line's spectrum into the half
+      //    spectra of its two components
+      warp_fft_fwd<P, 3, T>(z, tw, lane);
+#pragma unroll
+      for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int q = 0; q < P; ++q) ws[wpad(p * L + q + P * brev)] = z[p][q];
+      __syncwarp();
+#pragma unroll
+      for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int i = 0; i < KI; ++i) {
+          const int k = lane + 32 * i;
+          if (k < H) {
+            const cplx<T> zk = ws[wpad(p * L + k)];
+            const cplx<T> zm = ws[wpad(p * L + (k == 0 ? 0 : L - k))];
+            cplx<T> A, B;
+            A.x = T(0.5) * (zk.x + zm.x);
+            A.y = T(0.5) * (zk.y - zm.y);
+            B.x = T(0.5) * (zk.y + zm.y);
+            B.y = T(-0.5) * (zk.x - zm.x);
+            Sr[(2 * p) * cstrS + k] = A;
+            Sr[(2 * p + 1) * cstrS + k] = B;
+          }
+        }
+      __syncwarp();
+    }
+  }
+  if (FIRST) return;
+  const double d2 = block_sum(acc_d.value(), red);
+  const double n2 = block_sum(acc_n.value(), red);
+  __shared__ unsigned int s_ticket;
+  if (threadIdx.x == 0) {
+    partials[2 * (size_t)blockIdx.x] = d2;
+    partials[2 * (size_t)blockIdx.x + 1] = n2;
+    __threadfence();
+    s_ticket = atomicAdd(&ctl->ticket, 1u);
+  }
+  __syncthreads();
+  if (s_ticket != gridDim.x - 1) return;
+  __threadfence();
+  for (int load2 = 0; load2 < ctl->nload; ++load2) {
+    double a = 0.0, b = 0.0;
+    for (int q = threadIdx.x; q < blocks_per_load; q += blockDim.x) {
+      const size_t blk = (size_t)load2 * blocks_per_load + q;
+      a += __ldcg(&partials[2 * blk]);
+      b += __ldcg(&partials[2 * blk + 1]);
+    }
+    a = block_sum(a, red);
+    b = block_sum(b, red);
+    if (threadIdx.x == 0 && !st[load2].done) advance_state(st[load2], ctl, hist, load2, a, b);
+  }
+  if (threadIdx.x == 0) {
+    int all = 1;
+    for (int l = 0; l < ctl->nload; ++l) all &= st[l].done;
+    ctl->all_done = all;
+    ctl->ticket = 0u;
+    __threadfence();
+  }
+}
+
+template <typename T>
+__host__ inline size_t warprow_smem(int L) {
+  const int H = L / 2 + 1;
+  const int ws = ((6 * H > 3 * L ? 6 * H : 3 * L) * 17 + 15) / 16 + 2;
+  return (size_t)(L + (kWarpRowThreads / 32) * ws) * sizeof(T) * 2;
+}
+
+}  // namespace fh

@@ -109,6 +109,39 @@ class Case:
         return worst
 
 
+def sampled_iteration_check(fh, w, loads, n_prev, nsample, seed, tol, precision=0):
+    """One GPU iteration checked at sampled frequencies against the oracle.
+
+    The GPU runs n_prev iterations (E_prev), then one more (E_next).  On the CPU,
+    tau = (C - C0):(E_prev + eps0) is built with the oracle's own materials,
+    transformed with numpy's FFT on the oracle's Smith grid, and the oracle's
+    Gamma^p evaluated one frequency at a time at `nsample` random frequencies h
+    predicts E^_next(h) = -Gamma^p_h tau^(h) (Eq. (pde_coefficients)), compared
+    with the FFT of the GPU's E_next there.  `precision` selects the GPU's
+    arithmetic (0: FP64, 1: FP32)."""
+    case = Case.from_workload(w)   # oracle-side materials, generator, SNF grid (no table)
+    s = case.product(fh)
+    T = case.T
+    rng = np.random.default_rng(seed)
+    picks = rng.choice(T.m, size=nsample, replace=False)
+    picks = picks[np.any(T.freqs[picks] != 0, axis=1)]
+    Gp = np.stack([OGr.gamma_p(case.M, case.gen_o, case.C0_o, T.freqs[f]) for f in picks])
+    dC = case.Cp_o[case.ids] - case.C0_o[None]
+    inv = np.argsort(case.perm)            # oracle index -> product index
+    worst = 0.0
+    s.solve(case.eps0, tol=0.0, max_iter=n_prev, precision=precision)
+    prev = {L: s.get_strain(L)[:, inv].T.copy() for L in loads}   # (m, nv) oracle order
+    s.solve(case.eps0, tol=0.0, max_iter=1, init=1, precision=precision)
+    for L in loads:
+        nxt = s.get_strain(L)[:, inv].T
+        tau = np.einsum("mab,mb->ma", dC, prev[L] + case.eps0[L][None])
+        tau_h = T.fwd(tau.astype(complex))[picks]
+        pred = -np.einsum("hab,hb->ha", Gp, tau_h)
+        got = T.fwd(nxt.astype(complex))[picks]
+        worst = max(worst, np.abs(pred - got).max() / np.abs(got).max())
+    assert worst < tol, worst
+
+
 def rel(a, b):
     return np.abs(np.asarray(a) - np.asarray(b)).max() / np.abs(np.asarray(b)).max()
 

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from parity import Case, rel
+from parity import Case, rel, sampled_iteration_check as _sampled_iteration_check
 
 pytestmark = pytest.mark.gpu
 
@@ -273,39 +273,6 @@ def test_mixed_mode_continues_the_iteration_count(fh):
     assert list(b["iterations"]) == [i + 1 for i in a["iterations"]]
     h = s.get_residuals(0)
     assert len(h) == b["iterations"][0]
-
-
-def _sampled_iteration_check(fh, w, loads, n_prev, nsample, seed, tol):
-    """One GPU iteration checked at sampled frequencies against the oracle.
-
-    The GPU runs n_prev iterations (E_prev), then one more (E_next).  On the CPU,
-    tau = (C - C0):(E_prev + eps0) is built with the oracle's own materials,
-    transformed with numpy's FFT on the oracle's Smith grid, and the oracle's
-    Gamma^p evaluated one frequency at a time at `nsample` random frequencies h
-    predicts E^_next(h) = -Gamma^p_h tau^(h) (Eq. (pde_coefficients)), compared
-    with the FFT of the GPU's E_next there."""
-    from oracle import green as OGr, scheme as OS
-    case = Case.from_workload(w)   # oracle-side materials, generator, SNF grid (no table)
-    s = case.product(fh)
-    T = case.T
-    rng = np.random.default_rng(seed)
-    picks = rng.choice(T.m, size=nsample, replace=False)
-    picks = picks[np.any(T.freqs[picks] != 0, axis=1)]
-    Gp = np.stack([OGr.gamma_p(case.M, case.gen_o, case.C0_o, T.freqs[f]) for f in picks])
-    dC = case.Cp_o[case.ids] - case.C0_o[None]
-    inv = np.argsort(case.perm)            # oracle index -> product index
-    worst = 0.0
-    s.solve(case.eps0, tol=0.0, max_iter=n_prev)
-    prev = {L: s.get_strain(L)[:, inv].T.copy() for L in loads}   # (m, nv) oracle order
-    s.solve(case.eps0, tol=0.0, max_iter=1, init=1)
-    for L in loads:
-        nxt = s.get_strain(L)[:, inv].T
-        tau = np.einsum("mab,mb->ma", dC, prev[L] + case.eps0[L][None])
-        tau_h = T.fwd(tau.astype(complex))[picks]
-        pred = -np.einsum("hab,hb->ha", Gp, tau_h)
-        got = T.fwd(nxt.astype(complex))[picks]
-        worst = max(worst, np.abs(pred - got).max() / np.abs(got).max())
-    assert worst < tol, worst
 
 
 def test_full_size_box3d_iteration_sampled(fh):
