@@ -19,6 +19,7 @@
 #include "kernels.cuh"
 #include "cluster.cuh"
 #include "warprow.cuh"
+#include "linewarp.cuh"
 
 namespace fh {
 static thread_local std::string g_err;
@@ -222,6 +223,53 @@ void launch_line(fh_solver* s, int prec, int a, int mode, unsigned blocks, int n
   else launch_line_nv<T, 6>(s, prec, a, mode, blocks, n_outer, n_inner);
 }
 
+// Warp-per-column line pass (FP32, 3-D fields) for an axis of 32, 64, 128 or
+// 256 points: P = N / 32, else 0.
+int col_warp_p(const fh_solver* s, int prec, int a) {
+  if (prec != FH_PREC_FP32 || s->g.nv != 6) return 0;
+  const int N = s->g.dims[a];
+  return (N == 32 || N == 64 || N == 128 || N == 256) ? N / 32 : 0;
+}
+
+template <int P, int MODE>
+void launch_col_pass(fh_solver* s, int a, int nload) {
+  const GridInfo& g = s->g;
+  long long stride = g.H;
+  for (int k = a + 1; k + 1 < g.nd; ++k) stride *= g.dims[k];
+  const long long ncols = g.nhalf / g.dims[a];
+  const long long tiles = (ncols + fh::kColTile - 1) / fh::kColTile;
+  fh::line_pass_warp6<P, MODE><<<(unsigned)(tiles * nload), fh::kColThreads, fh::colpass_smem<P>(), s->work>>>(
+      g, s->ax[a].tw32, reinterpret_cast<float2*>(s->S), s->G32, s->st, stride, ncols, nload);
+}
+
+template <int P>
+void launch_col_pass_mode(fh_solver* s, int a, int mode, int nload) {
+  if (mode == 0) launch_col_pass<P, 0>(s, a, nload);
+  else if (mode == 1) launch_col_pass<P, 1>(s, a, nload);
+  else launch_col_pass<P, 2>(s, a, nload);
+}
+
+// line pass along axis a in the given mode (0 forward, 1 inverse, 2 forward +
+// Green + inverse), by the warp-per-column kernel where it applies
+template <typename T>
+void launch_axis(fh_solver* s, int prec, int a, int mode, int nload) {
+  const GridInfo& g = s->g;
+  if constexpr (sizeof(T) == 4) {
+    switch (col_warp_p(s, prec, a)) {
+      case 1: launch_col_pass_mode<1>(s, a, mode, nload); return;
+      case 2: launch_col_pass_mode<2>(s, a, mode, nload); return;
+      case 4: launch_col_pass_mode<4>(s, a, mode, nload); return;
+      case 8: launch_col_pass_mode<8>(s, a, mode, nload); return;
+      default: break;
+    }
+  }
+  long long n_outer = 1, n_inner = 1;
+  for (int k = 0; k < a; ++k) n_outer *= g.dims[k];
+  for (int k = a + 1; k + 1 < g.nd; ++k) n_inner *= g.dims[k];
+  const long long blocks = (long long)nload * n_outer * n_inner * s->ntiles[prec][a];
+  launch_line<T>(s, prec, a, mode, (unsigned)blocks, (int)n_outer, (int)n_inner);
+}
+
 // Enqueue the line passes of one iteration (everything between two row passes).
 template <typename T>
 void enqueue_line_passes(fh_solver* s, int prec, int nload) {
@@ -234,13 +282,7 @@ void enqueue_line_passes(fh_solver* s, int prec, int nload) {
     fh::green_1d<T><<<blocks, kThreads, 0, s->work>>>(g, S, Gptr<T>(s), s->st, nload);
     return;
   }
-  auto launch = [&](int a, int mode) {
-    long long n_outer = 1, n_inner = 1;
-    for (int k = 0; k < a; ++k) n_outer *= g.dims[k];
-    for (int k = a + 1; k + 1 < g.nd; ++k) n_inner *= g.dims[k];
-    const long long blocks = (long long)nload * n_outer * n_inner * s->ntiles[prec][a];
-    launch_line<T>(s, prec, a, mode, (unsigned)blocks, (int)n_outer, (int)n_inner);
-  };
+  auto launch = [&](int a, int mode) { launch_axis<T>(s, prec, a, mode, nload); };
   // forward along axes nd-2 .. 1, then axis 0 with the Green step, then inverse 1 .. nd-2
   for (int a = g.nd - 2; a >= 1; --a) launch(a, 0);
   launch(0, 2);
@@ -295,6 +337,15 @@ cudaError_t set_warp_attrs(fh_solver* s, int prec, size_t rs) {
                                                        fh::kWarpRowThreads, rs);
 }
 
+template <int P>
+cudaError_t set_col_attrs() {
+  const int sm = (int)fh::colpass_smem<P>();
+  cudaError_t e = cudaFuncSetAttribute(fh::line_pass_warp6<P, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(fh::line_pass_warp6<P, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(fh::line_pass_warp6<P, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  return e;
+}
+
 template <typename T, int NV>
 fh_status set_smem_attrs_nv(fh_solver* s, int prec) {
   const size_t rs = s->row_smem[prec];
@@ -315,7 +366,18 @@ fh_status set_smem_attrs_nv(fh_solver* s, int prec) {
     }
   }
   size_t lm = 0;
-  for (int a = 0; a + 1 < s->g.nd; ++a) lm = std::max(lm, s->line_smem[prec][a]);
+  for (int a = 0; a + 1 < s->g.nd; ++a) {
+    if constexpr (sizeof(T) == 4) {
+      switch (col_warp_p(s, prec, a)) {
+        case 1: CK((set_col_attrs<1>())); continue;
+        case 2: CK((set_col_attrs<2>())); continue;
+        case 4: CK((set_col_attrs<4>())); continue;
+        case 8: CK((set_col_attrs<8>())); continue;
+        default: break;
+      }
+    }
+    lm = std::max(lm, s->line_smem[prec][a]);
+  }
   if (lm > kMaxSmem) {
     fh::set_error("axis too long for this precision (shared memory)");
     return FH_ERR_UNSUPPORTED;
@@ -599,13 +661,7 @@ fh_status profile_passes(fh_solver* s, int prec, int nload, int reps, double* ms
   };
   rc = timed(0, [&] { enqueue_row_pass<T, false>(s, prec, nload); });
   if (rc != FH_OK) return rc;
-  auto line = [&](int a, int mode) {
-    long long n_outer = 1, n_inner = 1;
-    for (int k = 0; k < a; ++k) n_outer *= g.dims[k];
-    for (int k = a + 1; k + 1 < g.nd; ++k) n_inner *= g.dims[k];
-    const unsigned blocks = (unsigned)((long long)nload * n_outer * n_inner * s->ntiles[prec][a]);
-    launch_line<T>(s, prec, a, mode, blocks, (int)n_outer, (int)n_inner);
-  };
+  auto line = [&](int a, int mode) { launch_axis<T>(s, prec, a, mode, nload); };
   if (g.nd == 1) {
     rc = timed(1, [&] {
       const long long total = (long long)nload * g.nhalf;

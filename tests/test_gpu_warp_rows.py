@@ -1,7 +1,8 @@
-"""The FP32 warp-per-row pass of 3-D grids (contiguous axis of 32, 64, 128 or
-256 points) against the FP64 oracle: fixed-iteration tracking for every row
-length, grids with fewer rows than a block has warps, one- and two-axis Smith
-grids, the variational form, resumption, and a full-size sampled iteration.
+"""The FP32 warp-per-row and warp-per-column passes of 3-D grids (axes of 32,
+64, 128 or 256 points) against the FP64 oracle: fixed-iteration tracking for
+every row and column length, grids with fewer rows than a block has warps,
+one- and two-axis Smith grids, axes that mix the warp and block passes, the
+variational form, resumption, and full-size sampled iterations.
 """
 import numpy as np
 import pytest
@@ -46,6 +47,15 @@ WARP_CASES = [
      [(1.0, 0.3), (8.0, 0.3)], _ball(0.3), [2, 2, 256]),
     ("L64_single_row", [[1, 0, 0], [0, 1, 0], [0, 0, 64]], {"kind": "dirichlet"},
      [(1.0, 0.3), (5.0, 0.3)], _ball(0.3), [64]),
+    # warp-per-column passes: every axis, only the middle axis, a sheared grid
+    ("cols32_cube", [[32, 0, 0], [0, 32, 0], [0, 0, 32]], {"kind": "dlvp", "alpha": [0.25, 0.25, 0.25]},
+     [(1.0, 0.3), (25.0, 0.3)], _ball(0.2), [32, 32, 32]),
+    ("cols_middle_axis", [[32, 0, 0], [0, 8, 0], [0, 0, 64]], {"kind": "dirichlet"},
+     [(1.0, 0.3), (10.0, 0.25)], _ball(0.3), [8, 32, 64]),
+    ("cols_sheared", [[32, 8, 0], [0, 32, 0], [0, 0, 32]], {"kind": "boxspline", "order": 2, "radius": 2},
+     [(1.0, 0.3), (40.0, 0.3)], _ball(0.25), [8, 32, 128]),
+    ("cols64", [[32, 0, 0], [0, 64, 0], [0, 0, 64]], {"kind": "dirichlet"},
+     [(1.0, 0.3), (50.0, 0.3)], _ball(0.15), [32, 64, 64]),
 ]
 IDS = [c[0] for c in WARP_CASES]
 
@@ -125,6 +135,17 @@ def test_full_size_box3d_fp32_iteration_sampled(fh):
     """M = diag(128,128,128) (rows of 128 points), box spline of order 2 with
     alias radius 4, 6 loads: one FP32 iteration at 300 sampled frequencies."""
     sampled_iteration_check(fh, W.box3d(), loads=[0, 4], n_prev=3, nsample=300, seed=9, tol=2e-5, precision=FP32)
+
+
+def test_full_size_column_axis_of_256_sampled(fh):
+    """M = diag(32, 256, 256): a column axis and rows of 256 points, random
+    spheres, Dirichlet kernel: one FP32 iteration at 300 sampled frequencies."""
+    rng = np.random.default_rng(11)
+    c, r = W.random_inclusions(rng, 3, 12, 0.05, 0.1)
+    w = {"M": [[32, 0, 0], [0, 256, 0], [0, 0, 256]], "generator": {"kind": "dirichlet"},
+         "phases": [(1.0, 0.3), (30.0, 0.3)], "centres": c, "radii": r}
+    assert fh.Pattern(w["M"]).dims == [32, 256, 256]
+    sampled_iteration_check(fh, w, loads=[1, 5], n_prev=3, nsample=300, seed=12, tol=2e-5, precision=FP32)
 
 
 def test_full_size_fno3d_fp32_iteration_sampled(fh):
