@@ -16,6 +16,10 @@ error against the converged FP64 oracle (tests/golden/ceff_dlvp_sheared.txt).
 The headline is the mode selected with --mode (default: mixed, the fastest mode
 whose C_eff meets 1e-6).
 
+The line also carries the batched 2-D workload (512 microstructures) and the
+3-D box-spline workload (M = diag(128,128,128), 6 loads: time to 1e-6 per
+precision mode and the HBM roofline of each pass of one iteration).
+
 Prints one JSON line (rank 0).  --impl reference runs the FP64 CPU oracle on a
 bounded sample of the same workload instead.
 """
@@ -56,6 +60,12 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-cluster", type=int, default=0)
+    ap.add_argument("--no-box3d", action="store_true")
+    ap.add_argument("--only-box3d", action="store_true",
+                    help="run only the 3-D box-spline section (prints its JSON object)")
+    ap.add_argument("--box3d-n", type=int, default=128, help="grid size of the 3-D section")
+    ap.add_argument("--box3d-modes", default="mixed,fp32,fp64",
+                    help="precision modes of the 3-D section (comma-separated)")
     return ap.parse_args()
 
 
@@ -368,6 +378,100 @@ def run_batched(fh, steps, cluster):
                       "loads, working set > L2)", "gpu_launches": launches}
 
 
+def hbm_peak():
+    """Measured copy bandwidth of the GB300s (GB/s), else the fallback figure."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s (of fallback)"
+
+
+def run_box3d(fh, args):
+    """The 3-D workload: M = diag(n,n,n) (n = 128: m = 2 097 152), tensor-product
+    box spline of order 2 with alias radius 4, 50 spheres (seed 3) at contrast
+    50, the 6 Mandel unit loads.  The Gamma^p table is built once (a one-off
+    precompute, timed separately); one step is one solve of all 6 loads to
+    r <= tol.  Mixed and FP32 run `steps` steps, FP64 one.  Then the passes of
+    one iteration are timed alone (fh_profile_passes, CUDA events) and divided
+    into the bytes each must move: the HBM roofline of the 3-D kernels."""
+    import torch
+    n = args.box3d_n
+    w = W.box3d(n=n)
+    p = fh.Pattern(w["M"])
+    ids = W.phase_ids(p.points(), w["centres"], w["radii"])
+    Cp = np.stack([fh.isotropic_stiffness(*fh.lame(E, nu), 3) for E, nu in w["phases"]])
+    stream = torch.cuda.current_stream().cuda_stream
+    s = fh.Solver(p, fh.tensor_boxspline(3, 2, 4), 6, stream)
+    s.set_stiffness_phases(ids, Cp)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    s.set_reference(None)
+    e1.record()
+    e1.synchronize()
+    table_ms = e0.elapsed_time(e1)
+    eps0 = np.eye(6)
+    prec = {"fp64": fh.FH_PREC_FP64, "fp32": fh.FH_PREC_FP32, "mixed": fh.FH_PREC_MIXED}
+    modes, launches = {}, 0
+    wanted = [m for m in ("mixed", "fp32", "fp64") if m in args.box3d_modes.split(",")]
+    for mode, steps in [(m, args.steps if m != "fp64" else 1) for m in wanted]:
+        s.solve(eps0, tol=0.0, max_iter=5, precision=prec[mode])      # warm-up (graph capture)
+        times, out = [], None
+        for _ in range(steps):
+            e0.record()
+            out = s.solve(eps0, tol=args.tol, max_iter=20000, precision=prec[mode])
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        it = [int(x) for x in out["iterations"]]
+        modes[mode] = {"time_to_tol_ms": float(np.median(times)), "iterations": it,
+                       "ms_per_iteration": float(np.median(times)) / max(it),
+                       "voxel_iterations_per_s": p.m * sum(it) / (float(np.median(times)) * 1e-3),
+                       "status": int(out["status"]), "load_status": [int(x) for x in out["load_status"]],
+                       "ceff": s.get_ceff().tolist()}
+        if mode == "mixed":
+            launches = out["kernel_launches"]
+    if "fp64" in modes:
+        C64 = np.array(modes["fp64"]["ceff"])
+        for mode in modes:
+            if mode != "fp64":
+                modes[mode]["ceff_rel_err_vs_fp64"] = float(np.linalg.norm(np.array(modes[mode]["ceff"]) - C64)
+                                                            / np.linalg.norm(C64))
+    # per-pass roofline
+    nhalf = len(p.half_freqs())
+    peak, peak_src = hbm_peak()
+    passes = {}
+    for mode, rb, cb in [x for x in (("fp32", 4, 8), ("fp64", 8, 16)) if x[0] in wanted]:
+        s.solve(eps0, tol=0.0, max_iter=3, precision=prec[mode])
+        ms = s.profile_passes(6, prec[mode], reps=20)
+        spec = 6 * 6 * nhalf * cb                       # all loads' half spectra, one way
+        field = 6 * 6 * p.m * rb                        # all loads' strain fields, one way
+        table = 21 * nhalf * rb
+        bytes_ = {"row_pass": 2 * spec + 2 * field + p.m, "axis0_green_pass": 2 * spec + table,
+                  "axis1_forward_pass": 2 * spec, "axis1_inverse_pass": 2 * spec}
+        names = list(bytes_)
+        passes[mode] = {k: {"ms": float(ms[i]), "bytes": int(bytes_[k]),
+                            "gbs": bytes_[k] / (ms[i] * 1e-3) / 1e9,
+                            "frac_of_hbm": bytes_[k] / (ms[i] * 1e-3) / 1e9 / peak} for i, k in enumerate(names)}
+        tot_b = sum(bytes_.values())
+        tot_ms = float(sum(ms))
+        # the method's own minimum per iteration: read and write every strain
+        # field once, the phase ids and the table once
+        algo = 6 * 6 * p.m * rb * 2 + p.m + table
+        passes[mode]["iteration"] = {"ms": tot_ms, "bytes": int(tot_b), "gbs": tot_b / (tot_ms * 1e-3) / 1e9,
+                                     "frac_of_hbm": tot_b / (tot_ms * 1e-3) / 1e9 / peak,
+                                     "algorithmic_bytes": int(algo),
+                                     "algorithmic_gbs": algo / (tot_ms * 1e-3) / 1e9}
+    s.close()
+    return {"workload": f"box3d: M=diag({n},{n},{n}) (m={p.m}, grid {p.dims}), box spline order 2 alias radius 4 "
+                        f"(729 aliases), 50 spheres r~U[0.05,0.1] seed 3, contrast 50, 6 Mandel unit loads, "
+                        f"tol {args.tol}",
+            "table_build_ms": table_ms, "modes": modes, "passes": passes, "hbm_peak_gbs": peak,
+            "hbm_peak_source": peak_src, "gpu_launches_mixed_step": launches,
+            "timing": "CUDA events on the solver's stream; working set (1.2 GB FP32) larger than L2"}
+
+
 def measured_fp_peak(mode):
     """Dense peak of the arithmetic type measured here with cuBLAS (DGEMM / SGEMM without TF32)."""
     import torch
@@ -410,11 +514,23 @@ def main():
         dist.init_process_group("nccl")
     from paper_1701_04685_gb300 import build
     build.build()
+    if args.only_box3d:
+        import torch
+        torch.cuda.set_device(local_rank)
+        import paper_1701_04685_gb300 as fh
+        box = run_box3d(fh, args)
+        if rank == 0:
+            print(json.dumps({"box3d": box}), flush=True)
+        return
     results, e2e, roofline, clocks = run_gpu(args, rank, world, local_rank)
     batched = None
     if not args.no_batched:
         import paper_1701_04685_gb300 as fh
         batched = run_batched(fh, min(args.steps, 3), args.batch_cluster)
+    box = None
+    if not args.no_box3d:
+        import paper_1701_04685_gb300 as fh
+        box = run_box3d(fh, args)
     if rank != 0:
         return
     cpu = None
@@ -434,6 +550,7 @@ def main():
         "time_to_tol_ms": head["ms_per_step"],
         "modes": results,
         "batched": batched,
+        "box3d": box,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
