@@ -287,29 +287,36 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
   }
   cluster.sync();
   double* part0 = cluster.map_shared_rank(part, 0);
+  __shared__ int s_done;
   for (int it = 0; it < max_iter && !s.done; ++it) {
     col_phase();
     cluster.sync();
     ResAcc<T> acc_d, acc_n;
     row_phase(true, acc_d, acc_n);
-    const double d2 = block_sum(acc_d.value(), red);
-    const double n2 = block_sum(acc_n.value(), red);
+    const double d2 = block_sum_acc(acc_d, red);
+    const double n2 = block_sum_acc(acc_n, red);
     if (threadIdx.x == 0) {
       part0[2 * rank] = d2;
       part0[2 * rank + 1] = n2;
     }
     cluster.sync();
-    // every CTA sums the partials in the same order and takes the same decision
-    double a = 0.0, b = 0.0;
-    for (int q = 0; q < CS; ++q) {
-      a += part0[2 * q];
-      b += part0[2 * q + 1];
+    // thread 0 of every CTA sums the partials in the same order and takes the
+    // same decision; the other threads only need the stop flag
+    if (threadIdx.x == 0) {
+      double a = 0.0, b = 0.0;
+      for (int q = 0; q < CS; ++q) {
+        a += part0[2 * q];
+        b += part0[2 * q + 1];
+      }
+      if (rank == 0) {
+        LoadState t = s;
+        advance_state(t, ctl, hist, load, a, b);
+      }
+      update_state(s, a, b, tol, max_iter, stall_window);
+      s_done = s.done;
     }
-    if (rank == 0 && threadIdx.x == 0) {
-      LoadState t = s;
-      advance_state(t, ctl, hist, load, a, b);
-    }
-    update_state(s, a, b, tol, max_iter, stall_window);   // the same update in every thread
+    __syncthreads();
+    s.done = s_done;
   }
   // ---- results
   for (int i = threadIdx.x; i < nrow * L; i += blockDim.x) {
@@ -317,7 +324,7 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
 #pragma unroll
     for (int c = 0; c < NV; ++c) Eg[Ebase + (size_t)c * m + (r0 + r) * L + x] = El[(r * NV + c) * L + x];
   }
-  if (rank == 0 && threadIdx.x == 0) st[load] = s;
+  if (rank == 0 && threadIdx.x == 0) st[load] = s;   // thread 0 holds the full state
   cluster.sync();  // keep every CTA's shared memory alive until remote accesses are done
 }
 

@@ -125,6 +125,34 @@ template <> struct ResAcc<float> {
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// Block sum of the per-thread accumulators; result valid in thread 0.  The
+// FP32 variant reduces the double-float pairs across each warp with exact
+// TwoSum steps in FP32 and converts once per warp, so the narrow FP64 pipe
+// sees a handful of operations per block instead of several per thread.
+__device__ __forceinline__ double block_sum_acc(const ResAcc<double>& a, double* red) { return block_sum(a.value(), red); }
+__device__ __forceinline__ double block_sum_acc(const ResAcc<float>& a, double* red) {
+  float hi = a.hi, lo = a.lo;
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ohi = __shfl_down_sync(0xffffffffu, hi, o);
+    const float olo = __shfl_down_sync(0xffffffffu, lo, o);
+    const float s = hi + ohi;                 // TwoSum(hi, ohi)
+    const float bp = s - hi;
+    const float e = (hi - (s - bp)) + (ohi - bp);
+    hi = s;
+    lo = lo + olo + e;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = (double)hi + (double)lo;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) t += red[i];
+  }
+  return t;
+}
+
 // Advance the per-load state after one iteration's residual is known:
 // r_n = sqrt(d2 / n2) (Sec. 4's Cauchy criterion), then the stop tests.
 __device__ __forceinline__ void update_state(LoadState& s, double d2, double n2, double tol, int max_iter,
@@ -298,8 +326,8 @@ __global__ void __launch_bounds__(256, PassOcc<T>::value) row_pass(GridInfo g, D
   }
   if (FIRST) return;
   // 6. partial sums of this block
-  const double d2 = block_sum(acc_d.value(), red);
-  const double n2 = block_sum(acc_n.value(), red);
+  const double d2 = block_sum_acc(acc_d, red);
+  const double n2 = block_sum_acc(acc_n, red);
   __shared__ unsigned int s_ticket;
   if (threadIdx.x == 0) {
     partials[2 * (size_t)blockIdx.x] = d2;

@@ -304,8 +304,8 @@ __global__ void __launch_bounds__(kWarpRowThreads, (P <= 4 ? 2 : 1)) row_pass_wa
     }
   }
   if (FIRST) return;
-  const double d2 = block_sum(acc_d.value(), red);
-  const double n2 = block_sum(acc_n.value(), red);
+  const double d2 = block_sum_acc(acc_d, red);
+  const double n2 = block_sum_acc(acc_n, red);
   __shared__ unsigned int s_ticket;
   if (threadIdx.x == 0) {
     partials[2 * (size_t)blockIdx.x] = d2;
