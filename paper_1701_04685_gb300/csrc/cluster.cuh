@@ -77,12 +77,13 @@ __host__ __device__ inline ClusterLayout cluster_layout(int N0, int L, int nv, i
   return c;
 }
 
-// threads per CTA (8 warps: 16 warps measured slower, the 128-register cap
-// spills the radix-8 butterflies)
-template <typename T> struct ClusterThreads { static constexpr int value = 256; };
+// threads per CTA: 8 warps for general radix plans (with the 11- and
+// 13-point stages compiled in, 16 warps would cap registers at 128 and
+// spill); 16 warps for plans of radices 2, 4, 8 only
+template <typename T, bool POW2> struct ClusterThreads { static constexpr int value = POW2 ? 512 : 256; };
 
-template <typename T, int NV, int CS>
-__global__ void __launch_bounds__(ClusterThreads<T>::value, 1)
+template <typename T, int NV, int CS, bool POW2>
+__global__ void __launch_bounds__(ClusterThreads<T, POW2>::value, 1)
 cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __restrict__ tw0g,
                  const cplx<T>* __restrict__ tw1g, T* __restrict__ Eg, const uint8_t* __restrict__ phase,
                  const T* __restrict__ dC, int nphase, const T* __restrict__ Gt, Control* ctl, LoadState* st,
@@ -178,7 +179,7 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
         W0[p * Lp + padi<PS>(k)] = z;
       }
       __syncthreads();
-      Z = fft_lines_pp<+1, T, PS>(W0, W1, npair, Lp, plan1, tw1);
+      Z = fft_lines_pp<+1, T, PS, POW2>(W0, W1, npair, Lp, plan1, tw1);
       Zo = (Z == W0) ? W1 : W0;
     }
     for (int idx = threadIdx.x; idx < nrow * L; idx += blockDim.x) {
@@ -213,7 +214,7 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
     if (nreal & 1)
       for (int x = threadIdx.x; x < L; x += blockDim.x) Z[(npair - 1) * Lp + padi<PS>(x)].y = T(0);
     __syncthreads();
-    cplx<T>* Zf = fft_lines_pp<-1, T, PS>(Z, Zo, npair, Lp, plan1, tw1);
+    cplx<T>* Zf = fft_lines_pp<-1, T, PS, POW2>(Z, Zo, npair, Lp, plan1, tw1);
     for (int idx = threadIdx.x; idx < npair * H; idx += blockDim.x) {
       const int p = fdiv(idx, fH), k = idx - p * H;
       const cplx<T> zk = Zf[p * Lp + padi<PS>(k)];
@@ -240,7 +241,7 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
       X0[(c * ncol + j) * N0p + n] = rem[((int)loc[n] * NV + c) * H + c0 + j];
     }
     __syncthreads();
-    cplx<T>* Xf = fft_lines_pp<-1, T>(X0, X1, nl, N0p, plan0, tw0);
+    cplx<T>* Xf = fft_lines_pp<-1, T, 0, POW2>(X0, X1, nl, N0p, plan0, tw0);
     for (int idx = threadIdx.x; idx < N0 * ncol; idx += blockDim.x) {
       const int n = fdiv(idx, fnc);
       const int j = idx - n * ncol;
@@ -269,7 +270,7 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
       }
     }
     __syncthreads();
-    cplx<T>* Xi = fft_lines_pp<+1, T>(Xf, Xf == X0 ? X1 : X0, nl, N0p, plan0, tw0);
+    cplx<T>* Xi = fft_lines_pp<+1, T, 0, POW2>(Xf, Xf == X0 ? X1 : X0, nl, N0p, plan0, tw0);
     for (int idx = threadIdx.x; idx < NV * N0 * ncol; idx += blockDim.x) {
       const int t = fdiv(idx, fnc);
       const int j = idx - t * ncol;

@@ -217,7 +217,9 @@ __device__ __forceinline__ void stockham_stage(const cplx<T>* in, cplx<T>* out, 
 // occupies buf[q*ls .. q*ls + L); tmp has the same shape (ping-pong buffer).
 // Every thread of the block must call this.  Returns the buffer (buf or tmp)
 // that holds the result; a __syncthreads() has been executed on return.
-template <int DIR, typename T, int PADSH = 0>
+// POW2: the plan uses radices 2, 4 and 8 only (the caller checks); the other
+// stage kernels are then not compiled in, which keeps register use low.
+template <int DIR, typename T, int PADSH = 0, bool POW2 = false>
 __device__ cplx<T>* fft_lines_pp(cplx<T>* buf, cplx<T>* tmp, int nlines, int ls, const DevPlan& plan,
                                  const cplx<T>* __restrict__ tw) {
   const int L = plan.L;
@@ -226,15 +228,23 @@ __device__ cplx<T>* fft_lines_pp(cplx<T>* buf, cplx<T>* tmp, int nlines, int ls,
   int Ns = 1;
   for (int s = 0; s < plan.np; ++s) {
     const int r = plan.r[s];
-    switch (r) {
-      case 2: stockham_stage<2, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
-      case 3: stockham_stage<3, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
-      case 4: stockham_stage<4, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
-      case 5: stockham_stage<5, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
-      case 7: stockham_stage<7, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
-      case 8: stockham_stage<8, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
-      case 11: stockham_stage<11, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
-      default: stockham_stage<13, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
+    if constexpr (POW2) {
+      switch (r) {
+        case 2: stockham_stage<2, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
+        case 4: stockham_stage<4, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
+        default: stockham_stage<8, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
+      }
+    } else {
+      switch (r) {
+        case 2: stockham_stage<2, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
+        case 3: stockham_stage<3, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
+        case 4: stockham_stage<4, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
+        case 5: stockham_stage<5, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
+        case 7: stockham_stage<7, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
+        case 8: stockham_stage<8, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
+        case 11: stockham_stage<11, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
+        default: stockham_stage<13, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
+      }
     }
     __syncthreads();
     cplx<T>* sw = in; in = out; out = sw;

@@ -454,8 +454,19 @@ fh_status run_solve(fh_solver* s, int prec, int nload, int chunk, int max_iter, 
   return FH_OK;
 }
 
+// both axis plans use radices 2, 4, 8 only: the cluster kernel variant
+// without the other stages (fewer registers, 16 warps per CTA)
+bool pow2_plans(const fh_solver* s) {
+  for (int a = 0; a < 2; ++a)
+    for (int q = 0; q < s->ax[a].plan.np; ++q) {
+      const int r = s->ax[a].plan.r[q];
+      if (r != 2 && r != 4 && r != 8) return false;
+    }
+  return true;
+}
+
 // Cluster-resident path (2-axis grids): one cluster of CS CTAs per load case.
-template <typename T, int NV, int CS>
+template <typename T, int NV, int CS, bool POW2>
 fh_status cluster_fits_nv(fh_solver* s, bool* ok) {
   *ok = false;
   const GridInfo& g = s->g;
@@ -468,12 +479,12 @@ fh_status cluster_fits_nv(fh_solver* s, bool* ok) {
   }
   if (lay.total + 1024 > kMaxSmem) return FH_OK;
   s->cl_gsmem[sizeof(T) == 8 ? 0 : 1][CS == 16 ? 1 : 0] = gs;
-  auto kern = fh::cluster_solve_2d<T, NV, CS>;
+  auto kern = fh::cluster_solve_2d<T, NV, CS, POW2>;
   CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total));
   if (CS > 8) CK(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CS);
-  cfg.blockDim = dim3(fh::ClusterThreads<T>::value);
+  cfg.blockDim = dim3(fh::ClusterThreads<T, POW2>::value);
   cfg.dynamicSmemBytes = lay.total;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -493,18 +504,20 @@ fh_status cluster_fits_nv(fh_solver* s, bool* ok) {
 
 template <typename T, int CS>
 fh_status cluster_fits(fh_solver* s, bool* ok) {
-  return s->g.nv == 3 ? cluster_fits_nv<T, 3, CS>(s, ok) : cluster_fits_nv<T, 6, CS>(s, ok);
+  if (pow2_plans(s))
+    return s->g.nv == 3 ? cluster_fits_nv<T, 3, CS, true>(s, ok) : cluster_fits_nv<T, 6, CS, true>(s, ok);
+  return s->g.nv == 3 ? cluster_fits_nv<T, 3, CS, false>(s, ok) : cluster_fits_nv<T, 6, CS, false>(s, ok);
 }
 
-template <typename T, int NV, int CS>
+template <typename T, int NV, int CS, bool POW2>
 fh_status launch_cluster_nv(fh_solver* s, int nload) {
   const GridInfo& g = s->g;
   const bool gs = s->cl_gsmem[sizeof(T) == 8 ? 0 : 1][CS == 16 ? 1 : 0];
   const fh::ClusterLayout lay = fh::cluster_layout<T>(g.dims[0], g.L, g.nv, CS, gs);
-  auto kern = fh::cluster_solve_2d<T, NV, CS>;
+  auto kern = fh::cluster_solve_2d<T, NV, CS, POW2>;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nload * CS);
-  cfg.blockDim = dim3(fh::ClusterThreads<T>::value);
+  cfg.blockDim = dim3(fh::ClusterThreads<T, POW2>::value);
   cfg.dynamicSmemBytes = lay.total;
   cfg.stream = s->work;
   cudaLaunchAttribute attr[1];
@@ -523,7 +536,9 @@ fh_status launch_cluster_nv(fh_solver* s, int nload) {
 
 template <typename T, int CS>
 fh_status launch_cluster(fh_solver* s, int nload) {
-  return s->g.nv == 3 ? launch_cluster_nv<T, 3, CS>(s, nload) : launch_cluster_nv<T, 6, CS>(s, nload);
+  if (pow2_plans(s))
+    return s->g.nv == 3 ? launch_cluster_nv<T, 3, CS, true>(s, nload) : launch_cluster_nv<T, 6, CS, true>(s, nload);
+  return s->g.nv == 3 ? launch_cluster_nv<T, 3, CS, false>(s, nload) : launch_cluster_nv<T, 6, CS, false>(s, nload);
 }
 
 // Pick path and cluster size; returns 1 (passes) or 2 (cluster) in *path.
