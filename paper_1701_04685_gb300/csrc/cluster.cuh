@@ -90,7 +90,6 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
                  double* __restrict__ hist, int g_smem) {
   constexpr int NTRI = NV * (NV + 1) / 2;
   extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ double red[32];
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int load = blockIdx.x / CS;
@@ -287,34 +286,38 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
     row_phase(false, a, b);
   }
   cluster.sync();
-  double* part0 = cluster.map_shared_rank(part, 0);
   __shared__ int s_done;
+  __shared__ double2 red2[32];
+  const int hist_cap = ctl->hist_cap;
   for (int it = 0; it < max_iter && !s.done; ++it) {
     col_phase();
     cluster.sync();
     ResAcc<T> acc_d, acc_n;
     row_phase(true, acc_d, acc_n);
-    const double d2 = block_sum_acc(acc_d, red);
-    const double n2 = block_sum_acc(acc_n, red);
-    if (threadIdx.x == 0) {
-      part0[2 * rank] = d2;
-      part0[2 * rank + 1] = n2;
+    // this CTA's partial sums, pushed into every CTA's `part` (lane q of
+    // warp 0 stores into CTA q), so that after the barrier all reads are local
+    double d2 = 0.0, n2 = 0.0;
+    block_sum_pair(acc_d, acc_n, red2, d2, n2);
+    if (threadIdx.x < CS) {
+      double* dst = cluster.map_shared_rank(part, (int)threadIdx.x);
+      dst[2 * rank] = d2;
+      dst[2 * rank + 1] = n2;
     }
     cluster.sync();
-    // thread 0 of every CTA sums the partials in the same order and takes the
-    // same decision; the other threads only need the stop flag
-    if (threadIdx.x == 0) {
-      double a = 0.0, b = 0.0;
-      for (int q = 0; q < CS; ++q) {
-        a += part0[2 * q];
-        b += part0[2 * q + 1];
+    // warp 0 of every CTA sums the CS partials in the same fixed order and
+    // takes the same decision; the other threads only need the stop flag
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      double a = lane < CS ? part[2 * lane] : 0.0, b = lane < CS ? part[2 * lane + 1] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
       }
-      if (rank == 0) {
-        LoadState t = s;
-        advance_state(t, ctl, hist, load, a, b);
+      if (lane == 0) {
+        update_state(s, a, b, tol, max_iter, stall_window);
+        if (rank == 0 && s.iter <= hist_cap) hist[(size_t)load * hist_cap + (s.iter - 1)] = s.r;
+        s_done = s.done;
       }
-      update_state(s, a, b, tol, max_iter, stall_window);
-      s_done = s.done;
     }
     __syncthreads();
     s.done = s_done;

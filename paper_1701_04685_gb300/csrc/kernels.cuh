@@ -153,6 +153,64 @@ __device__ __forceinline__ double block_sum_acc(const ResAcc<float>& a, double* 
   return t;
 }
 
+// Both residual accumulators of a block reduced in one pass (one block
+// barrier); the sums are valid in every lane of warp 0.  `red2` holds >= 32
+// double2.  Fixed order, so every launch of the same shape gives the same bits.
+__device__ __forceinline__ void two_sum_merge(float& hi, float& lo, float ohi, float olo) {
+  const float s = hi + ohi;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (ohi - bp);
+  hi = s;
+  lo = lo + olo + e;
+}
+__device__ __forceinline__ void block_sum_pair(const ResAcc<float>& a, const ResAcc<float>& b, double2* red2,
+                                               double& d2, double& n2) {
+  float ah = a.hi, al = a.lo, bh = b.hi, bl = b.lo;
+  for (int o = 16; o > 0; o >>= 1) {
+    two_sum_merge(ah, al, __shfl_down_sync(0xffffffffu, ah, o), __shfl_down_sync(0xffffffffu, al, o));
+    two_sum_merge(bh, bl, __shfl_down_sync(0xffffffffu, bh, o), __shfl_down_sync(0xffffffffu, bl, o));
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float4* red4 = reinterpret_cast<float4*>(red2);
+  if (lane == 0) red4[w] = make_float4(ah, al, bh, bl);
+  __syncthreads();
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    const float4 v = lane < nw ? red4[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    ah = v.x; al = v.y; bh = v.z; bl = v.w;
+    for (int o = 16; o > 0; o >>= 1) {
+      two_sum_merge(ah, al, __shfl_down_sync(0xffffffffu, ah, o), __shfl_down_sync(0xffffffffu, al, o));
+      two_sum_merge(bh, bl, __shfl_down_sync(0xffffffffu, bh, o), __shfl_down_sync(0xffffffffu, bl, o));
+    }
+    ah = __shfl_sync(0xffffffffu, ah, 0); al = __shfl_sync(0xffffffffu, al, 0);
+    bh = __shfl_sync(0xffffffffu, bh, 0); bl = __shfl_sync(0xffffffffu, bl, 0);
+    d2 = (double)ah + (double)al;
+    n2 = (double)bh + (double)bl;
+  }
+}
+__device__ __forceinline__ void block_sum_pair(const ResAcc<double>& a, const ResAcc<double>& b, double2* red2,
+                                               double& d2, double& n2) {
+  double x = a.s, y = b.s;
+  for (int o = 16; o > 0; o >>= 1) {
+    x += __shfl_down_sync(0xffffffffu, x, o);
+    y += __shfl_down_sync(0xffffffffu, y, o);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red2[w] = make_double2(x, y);
+  __syncthreads();
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    const double2 v = lane < nw ? red2[lane] : make_double2(0.0, 0.0);
+    x = v.x; y = v.y;
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_down_sync(0xffffffffu, x, o);
+      y += __shfl_down_sync(0xffffffffu, y, o);
+    }
+    d2 = __shfl_sync(0xffffffffu, x, 0);
+    n2 = __shfl_sync(0xffffffffu, y, 0);
+  }
+}
+
 // Advance the per-load state after one iteration's residual is known:
 // r_n = sqrt(d2 / n2) (Sec. 4's Cauchy criterion), then the stop tests.
 __device__ __forceinline__ void update_state(LoadState& s, double d2, double n2, double tol, int max_iter,
