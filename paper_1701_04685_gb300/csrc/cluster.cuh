@@ -228,10 +228,14 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
     }
   };
 
-  // ---- column phase: gather columns over DSMEM, FFT, Green, inverse FFT, scatter
+  // ---- column phase: gather columns over DSMEM, FFT, Green, inverse FFT,
+  // scatter; run by the worker threads 0 .. nwork-1 only (the last warp is
+  // the control warp, see the iteration loop), synchronised on a named barrier
+  const int nwork = (int)blockDim.x - 32;
+  const int tid = (int)threadIdx.x;
   auto col_phase = [&]() {
     const int nl = NV * ncol;
-    for (int idx = threadIdx.x; idx < NV * N0 * ncol; idx += blockDim.x) {
+    for (int idx = tid; idx < NV * N0 * ncol; idx += nwork) {
       const int t = fdiv(idx, fnc);
       const int j = idx - t * ncol;
       const int c = fdiv(t, fN0);
@@ -239,9 +243,9 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
       const cplx<T>* rem = cluster.map_shared_rank(Sl, (int)own[n]);
       X0[(c * ncol + j) * N0p + n] = rem[((int)loc[n] * NV + c) * H + c0 + j];
     }
-    __syncthreads();
-    cplx<T>* Xf = fft_lines_pp<-1, T, 0, POW2>(X0, X1, nl, N0p, plan0, tw0);
-    for (int idx = threadIdx.x; idx < N0 * ncol; idx += blockDim.x) {
+    team_sync(nwork);
+    cplx<T>* Xf = fft_lines_pp<-1, T, 0, POW2>(X0, X1, nl, N0p, plan0, tw0, tid, nwork);
+    for (int idx = tid; idx < N0 * ncol; idx += nwork) {
       const int n = fdiv(idx, fnc);
       const int j = idx - n * ncol;
       cplx<T> tv[NV];
@@ -268,9 +272,9 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
         Xf[(a * ncol + j) * N0p + n] = e;
       }
     }
-    __syncthreads();
-    cplx<T>* Xi = fft_lines_pp<+1, T, 0, POW2>(Xf, Xf == X0 ? X1 : X0, nl, N0p, plan0, tw0);
-    for (int idx = threadIdx.x; idx < NV * N0 * ncol; idx += blockDim.x) {
+    team_sync(nwork);
+    cplx<T>* Xi = fft_lines_pp<+1, T, 0, POW2>(Xf, Xf == X0 ? X1 : X0, nl, N0p, plan0, tw0, tid, nwork);
+    for (int idx = tid; idx < NV * N0 * ncol; idx += nwork) {
       const int t = fdiv(idx, fnc);
       const int j = idx - t * ncol;
       const int c = fdiv(t, fN0);
@@ -286,28 +290,25 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
     row_phase(false, a, b);
   }
   cluster.sync();
+  // Iteration n: the workers run the column phase of n while the control
+  // warp (the last warp) sums the residual partials of n - 1 and takes the
+  // stop decision; the first cluster barrier publishes the decision before E
+  // is touched.  The column phase only rewrites the half spectra (scratch
+  // rebuilt from E at the start of every solve), so the one that follows the
+  // last iteration is harmless.
   __shared__ int s_done;
   __shared__ double2 red2[32];
   const int hist_cap = ctl->hist_cap;
-  for (int it = 0; it < max_iter && !s.done; ++it) {
-    col_phase();
-    cluster.sync();
-    ResAcc<T> acc_d, acc_n;
-    row_phase(true, acc_d, acc_n);
-    // this CTA's partial sums, pushed into every CTA's `part` (lane q of
-    // warp 0 stores into CTA q), so that after the barrier all reads are local
-    double d2 = 0.0, n2 = 0.0;
-    block_sum_pair(acc_d, acc_n, red2, d2, n2);
-    if (threadIdx.x < CS) {
-      double* dst = cluster.map_shared_rank(part, (int)threadIdx.x);
-      dst[2 * rank] = d2;
-      dst[2 * rank + 1] = n2;
-    }
-    cluster.sync();
-    // warp 0 of every CTA sums the CS partials in the same fixed order and
-    // takes the same decision; the other threads only need the stop flag
-    if (threadIdx.x < 32) {
-      const int lane = threadIdx.x;
+  const bool control = tid >= nwork;
+  if (tid == 0) s_done = (s.done || max_iter <= 0) ? 1 : 0;
+  __syncthreads();
+  for (int it = 0;; ++it) {
+    if (!control) {
+      col_phase();
+    } else if (it > 0) {
+      // every CTA sums the CS partials of iteration it - 1 in the same fixed
+      // order and takes the same decision
+      const int lane = tid - nwork;
       double a = lane < CS ? part[2 * lane] : 0.0, b = lane < CS ? part[2 * lane + 1] : 0.0;
       for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_down_sync(0xffffffffu, a, o);
@@ -319,8 +320,20 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
         s_done = s.done;
       }
     }
-    __syncthreads();
-    s.done = s_done;
+    cluster.sync();
+    if (s_done) break;
+    ResAcc<T> acc_d, acc_n;
+    row_phase(true, acc_d, acc_n);
+    // this CTA's partial sums, pushed into every CTA's `part` (lane q of
+    // warp 0 stores into CTA q), so that after the barrier all reads are local
+    double d2 = 0.0, n2 = 0.0;
+    block_sum_pair(acc_d, acc_n, red2, d2, n2);
+    if (tid < CS) {
+      double* dst = cluster.map_shared_rank(part, tid);
+      dst[2 * rank] = d2;
+      dst[2 * rank + 1] = n2;
+    }
+    cluster.sync();
   }
   // ---- results
   for (int i = threadIdx.x; i < nrow * L; i += blockDim.x) {
@@ -328,7 +341,7 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
 #pragma unroll
     for (int c = 0; c < NV; ++c) Eg[Ebase + (size_t)c * m + (r0 + r) * L + x] = El[(r * NV + c) * L + x];
   }
-  if (rank == 0 && threadIdx.x == 0) st[load] = s;   // thread 0 holds the full state
+  if (rank == 0 && tid == nwork) st[load] = s;   // the control lane holds the full state
   cluster.sync();  // keep every CTA's shared memory alive until remote accesses are done
 }
 

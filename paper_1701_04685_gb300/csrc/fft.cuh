@@ -183,12 +183,12 @@ template <int PADSH> __host__ __device__ inline int padded_len(int L) { return P
 
 template <int R, int DIR, typename T, int PADSH = 0>
 __device__ __forceinline__ void stockham_stage(const cplx<T>* in, cplx<T>* out, int nlines, int ls, int L, int Ns,
-                                               const cplx<T>* __restrict__ tw) {
+                                               const cplx<T>* __restrict__ tw, int tid, int nthr) {
   const int nb = L / R;
   const int stride = L / (Ns * R);
   const int total = nlines * nb;
   const FDiv fnb = make_fdiv(nb), fns = make_fdiv(Ns);
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+  for (int idx = tid; idx < total; idx += nthr) {
     const int line = fdiv(idx, fnb);
     const int j = idx - line * nb;
     const cplx<T>* li = in + line * ls;
@@ -213,15 +213,24 @@ __device__ __forceinline__ void stockham_stage(const cplx<T>* in, cplx<T>* out, 
   }
 }
 
+// Barrier of a team of threads: the whole block (nthr == blockDim.x), else the
+// first nthr threads (a multiple of 32) on named barrier 1.
+__device__ __forceinline__ void team_sync(int nthr) {
+  if (nthr == (int)blockDim.x) __syncthreads();
+  else asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory");
+}
+
 // Transform `nlines` lines of length plan.L held in shared memory.  Line q
 // occupies buf[q*ls .. q*ls + L); tmp has the same shape (ping-pong buffer).
-// Every thread of the block must call this.  Returns the buffer (buf or tmp)
-// that holds the result; a __syncthreads() has been executed on return.
+// Every thread of the team (threads tid = 0 .. nthr-1; by default the whole
+// block) must call this.  Returns the buffer (buf or tmp) that holds the
+// result; a team barrier has been executed on return.
 // POW2: the plan uses radices 2, 4 and 8 only (the caller checks); the other
 // stage kernels are then not compiled in, which keeps register use low.
 template <int DIR, typename T, int PADSH = 0, bool POW2 = false>
 __device__ cplx<T>* fft_lines_pp(cplx<T>* buf, cplx<T>* tmp, int nlines, int ls, const DevPlan& plan,
-                                 const cplx<T>* __restrict__ tw) {
+                                 const cplx<T>* __restrict__ tw, int tid = -1, int nthr = 0) {
+  if (nthr == 0) { tid = threadIdx.x; nthr = blockDim.x; }
   const int L = plan.L;
   cplx<T>* in = buf;
   cplx<T>* out = tmp;
@@ -230,23 +239,23 @@ __device__ cplx<T>* fft_lines_pp(cplx<T>* buf, cplx<T>* tmp, int nlines, int ls,
     const int r = plan.r[s];
     if constexpr (POW2) {
       switch (r) {
-        case 2: stockham_stage<2, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
-        case 4: stockham_stage<4, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
-        default: stockham_stage<8, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
+        case 2: stockham_stage<2, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw, tid, nthr); break;
+        case 4: stockham_stage<4, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw, tid, nthr); break;
+        default: stockham_stage<8, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw, tid, nthr); break;
       }
     } else {
       switch (r) {
-        case 2: stockham_stage<2, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
-        case 3: stockham_stage<3, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
-        case 4: stockham_stage<4, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
-        case 5: stockham_stage<5, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
-        case 7: stockham_stage<7, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
-        case 8: stockham_stage<8, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
-        case 11: stockham_stage<11, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
-        default: stockham_stage<13, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw); break;
+        case 2: stockham_stage<2, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw, tid, nthr); break;
+        case 3: stockham_stage<3, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw, tid, nthr); break;
+        case 4: stockham_stage<4, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw, tid, nthr); break;
+        case 5: stockham_stage<5, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw, tid, nthr); break;
+        case 7: stockham_stage<7, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw, tid, nthr); break;
+        case 8: stockham_stage<8, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw, tid, nthr); break;
+        case 11: stockham_stage<11, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw, tid, nthr); break;
+        default: stockham_stage<13, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw, tid, nthr); break;
       }
     }
-    __syncthreads();
+    team_sync(nthr);
     cplx<T>* sw = in; in = out; out = sw;
     Ns *= r;
   }
