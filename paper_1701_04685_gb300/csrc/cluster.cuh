@@ -25,6 +25,7 @@
 #include <cooperative_groups.h>
 
 #include "kernels.cuh"
+#include "warprow.cuh"
 
 namespace fh {
 
@@ -178,7 +179,9 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
         W0[p * Lp + padi<PS>(k)] = z;
       }
       __syncthreads();
-      Z = fft_lines_pp<+1, T, PS, POW2>(W0, W1, npair, Lp, plan1, tw1);
+      bool warp_done = false;   // FP32, power-of-two rows of 32..512 points: one warp per line, in place
+      if constexpr (POW2 && sizeof(T) == 4) warp_done = warp_lines_any<+1, PS, T>(W0, npair, Lp, L, tw1, threadIdx.x, blockDim.x);
+      Z = warp_done ? W0 : fft_lines_pp<+1, T, PS, POW2>(W0, W1, npair, Lp, plan1, tw1);
       Zo = (Z == W0) ? W1 : W0;
     }
     for (int idx = threadIdx.x; idx < nrow * L; idx += blockDim.x) {
@@ -213,7 +216,9 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
     if (nreal & 1)
       for (int x = threadIdx.x; x < L; x += blockDim.x) Z[(npair - 1) * Lp + padi<PS>(x)].y = T(0);
     __syncthreads();
-    cplx<T>* Zf = fft_lines_pp<-1, T, PS, POW2>(Z, Zo, npair, Lp, plan1, tw1);
+    bool warp_done = false;
+    if constexpr (POW2 && sizeof(T) == 4) warp_done = warp_lines_any<-1, PS, T>(Z, npair, Lp, L, tw1, threadIdx.x, blockDim.x);
+    cplx<T>* Zf = warp_done ? Z : fft_lines_pp<-1, T, PS, POW2>(Z, Zo, npair, Lp, plan1, tw1);
     for (int idx = threadIdx.x; idx < npair * H; idx += blockDim.x) {
       const int p = fdiv(idx, fH), k = idx - p * H;
       const cplx<T> zk = Zf[p * Lp + padi<PS>(k)];
@@ -244,7 +249,9 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
       X0[(c * ncol + j) * N0p + n] = rem[((int)loc[n] * NV + c) * H + c0 + j];
     }
     team_sync(nwork);
-    cplx<T>* Xf = fft_lines_pp<-1, T, 0, POW2>(X0, X1, nl, N0p, plan0, tw0, tid, nwork);
+    bool warp_done = false;   // FP32, power-of-two columns of 32..512 points: one warp per line, in place
+    if constexpr (POW2 && sizeof(T) == 4) warp_done = warp_lines_any<-1, 0, T>(X0, nl, N0p, N0, tw0, tid, nwork);
+    cplx<T>* Xf = warp_done ? X0 : fft_lines_pp<-1, T, 0, POW2>(X0, X1, nl, N0p, plan0, tw0, tid, nwork);
     for (int idx = tid; idx < N0 * ncol; idx += nwork) {
       const int n = fdiv(idx, fnc);
       const int j = idx - n * ncol;
@@ -273,7 +280,8 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
       }
     }
     team_sync(nwork);
-    cplx<T>* Xi = fft_lines_pp<+1, T, 0, POW2>(Xf, Xf == X0 ? X1 : X0, nl, N0p, plan0, tw0, tid, nwork);
+    if constexpr (POW2 && sizeof(T) == 4) warp_done = warp_lines_any<+1, 0, T>(Xf, nl, N0p, N0, tw0, tid, nwork);
+    cplx<T>* Xi = warp_done ? Xf : fft_lines_pp<+1, T, 0, POW2>(Xf, Xf == X0 ? X1 : X0, nl, N0p, plan0, tw0, tid, nwork);
     for (int idx = tid; idx < NV * N0 * ncol; idx += nwork) {
       const int t = fdiv(idx, fnc);
       const int j = idx - t * ncol;

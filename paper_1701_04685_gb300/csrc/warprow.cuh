@@ -31,11 +31,52 @@ __device__ __forceinline__ cplx<T> shfl_xor_c(cplx<T> v, int m) {
   return r;
 }
 
+// 16-point DFT in registers, X_k = sum_n v_n w^{nk}, w = exp(DIR 2 pi i / 16):
+// n = 4 n1 + n2, k = k1 + 4 k2; length-4 DFTs over n1, twiddles w^{n2 k1},
+// length-4 DFTs over n2.
+template <int DIR, typename T>
+__device__ __forceinline__ void dft16(cplx<T>* v) {
+  const T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173), h = T(0.70710678118654752440);
+  cplx<T> y[4][4];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    cplx<T> a[4] = {v[n2], v[4 + n2], v[8 + n2], v[12 + n2]};
+    dft4<DIR, T>(a);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) y[n2][k1] = a[k1];
+  }
+  auto tw16 = [&](int m) {   // exp(DIR 2 pi i m / 16) for m in {1, 2, 3, 4, 6, 9}
+    cplx<T> w;
+    switch (m) {
+      case 1: w.x = c1; w.y = s1; break;
+      case 2: w.x = h; w.y = h; break;
+      case 3: w.x = s1; w.y = c1; break;
+      case 4: w.x = T(0); w.y = T(1); break;
+      case 6: w.x = -h; w.y = h; break;
+      default: w.x = -c1; w.y = -s1; break;
+    }
+    if (DIR < 0) w.y = -w.y;
+    return w;
+  };
+#pragma unroll
+  for (int n2 = 1; n2 < 4; ++n2)
+#pragma unroll
+    for (int k1 = 1; k1 < 4; ++k1) y[n2][k1] = cmul(y[n2][k1], tw16(n2 * k1));
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    cplx<T> a[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+    dft4<DIR, T>(a);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = a[k2];
+  }
+}
+
 template <int P, int DIR, typename T>
 __device__ __forceinline__ void small_dft(cplx<T>* v) {
   if (P == 2) dft2<DIR, T>(v);
   else if (P == 4) dft4<DIR, T>(v);
   else if (P == 8) dft8<DIR, T>(v);
+  else if (P == 16) dft16<DIR, T>(v);
 }
 
 // w_L^{DIR t} from the table tw[t] = exp(-2 pi i t / L)
@@ -143,6 +184,53 @@ __device__ __forceinline__ void load_rows<double>(const double* p, double (&d)[1
   for (int i = 0; i < 6; ++i) {
     const double2 v = q[i];
     d[2 * i] = v.x; d[2 * i + 1] = v.y;
+  }
+}
+
+// In-place transform of `nlines` lines of length L = 32 P held in shared
+// memory (line q at buf + q * ls, entry i at padi<PS>(i)), one warp per line,
+// by the warps of a thread team (threads 0 .. nthr-1).  Forward takes natural
+// order to natural order through the bit-reversed register layout of
+// warp_fft_fwd; inverse (unnormalised) likewise.  Ends with a team barrier.
+template <int DIR, int P, int PS, typename T>
+__device__ __forceinline__ void warp_lines(cplx<T>* buf, int nlines, int ls, const cplx<T>* tw, int tid, int nthr) {
+  const int lane = tid & 31, nwarps = nthr >> 5;
+  const int brev = bitrev5(lane);
+  for (int line = tid >> 5; line < nlines; line += nwarps) {
+    cplx<T>* b = buf + (size_t)line * ls;
+    cplx<T> v[1][P];
+    if (DIR < 0) {
+#pragma unroll
+      for (int j = 0; j < P; ++j) v[0][j] = b[padi<PS>(lane + 32 * j)];
+      warp_fft_fwd<P, 1, T>(v, tw, lane);
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < P; ++q) b[padi<PS>(q + P * brev)] = v[0][q];
+    } else {
+#pragma unroll
+      for (int q = 0; q < P; ++q) v[0][q] = b[padi<PS>(q + P * brev)];
+      warp_fft_inv<P, 1, T>(v, tw, lane);
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < P; ++j) b[padi<PS>(lane + 32 * j)] = v[0][j];
+    }
+    __syncwarp();
+  }
+  team_sync(nthr);
+}
+
+// warp_lines for a runtime line length L (32, 64, 128, 256 or 512); returns
+// false (and does nothing) for any other length
+template <int DIR, int PS, typename T>
+__device__ __forceinline__ bool warp_lines_any(cplx<T>* buf, int nlines, int ls, int L, const cplx<T>* tw, int tid,
+                                               int nthr) {
+  switch (L) {
+    case 32: warp_lines<DIR, 1, PS, T>(buf, nlines, ls, tw, tid, nthr); return true;
+    case 64: warp_lines<DIR, 2, PS, T>(buf, nlines, ls, tw, tid, nthr); return true;
+    case 128: warp_lines<DIR, 4, PS, T>(buf, nlines, ls, tw, tid, nthr); return true;
+    case 256: warp_lines<DIR, 8, PS, T>(buf, nlines, ls, tw, tid, nthr); return true;
+    case 512: warp_lines<DIR, 16, PS, T>(buf, nlines, ls, tw, tid, nthr); return true;
+    default: return false;
   }
 }
 
