@@ -217,8 +217,12 @@ fh_status fh_solve(fh_solver* s, int nload, const double* eps0,
  * work is enqueued on its own stream before any is waited for, so cluster-
  * resident solves of different patterns run concurrently on the GPU; solvers
  * that need the whole-GPU pass path run their host-driven loops in turn while
- * the others proceed.  Returns the worst per-load status over the batch or an
- * error code (nothing is run when an argument check fails). */
+ * the others proceed.  Solvers are started largest first.  With path and
+ * cluster left at 0 (and no earlier tuning of the solver), a batch takes the
+ * 8-CTA cluster wherever the fields fit: two of those run per GPC, where a
+ * 16-CTA cluster occupies a GPC alone, so the batch finishes sooner even
+ * though each solve alone is slower.  Returns the worst per-load status over
+ * the batch or an error code (nothing is run when an argument check fails). */
 fh_status fh_solve_batch(fh_solver* const* solvers, int n, const int* nload, const double* const* eps0,
                          const fh_solve_opts* opts, fh_result* res);
 

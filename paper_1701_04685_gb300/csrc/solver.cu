@@ -1197,6 +1197,22 @@ fh_status autotune(fh_solver* s, int nload, const double* eps0, int prec, int ch
 
 }  // namespace
 
+namespace {
+
+// Cluster size for a batched solve left to the library: a 16-CTA cluster has
+// to sit inside one GPC, so at most one runs per GPC; 8-CTA clusters pack two
+// per GPC.  A batch is throughput-bound, so it takes the 8-CTA cluster
+// wherever the fields fit, else the usual choice (16, or the pass path).
+fh_status batch_cluster_choice(fh_solver* s, int prec, int* path, int* cs) {
+  bool ok8 = false;
+  fh_status rc = prec == FH_PREC_FP64 ? cluster_fits<double, 8>(s, &ok8) : cluster_fits<float, 8>(s, &ok8);
+  if (rc != FH_OK) return rc;
+  if (ok8) { *path = 2; *cs = 8; }
+  return FH_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 fh_status fh_solve(fh_solver* s, int nload, const double* eps0, const fh_solve_opts* opts, fh_result* res) {
@@ -1250,8 +1266,15 @@ fh_status fh_solve_batch(fh_solver* const* solvers, int n, const int* nload, con
   const bool mixed = opts->precision == FH_PREC_MIXED;
   const int prec1 = opts->precision == FH_PREC_FP64 ? FH_PREC_FP64 : FH_PREC_FP32;
   std::vector<PhaseOut> A(n), B(n);
+  // largest problems first (longest-processing-time order): the small ones
+  // fill the GPU at the end instead of leaving a long solve running alone
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (double)solvers[a]->g.m * nload[a] > (double)solvers[b]->g.m * nload[b];
+  });
   // phase 1: every solver's work is enqueued before any is waited for
-  for (int i = 0; i < n; ++i) {
+  for (int i : order) {
     fh_status rc = join_user(solvers[i]);
     if (rc != FH_OK) return rc;
     solvers[i]->form = opts->form;
@@ -1260,6 +1283,9 @@ fh_status fh_solve_batch(fh_solver* const* solvers, int n, const int* nload, con
     if (p1 == 0 && c1 == 0 && solvers[i]->tuned_path[slot] != 0) {   // keep an earlier tuning
       p1 = solvers[i]->tuned_path[slot];
       c1 = solvers[i]->tuned_cs[slot];
+    } else if (p1 == 0 && c1 == 0) {
+      fh_status rc = batch_cluster_choice(solvers[i], prec1, &p1, &c1);
+      if (rc != FH_OK) return rc;
     }
     rc = begin_phase(solvers[i], nload[i], eps0[i], opts->tol, opts->max_iter, prec1, opts->init, chunk, p1, c1,
                      nullptr, &A[i], mixed ? kStallWindow : 0);
@@ -1270,13 +1296,16 @@ fh_status fh_solve_batch(fh_solver* const* solvers, int n, const int* nload, con
     if (rc != FH_OK) return rc;
   }
   if (mixed) {
-    for (int i = 0; i < n; ++i) {
+    for (int i : order) {
       LoadState st0[FH_MAX_LOADS];
       polish_start(A[i], st0);
       int p2 = opts->path, c2 = opts->cluster;
       if (p2 == 0 && c2 == 0 && solvers[i]->tuned_path[0] != 0) {
         p2 = solvers[i]->tuned_path[0];
         c2 = solvers[i]->tuned_cs[0];
+      } else if (p2 == 0 && c2 == 0) {
+        fh_status rc = batch_cluster_choice(solvers[i], FH_PREC_FP64, &p2, &c2);
+        if (rc != FH_OK) return rc;
       }
       fh_status rc = begin_phase(solvers[i], nload[i], eps0[i], opts->tol, opts->max_iter, FH_PREC_FP64, 1, chunk, p2,
                                  c2, st0, &B[i]);
