@@ -308,7 +308,7 @@ def run_gpu(args, rank, world, local_rank):
         out = s.solve(eps0, tol=args.tol, max_iter=20000, precision=prec[bulk])
         flops = per_iter * float(np.sum(out["iterations"]))
         dur_ms = out["elapsed_ms"]
-        kernel = f"cluster_solve_2d<{'float' if bulk == 'fp32' else 'double'},3,{out['cluster']}> (one launch per solve)"
+        kernel = f"cluster_solve_2d<{'float' if bulk == 'fp32' else 'double'},3,{out['cluster']}> (one launch per solve, one cluster per load)"
         passes = None
     else:
         step(bulk)

@@ -214,10 +214,11 @@ fh_status fh_solve(fh_solver* s, int nload, const double* eps0,
 /* Batched solve: runs fh_solve on n distinct solvers (patterns of any sizes)
  * with one shared set of options; nload[i] and eps0[i] are solver i's load
  * count and strains, res[i] (host, may be NULL) its result.  Every solver's
- * work is enqueued on its own stream before any is waited for, so cluster-
- * resident solves of different patterns run concurrently on the GPU; solvers
- * that need the whole-GPU pass path run their host-driven loops in turn while
- * the others proceed.  Solvers are started largest first.  With path and
+ * set-up is enqueued on its own stream before any is waited for; the cluster-
+ * resident solves of all solvers then run as one persistent launch per
+ * cluster-kernel variant, whose clusters take (solver, load) tasks from a list
+ * ordered largest pattern first; solvers that need the whole-GPU pass path
+ * run their host-driven loops in turn.  With path and
  * cluster left at 0 (and no earlier tuning of the solver), a batch takes the
  * 8-CTA cluster wherever the fields fit: two of those run per GPC, where a
  * 16-CTA cluster occupies a GPC alone, so the batch finishes sooner even

@@ -80,20 +80,22 @@ __host__ __device__ inline ClusterLayout cluster_layout(int N0, int L, int nv, i
 
 // threads per CTA: 8 warps for general radix plans (with the 11- and
 // 13-point stages compiled in, 16 warps would cap registers at 128 and
-// spill); 16 warps for plans of radices 2, 4, 8 only
-template <typename T, bool POW2> struct ClusterThreads { static constexpr int value = POW2 ? 512 : 256; };
+// spill) and in FP64; 16 warps for FP32 plans of radices 2, 4, 8 only
+template <typename T, bool POW2> struct ClusterThreads { static constexpr int value = (POW2 && sizeof(T) == 4) ? 512 : 256; };
 
+// The whole solve of load `load` by the cluster this CTA belongs to.  Ends
+// with a cluster barrier, after which the cluster may start another solve.
 template <typename T, int NV, int CS, bool POW2>
-__global__ void __launch_bounds__(ClusterThreads<T, POW2>::value, 1)
-cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __restrict__ tw0g,
-                 const cplx<T>* __restrict__ tw1g, T* __restrict__ Eg, const uint8_t* __restrict__ phase,
-                 const T* __restrict__ dC, int nphase, const T* __restrict__ Gt, Control* ctl, LoadState* st,
-                 double* __restrict__ hist, int g_smem) {
+__device__ __forceinline__ void cluster_solve_body(const GridInfo& g, const DevPlan& plan0, const DevPlan& plan1,
+                                                   const cplx<T>* __restrict__ tw0g, const cplx<T>* __restrict__ tw1g,
+                                                   T* __restrict__ Eg, const uint8_t* __restrict__ phase,
+                                                   const T* __restrict__ dC, int nphase, const T* __restrict__ Gt,
+                                                   Control* ctl, LoadState* st, double* __restrict__ hist, int g_smem,
+                                                   int load) {
   constexpr int NTRI = NV * (NV + 1) / 2;
   extern __shared__ __align__(128) unsigned char sm[];
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
-  const int load = blockIdx.x / CS;
   const int N0 = g.dims[0], L = g.L, H = g.H;
   const int m = (int)g.m;
   const ClusterLayout lay = cluster_layout<T>(N0, L, NV, CS, g_smem != 0);
@@ -351,6 +353,55 @@ cluster_solve_2d(GridInfo g, DevPlan plan0, DevPlan plan1, const cplx<T>* __rest
   }
   if (rank == 0 && tid == nwork) st[load] = s;   // the control lane holds the full state
   cluster.sync();  // keep every CTA's shared memory alive until remote accesses are done
+}
+
+// One solve of one load of one solver: the unit of work of the cluster kernel.
+struct ClusterTask {
+  GridInfo g;
+  DevPlan plan0, plan1;
+  const void* tw0;
+  const void* tw1;
+  void* E;
+  const uint8_t* phase;
+  const void* dC;
+  const void* Gt;
+  Control* ctl;
+  LoadState* st;
+  double* hist;
+  int nphase;
+  int g_smem;
+  int load;
+  int pad_;
+};
+
+// The cluster kernel: resident clusters take tasks from `tasks` until none is
+// left.  A single solve queues its own loads (one cluster each); a batched
+// solve queues every load of every solver of the batch, largest pattern first,
+// on as many clusters as fit.  Rank 0 of a cluster draws the next index with
+// one atomic and the other CTAs read it from rank 0's shared memory; clusters
+// never wait on one another.  The task is staged in shared memory.
+template <typename T, int NV, int CS, bool POW2>
+__global__ void __launch_bounds__(ClusterThreads<T, POW2>::value, 1)
+cluster_solve_2d(const ClusterTask* __restrict__ tasks, int ntasks, unsigned int* next) {
+  cg::cluster_group cluster = cg::this_cluster();
+  __shared__ int s_task;
+  __shared__ __align__(16) ClusterTask t;
+  for (;;) {
+    if (cluster.block_rank() == 0 && threadIdx.x == 0) s_task = (int)atomicAdd(next, 1u);
+    cluster.sync();
+    const int task = *cluster.map_shared_rank(&s_task, 0);
+    if (task < ntasks) {
+      const int* src = reinterpret_cast<const int*>(tasks + task);
+      int* dst = reinterpret_cast<int*>(&t);
+      for (int i = threadIdx.x; i < (int)(sizeof(ClusterTask) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    }
+    cluster.sync();   // every CTA holds the index (and the task) before rank 0 draws the next one
+    if (task >= ntasks) return;
+    cluster_solve_body<T, NV, CS, POW2>(t.g, t.plan0, t.plan1, static_cast<const cplx<T>*>(t.tw0),
+                                        static_cast<const cplx<T>*>(t.tw1), static_cast<T*>(t.E), t.phase,
+                                        static_cast<const T*>(t.dC), t.nphase, static_cast<const T*>(t.Gt), t.ctl,
+                                        t.st, t.hist, t.g_smem, t.load);
+  }
 }
 
 }  // namespace fh

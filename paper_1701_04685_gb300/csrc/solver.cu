@@ -122,6 +122,9 @@ struct fh_solver {
   bool cl_gsmem[2][2] = {{true, true}, {true, true}};  // [fp64/fp32][cluster 8/16]: table slice in smem
   LoadState* h_states = nullptr;                       // pinned copies read back after a phase
   double* h_ms = nullptr;
+  fh::ClusterTask* qtasks = nullptr;                    // cluster-kernel task list of a single solve
+  unsigned int* qnext = nullptr;
+  fh::ClusterTask* h_tasks = nullptr;                   // pinned staging of that list
 };
 
 namespace {
@@ -509,28 +512,60 @@ fh_status cluster_fits(fh_solver* s, bool* ok) {
   return s->g.nv == 3 ? cluster_fits_nv<T, 3, CS, false>(s, ok) : cluster_fits_nv<T, 6, CS, false>(s, ok);
 }
 
-template <typename T, int NV, int CS, bool POW2>
-fh_status launch_cluster_nv(fh_solver* s, int nload) {
-  const GridInfo& g = s->g;
+// Task of the cluster kernel for load l of solver s.
+template <typename T, int CS>
+fh::ClusterTask cluster_task(const fh_solver* s, int l) {
   const bool gs = s->cl_gsmem[sizeof(T) == 8 ? 0 : 1][CS == 16 ? 1 : 0];
-  const fh::ClusterLayout lay = fh::cluster_layout<T>(g.dims[0], g.L, g.nv, CS, gs);
-  auto kern = fh::cluster_solve_2d<T, NV, CS, POW2>;
+  fh::ClusterTask t{};
+  t.g = s->g;
+  t.plan0 = s->ax[0].plan;
+  t.plan1 = s->ax[1].plan;
+  t.tw0 = twp<T>(s->ax[0]);
+  t.tw1 = twp<T>(s->ax[1]);
+  t.E = Eptr<T>(const_cast<fh_solver*>(s));
+  t.phase = s->phase;
+  t.dC = dCptr<T>(const_cast<fh_solver*>(s));
+  t.Gt = Gptr<T>(const_cast<fh_solver*>(s));
+  t.ctl = s->ctl;
+  t.st = s->st;
+  t.hist = s->hist;
+  t.nphase = s->nphase;
+  t.g_smem = gs ? 1 : 0;
+  t.load = l;
+  return t;
+}
+
+// Launch configuration of the cluster kernel with `nclusters` clusters.
+template <typename T, int NV, int CS, bool POW2>
+cudaLaunchConfig_t cluster_config(size_t smem, int nclusters, cudaStream_t stream, cudaLaunchAttribute* attr) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(nload * CS);
+  cfg.gridDim = dim3(nclusters * CS);
   cfg.blockDim = dim3(fh::ClusterThreads<T, POW2>::value);
-  cfg.dynamicSmemBytes = lay.total;
-  cfg.stream = s->work;
-  cudaLaunchAttribute attr[1];
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = CS;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  using C = typename fh::cplx_t<T>::type;
-  CK(cudaLaunchKernelEx(&cfg, kern, g, s->ax[0].plan, s->ax[1].plan, (const C*)twp<T>(s->ax[0]),
-                        (const C*)twp<T>(s->ax[1]), Eptr<T>(s), (const uint8_t*)s->phase, dCptr<T>(s), s->nphase,
-                        Gptr<T>(s), s->ctl, s->st, s->hist, gs ? 1 : 0));
+  return cfg;
+}
+
+// A single solve: one cluster per load, each taking its own load's task.
+template <typename T, int NV, int CS, bool POW2>
+fh_status launch_cluster_nv(fh_solver* s, int nload) {
+  const GridInfo& g = s->g;
+  const bool gs = s->cl_gsmem[sizeof(T) == 8 ? 0 : 1][CS == 16 ? 1 : 0];
+  const fh::ClusterLayout lay = fh::cluster_layout<T>(g.dims[0], g.L, g.nv, CS, gs);
+  for (int l = 0; l < nload; ++l) s->h_tasks[l] = cluster_task<T, CS>(s, l);
+  CK(cudaMemcpyAsync(s->qtasks, s->h_tasks, nload * sizeof(fh::ClusterTask), cudaMemcpyHostToDevice, s->work));
+  CK(cudaMemsetAsync(s->qnext, 0, sizeof(unsigned int), s->work));
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = cluster_config<T, NV, CS, POW2>(lay.total, nload, s->work, attr);
+  const fh::ClusterTask* tp = s->qtasks;
+  unsigned int* np = s->qnext;
+  CK(cudaLaunchKernelEx(&cfg, fh::cluster_solve_2d<T, NV, CS, POW2>, tp, nload, np));
   return FH_OK;
 }
 
@@ -583,7 +618,7 @@ void free_all(fh_solver* s) {
   for (auto& e : s->graphs) cudaGraphExecDestroy(e.exec);
   s->graphs.clear();
   void* ptrs[] = {s->E64, s->E32, s->S, s->phase, s->Cp64, s->dC64, s->dC32, s->Cp32, s->G64, s->G32, s->ctl, s->st,
-                  s->partials, s->partials2, s->hist, s->mstress, s->err, s->scratch64};
+                  s->partials, s->partials2, s->hist, s->mstress, s->err, s->scratch64, s->qtasks, s->qnext};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& a : s->ax) {
@@ -593,6 +628,7 @@ void free_all(fh_solver* s) {
   if (s->h_flag) cudaFreeHost(s->h_flag);
   if (s->h_states) cudaFreeHost(s->h_states);
   if (s->h_ms) cudaFreeHost(s->h_ms);
+  if (s->h_tasks) cudaFreeHost(s->h_tasks);
   if (s->ev0) cudaEventDestroy(s->ev0);
   if (s->ev1) cudaEventDestroy(s->ev1);
   if (s->ev_user) cudaEventDestroy(s->ev_user);
@@ -851,6 +887,9 @@ fh_status fh_solver_create(const fh_pattern* p, const fh_generator* gen, int nlo
   CKS(cudaMallocHost(&s->h_flag, sizeof(int)));
   CKS(cudaMallocHost(&s->h_states, FH_MAX_LOADS * sizeof(LoadState)));
   CKS(cudaMallocHost(&s->h_ms, FH_MAX_LOADS * fh::MAXV * sizeof(double)));
+  CKS(cudaMalloc(&s->qtasks, FH_MAX_LOADS * sizeof(fh::ClusterTask)));
+  CKS(cudaMalloc(&s->qnext, sizeof(unsigned int)));
+  CKS(cudaMallocHost(&s->h_tasks, FH_MAX_LOADS * sizeof(fh::ClusterTask)));
   CKS(cudaMemset(s->ctl, 0, sizeof(Control)));
   CKS(cudaMemset(s->st, 0, FH_MAX_LOADS * sizeof(LoadState)));
   CKS(cudaMemset(s->err, 0, sizeof(int)));
@@ -1014,7 +1053,7 @@ struct PhaseOut {
 // `start` (may be null) gives the per-load state to continue from.
 fh_status begin_phase(fh_solver* s, int nload, const double* eps0, double tol, int max_iter, int prec, int init,
                       int chunk, int want_path, int want_cs, const LoadState* start, PhaseOut* out,
-                      int stall_window = 0) {
+                      int stall_window = 0, bool defer_cluster = false) {
   const int nv = s->g.nv;
   Control h{};
   h.stall_window = stall_window;
@@ -1042,6 +1081,12 @@ fh_status begin_phase(fh_solver* s, int nload, const double* eps0, double tol, i
   fh_status rc = prec == FH_PREC_FP64 ? choose_path<double>(s, want_path, want_cs, &out->path, &out->cs)
                                       : choose_path<float>(s, want_path, want_cs, &out->path, &out->cs);
   if (rc != FH_OK) return rc;
+  if (out->path == 2 && defer_cluster) {
+    // the cluster solve itself is queued by the caller (batched solves)
+    out->nload = nload;
+    CK(cudaEventRecord(s->ev0, s->work));
+    return FH_OK;
+  }
   if (out->path == 2)
     rc = prec == FH_PREC_FP64 ? run_solve_cluster<double>(s, nload, out->cs, &out->launches)
                               : run_solve_cluster<float>(s, nload, out->cs, &out->launches);
@@ -1199,6 +1244,141 @@ fh_status autotune(fh_solver* s, int nload, const double* eps0, int prec, int ch
 
 namespace {
 
+// After a queued cluster solve: the mean stresses and the read-back that
+// begin_phase does for a solve it runs itself.
+template <typename T>
+fh_status finish_deferred(fh_solver* s, int nload, PhaseOut* out) {
+  const int bpl = std::max(1, (int)std::min<long long>((s->g.m + kThreads - 1) / kThreads, 64));
+  fh::mean_stress<T><<<nload * bpl, kThreads, 0, s->work>>>(s->g, Eptr<T>(s), s->phase, s->Cp64, s->ctl, s->partials2,
+                                                            s->mstress, bpl);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(s->ev1, s->work));
+  CK(cudaMemcpyAsync(s->h_states, s->st, sizeof(LoadState) * nload, cudaMemcpyDeviceToHost, s->work));
+  CK(cudaMemcpyAsync(s->h_ms, s->mstress, sizeof(double) * nload * fh::MAXV, cudaMemcpyDeviceToHost, s->work));
+  out->launches = 2;   // its share of the queue launch, and the mean stress
+  return FH_OK;
+}
+
+// One queue launch for every (solver, load) of a group of deferred cluster
+// solves that share precision, n_v, cluster size and radix variant; tasks are
+// ordered largest pattern first, and as many clusters as fit stay resident.
+struct QueueGroup {
+  int prec, nv, cs;
+  bool pow2;
+  std::vector<int> members;   // indices into the batch
+};
+
+template <typename T, int NV, int CS, bool POW2>
+fh_status launch_queue(fh_solver* const* solvers, const std::vector<int>& members, const int* nload,
+                       cudaStream_t stream, fh::ClusterTask** dtasks, unsigned int** dnext) {
+  std::vector<fh::ClusterTask> tasks;
+  size_t smem = 0;
+  for (int i : members) {
+    fh_solver* s = solvers[i];
+    const bool gs = s->cl_gsmem[sizeof(T) == 8 ? 0 : 1][CS == 16 ? 1 : 0];
+    smem = std::max(smem, fh::cluster_layout<T>(s->g.dims[0], s->g.L, s->g.nv, CS, gs).total);
+    for (int l = 0; l < nload[i]; ++l) tasks.push_back(cluster_task<T, CS>(s, l));
+  }
+  std::stable_sort(tasks.begin(), tasks.end(),
+                   [](const fh::ClusterTask& a, const fh::ClusterTask& b) { return a.g.m > b.g.m; });
+  auto kern = fh::cluster_solve_2d<T, NV, CS, POW2>;
+  CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (CS > 8) CK(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = cluster_config<T, NV, CS, POW2>(smem, 1, stream, attr);
+  int resident = 0;
+  CK(cudaOccupancyMaxActiveClusters(&resident, kern, &cfg));
+  const int nclusters = std::max(1, std::min<int>((int)tasks.size(), resident));
+  cfg.gridDim = dim3(nclusters * CS);
+  CK(cudaMalloc(dtasks, tasks.size() * sizeof(fh::ClusterTask)));
+  CK(cudaMalloc(dnext, sizeof(unsigned int)));
+  CK(cudaMemcpyAsync(*dtasks, tasks.data(), tasks.size() * sizeof(fh::ClusterTask), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemsetAsync(*dnext, 0, sizeof(unsigned int), stream));
+  const fh::ClusterTask* tp = *dtasks;
+  const int nt = (int)tasks.size();
+  unsigned int* np = *dnext;
+  CK(cudaLaunchKernelEx(&cfg, kern, tp, nt, np));
+  return FH_OK;
+}
+
+template <typename T, int NV>
+fh_status launch_queue_nv(const QueueGroup& q, fh_solver* const* solvers, const int* nload, cudaStream_t stream,
+                          fh::ClusterTask** dt, unsigned int** dn) {
+  if (q.cs == 16)
+    return q.pow2 ? launch_queue<T, NV, 16, true>(solvers, q.members, nload, stream, dt, dn)
+                  : launch_queue<T, NV, 16, false>(solvers, q.members, nload, stream, dt, dn);
+  return q.pow2 ? launch_queue<T, NV, 8, true>(solvers, q.members, nload, stream, dt, dn)
+                : launch_queue<T, NV, 8, false>(solvers, q.members, nload, stream, dt, dn);
+}
+
+// Queue the deferred cluster solves of a phase: group them, let one stream
+// per group wait for the set-up of its members, launch one queue kernel per
+// group (the groups run concurrently), and let every solver's stream wait for
+// its group's kernel before finishing its phase.
+fh_status run_queued(fh_solver* const* solvers, const int* nload, const std::vector<int>& deferred, int prec,
+                     std::vector<PhaseOut>& out) {
+  if (deferred.empty()) return FH_OK;
+  std::vector<QueueGroup> groups;
+  for (int i : deferred) {
+    const QueueGroup key{prec, solvers[i]->g.nv, out[i].cs, pow2_plans(solvers[i]), {}};
+    auto it = std::find_if(groups.begin(), groups.end(), [&](const QueueGroup& q) {
+      return q.nv == key.nv && q.cs == key.cs && q.pow2 == key.pow2;
+    });
+    if (it == groups.end()) { groups.push_back(key); it = groups.end() - 1; }
+    it->members.push_back(i);
+  }
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> evs;
+  std::vector<void*> bufs;
+  auto cleanup = [&]() {
+    for (cudaStream_t q : streams) cudaStreamSynchronize(q);
+    for (void* b : bufs) cudaFree(b);
+    for (cudaEvent_t e : evs) cudaEventDestroy(e);
+    for (cudaStream_t q : streams) cudaStreamDestroy(q);
+  };
+  auto new_event = [&](cudaEvent_t* e) {
+    if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return false;
+    evs.push_back(*e);
+    return true;
+  };
+  for (const QueueGroup& q : groups) {
+    cudaStream_t qs;
+    if (cudaStreamCreateWithFlags(&qs, cudaStreamNonBlocking) != cudaSuccess) { cleanup(); return FH_ERR_CUDA; }
+    streams.push_back(qs);
+    for (int i : q.members) {
+      cudaEvent_t e;
+      if (!new_event(&e) || cudaEventRecord(e, solvers[i]->work) != cudaSuccess ||
+          cudaStreamWaitEvent(qs, e, 0) != cudaSuccess) {
+        cleanup();
+        return FH_ERR_CUDA;
+      }
+    }
+    fh::ClusterTask* dt = nullptr;
+    unsigned int* dn = nullptr;
+    fh_status rc;
+    if (prec == FH_PREC_FP64)
+      rc = q.nv == 3 ? launch_queue_nv<double, 3>(q, solvers, nload, qs, &dt, &dn)
+                     : launch_queue_nv<double, 6>(q, solvers, nload, qs, &dt, &dn);
+    else
+      rc = q.nv == 3 ? launch_queue_nv<float, 3>(q, solvers, nload, qs, &dt, &dn)
+                     : launch_queue_nv<float, 6>(q, solvers, nload, qs, &dt, &dn);
+    if (dt) bufs.push_back(dt);
+    if (dn) bufs.push_back(dn);
+    if (rc != FH_OK) { cleanup(); return rc; }
+    cudaEvent_t done;
+    if (!new_event(&done) || cudaEventRecord(done, qs) != cudaSuccess) { cleanup(); return FH_ERR_CUDA; }
+    for (int i : q.members) {
+      fh_solver* s = solvers[i];
+      if (cudaStreamWaitEvent(s->work, done, 0) != cudaSuccess) { cleanup(); return FH_ERR_CUDA; }
+      rc = prec == FH_PREC_FP64 ? finish_deferred<double>(s, nload[i], &out[i])
+                                : finish_deferred<float>(s, nload[i], &out[i]);
+      if (rc != FH_OK) { cleanup(); return rc; }
+    }
+  }
+  cleanup();   // waits for the queue kernels; the solvers' streams carry on
+  return FH_OK;
+}
+
 // Cluster size for a batched solve left to the library: a 16-CTA cluster has
 // to sit inside one GPC, so at most one runs per GPC; 8-CTA clusters pack two
 // per GPC.  A batch is throughput-bound, so it takes the 8-CTA cluster
@@ -1273,7 +1453,10 @@ fh_status fh_solve_batch(fh_solver* const* solvers, int n, const int* nload, con
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     return (double)solvers[a]->g.m * nload[a] > (double)solvers[b]->g.m * nload[b];
   });
-  // phase 1: every solver's work is enqueued before any is waited for
+  // phase 1: every solver's work is enqueued before any is waited for; the
+  // cluster-resident solves go through one persistent queue launch per
+  // kernel variant
+  std::vector<int> deferred1, deferred2;
   for (int i : order) {
     fh_status rc = join_user(solvers[i]);
     if (rc != FH_OK) return rc;
@@ -1288,7 +1471,12 @@ fh_status fh_solve_batch(fh_solver* const* solvers, int n, const int* nload, con
       if (rc != FH_OK) return rc;
     }
     rc = begin_phase(solvers[i], nload[i], eps0[i], opts->tol, opts->max_iter, prec1, opts->init, chunk, p1, c1,
-                     nullptr, &A[i], mixed ? kStallWindow : 0);
+                     nullptr, &A[i], mixed ? kStallWindow : 0, true);
+    if (rc != FH_OK) return rc;
+    if (A[i].path == 2) deferred1.push_back(i);
+  }
+  {
+    fh_status rc = run_queued(solvers, nload, deferred1, prec1, A);
     if (rc != FH_OK) return rc;
   }
   for (int i = 0; i < n; ++i) {
@@ -1308,7 +1496,12 @@ fh_status fh_solve_batch(fh_solver* const* solvers, int n, const int* nload, con
         if (rc != FH_OK) return rc;
       }
       fh_status rc = begin_phase(solvers[i], nload[i], eps0[i], opts->tol, opts->max_iter, FH_PREC_FP64, 1, chunk, p2,
-                                 c2, st0, &B[i]);
+                                 c2, st0, &B[i], 0, true);
+      if (rc != FH_OK) return rc;
+      if (B[i].path == 2) deferred2.push_back(i);
+    }
+    {
+      fh_status rc = run_queued(solvers, nload, deferred2, FH_PREC_FP64, B);
       if (rc != FH_OK) return rc;
     }
     for (int i = 0; i < n; ++i) {
