@@ -1,6 +1,7 @@
 // Cluster-resident Basic-Scheme solver for 2-axis Smith grids.
 //
-// One thread-block cluster owns one load case for the whole solve.  The
+// One thread-block cluster owns one load case for the whole solve (a task;
+// the kernel's clusters take tasks from a queue until it is empty).  The
 // strain E, the half spectrum and the cluster's slice of the Gamma^p table
 // stay in the distributed shared memory of the cluster; only the final strain
 // goes back to global memory.  Each iteration of the paper's fixed point
@@ -9,14 +10,15 @@
 //   column phase  CTA c gathers its half-spectrum columns [c0, c1) of every row
 //                 from the owning CTAs (DSMEM loads), FFT along axis 0, Green
 //                 step E^ = -Gamma^p tau^ (E^_0 = 0), inverse FFT, scatters
-//                 the columns back (DSMEM stores)
-//   cluster barrier
+//                 the columns back (DSMEM stores); meanwhile the control warp
+//                 of every CTA takes the stop decision of the previous
+//                 iteration (the CS partial sums in a fixed order, so every
+//                 CTA takes the same decision; rank 0 records r_n)
+//   cluster barrier (the decision is read; a stopped load leaves the loop)
 //   row phase     CTA c, for its rows [r0, r1): inverse FFT along the
-//                 contiguous axis, E_new, FP64 residual partial sums (sent to
-//                 rank 0), tau = (C - C0):(E_new + eps0), forward FFT
+//                 contiguous axis, E_new, FP64 residual partial sums (pushed
+//                 to every CTA), tau = (C - C0):(E_new + eps0), forward FFT
 //   cluster barrier
-//   stop test     every CTA sums the CS partials in the same fixed order and
-//                 takes the same decision; rank 0 records r_n.
 //
 // Cluster barriers are hardware barriers (no spin loops); the iteration count
 // is bounded by max_iter.
