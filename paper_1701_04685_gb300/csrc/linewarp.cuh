@@ -86,7 +86,6 @@ __global__ void __launch_bounds__(kColThreads) line_pass_warp6(GridInfo g, const
     }
   }
   __syncthreads();
-  const int brev = bitrev5(lane);
 
   // 2. warp transforms of column `warp`, three components at a time
   auto forward = [&]() {
@@ -99,13 +98,13 @@ __global__ void __launch_bounds__(kColThreads) line_pass_warp6(GridInfo g, const
 #pragma unroll
         for (int j = 0; j < P; ++j) z[p][j] = col[wpad(lane + 32 * j)];
       }
-      warp_fft_fwd<P, 3, float>(z, tw, lane);
+      warp_fft_fwd_any<P, 3, float>(z, tw, lane);
       __syncwarp();
 #pragma unroll
       for (int p = 0; p < 3; ++p) {
         float2* col = tile + ((3 * half + p) * kColTile + warp) * LS;
 #pragma unroll
-        for (int q = 0; q < P; ++q) col[wpad(q + P * brev)] = z[p][q];
+        for (int q = 0; q < P; ++q) col[wpad(warp_freq<P>(lane, q))] = z[p][q];
       }
     }
   };
@@ -117,9 +116,9 @@ __global__ void __launch_bounds__(kColThreads) line_pass_warp6(GridInfo g, const
       for (int p = 0; p < 3; ++p) {
         const float2* col = tile + ((3 * half + p) * kColTile + warp) * LS;
 #pragma unroll
-        for (int q = 0; q < P; ++q) z[p][q] = col[wpad(q + P * brev)];
+        for (int q = 0; q < P; ++q) z[p][q] = col[wpad(warp_freq<P>(lane, q))];
       }
-      warp_fft_inv<P, 3, float>(z, tw, lane);
+      warp_fft_inv_any<P, 3, float>(z, tw, lane);
       __syncwarp();
 #pragma unroll
       for (int p = 0; p < 3; ++p) {

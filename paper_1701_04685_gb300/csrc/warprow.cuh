@@ -160,6 +160,114 @@ __device__ __forceinline__ void warp_fft_inv(cplx<T> (&v)[NL][P], const cplx<T>*
   }
 }
 
+// Paired form of the 32-point lane exchange, for P >= 2 values per lane:
+// registers 2j and 2j+1 hold two independent lane DFTs (x and y).  In stage h
+// the lower lane of each pair keeps x and sends y, the upper lane keeps y and
+// sends x, so each lane receives one complex value and computes one whole
+// radix-2 butterfly in registers: half the shuffles of warp_fft_fwd, and no
+// multiplication by a unit twiddle.  After the five stages lane l, register q
+// holds frequency pair_freq(l, q, P) (lane bit 4 then names the DFT of the
+// pair, register bit 0 the lowest position bit); the inverse takes that layout
+// back to natural order (lane l, register j: point l + 32 j).
+__device__ __forceinline__ int pair_freq(int lane, int q, int P) {
+  return 2 * (q >> 1) + (lane >> 4) + P * bitrev5(((lane & 15) << 1) | (q & 1));
+}
+
+template <int P, int NL, typename T>
+__device__ __forceinline__ void warp_fft_fwd_pairs(cplx<T> (&v)[NL][P], const cplx<T>* tw, int lane) {
+  constexpr int L = 32 * P;
+#pragma unroll
+  for (int n = 0; n < NL; ++n) {
+    small_dft<P, -1, T>(v[n]);
+#pragma unroll
+    for (int q = 1; q < P; ++q) v[n][q] = cmul(v[n][q], twl<-1, T>(tw, lane * q));
+  }
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool upper = (lane & h) != 0;
+    const T sgn = upper ? T(-1) : T(1);
+    cplx<T> w;
+    if (h > 1) {
+      w = twl<-1, T>(tw, (lane & (h - 1)) * (L / (2 * h)));
+      w.x *= sgn;
+      w.y *= sgn;
+    }
+#pragma unroll
+    for (int n = 0; n < NL; ++n)
+#pragma unroll
+      for (int j = 0; j < P / 2; ++j) {
+        const cplx<T> r0 = v[n][2 * j], r1 = v[n][2 * j + 1];
+        const cplx<T> s = upper ? r1 : r0;
+        const cplx<T> t = shfl_xor_c<T>(upper ? r0 : r1, h);
+        v[n][2 * j] = cadd(s, t);
+        const cplx<T> d = csub(s, t);
+        if (h > 1) {
+          v[n][2 * j + 1] = cmul(d, w);
+        } else {
+          v[n][2 * j + 1].x = sgn * d.x;
+          v[n][2 * j + 1].y = sgn * d.y;
+        }
+      }
+  }
+}
+
+template <int P, int NL, typename T>
+__device__ __forceinline__ void warp_fft_inv_pairs(cplx<T> (&v)[NL][P], const cplx<T>* tw, int lane) {
+  constexpr int L = 32 * P;
+#pragma unroll
+  for (int h = 1; h <= 16; h <<= 1) {
+    const bool upper = (lane & h) != 0;
+    const T sgn = upper ? T(-1) : T(1);
+    cplx<T> w;
+    if (h > 1) {
+      w = twl<+1, T>(tw, (lane & (h - 1)) * (L / (2 * h)));
+      w.x *= sgn;
+      w.y *= sgn;
+    }
+#pragma unroll
+    for (int n = 0; n < NL; ++n)
+#pragma unroll
+      for (int j = 0; j < P / 2; ++j) {
+        const cplx<T> r0 = v[n][2 * j], r1 = v[n][2 * j + 1];
+        cplx<T> u;
+        if (h > 1) {
+          u = cmul(r1, w);
+        } else {
+          u.x = sgn * r1.x;
+          u.y = sgn * r1.y;
+        }
+        const cplx<T> s2 = cadd(r0, u);
+        const cplx<T> recv = shfl_xor_c<T>(csub(r0, u), h);
+        v[n][2 * j] = upper ? recv : s2;
+        v[n][2 * j + 1] = upper ? s2 : recv;
+      }
+  }
+#pragma unroll
+  for (int n = 0; n < NL; ++n) {
+#pragma unroll
+    for (int q = 1; q < P; ++q) v[n][q] = cmul(v[n][q], twl<+1, T>(tw, lane * q));
+    small_dft<P, +1, T>(v[n]);
+  }
+}
+
+// The warp line FFT used by the kernels: the paired exchange for P >= 2, the
+// plain one for P = 1.  warp_freq gives the frequency that lane l, register q
+// holds after the forward transform (and must hold before the inverse).
+template <int P>
+__device__ __forceinline__ int warp_freq(int lane, int q) {
+  return P >= 2 ? pair_freq(lane, q, P) : q + P * bitrev5(lane);
+}
+template <int P, int NL, typename T>
+__device__ __forceinline__ void warp_fft_fwd_any(cplx<T> (&v)[NL][P], const cplx<T>* tw, int lane) {
+  if constexpr (P >= 2) warp_fft_fwd_pairs<P, NL, T>(v, tw, lane);
+  else warp_fft_fwd<P, NL, T>(v, tw, lane);
+}
+template <int P, int NL, typename T>
+__device__ __forceinline__ void warp_fft_inv_any(cplx<T> (&v)[NL][P], const cplx<T>* tw, int lane) {
+  if constexpr (P >= 2) warp_fft_inv_pairs<P, NL, T>(v, tw, lane);
+  else warp_fft_inv<P, NL, T>(v, tw, lane);
+}
+
 // shared-memory index with one spare slot per 16 entries: the stride-P
 // accesses of the bit-reversed layout then spread evenly over the banks
 __device__ __forceinline__ int wpad(int i) { return i + (i >> 4); }
@@ -195,21 +303,20 @@ __device__ __forceinline__ void load_rows<double>(const double* p, double (&d)[1
 template <int DIR, int P, int PS, typename T>
 __device__ __forceinline__ void warp_lines(cplx<T>* buf, int nlines, int ls, const cplx<T>* tw, int tid, int nthr) {
   const int lane = tid & 31, nwarps = nthr >> 5;
-  const int brev = bitrev5(lane);
   for (int line = tid >> 5; line < nlines; line += nwarps) {
     cplx<T>* b = buf + (size_t)line * ls;
     cplx<T> v[1][P];
     if (DIR < 0) {
 #pragma unroll
       for (int j = 0; j < P; ++j) v[0][j] = b[padi<PS>(lane + 32 * j)];
-      warp_fft_fwd<P, 1, T>(v, tw, lane);
+      warp_fft_fwd_any<P, 1, T>(v, tw, lane);
       __syncwarp();
 #pragma unroll
-      for (int q = 0; q < P; ++q) b[padi<PS>(q + P * brev)] = v[0][q];
+      for (int q = 0; q < P; ++q) b[padi<PS>(warp_freq<P>(lane, q))] = v[0][q];
     } else {
 #pragma unroll
-      for (int q = 0; q < P; ++q) v[0][q] = b[padi<PS>(q + P * brev)];
-      warp_fft_inv<P, 1, T>(v, tw, lane);
+      for (int q = 0; q < P; ++q) v[0][q] = b[padi<PS>(warp_freq<P>(lane, q))];
+      warp_fft_inv_any<P, 1, T>(v, tw, lane);
       __syncwarp();
 #pragma unroll
       for (int j = 0; j < P; ++j) b[padi<PS>(lane + 32 * j)] = v[0][j];
@@ -275,7 +382,6 @@ __global__ void __launch_bounds__(kWarpRowThreads, (P <= 4 ? 2 : 1)) row_pass_wa
     const bool incremental = ctl->form == 1;
     const size_t cstrS = (size_t)g.nrows * H;
     const size_t cstrE = (size_t)g.m;
-    const int brev = bitrev5(lane);
     const T* Eload = E + (size_t)load * NV * cstrE;
     cplx<T>* Sload = S + (size_t)load * NV * cstrS;
     for (long long row = (long long)qb * NW + warp; row < g.nrows; row += (long long)blocks_per_load * NW) {
@@ -315,7 +421,7 @@ __global__ void __launch_bounds__(kWarpRowThreads, (P <= 4 ? 2 : 1)) row_pass_wa
         for (int p = 0; p < 3; ++p)
 #pragma unroll
           for (int q = 0; q < P; ++q) {
-            const int k = q + P * brev;
+            const int k = warp_freq<P>(lane, q);
             const bool lo = k <= L / 2;
             const int kk = lo ? k : L - k;
             cplx<T> A = ws[wpad((2 * p) * H + kk)], B = ws[wpad((2 * p + 1) * H + kk)];
@@ -324,7 +430,7 @@ __global__ void __launch_bounds__(kWarpRowThreads, (P <= 4 ? 2 : 1)) row_pass_wa
             z[p][q].y = A.y + B.x;
           }
         __syncwarp();
-        warp_fft_inv<P, 3, T>(z, tw, lane);
+        warp_fft_inv_any<P, 3, T>(z, tw, lane);
       }
       // 3. pointwise: E_new, residual sums, tau
       T rd = T(0), rn = T(0);
@@ -365,11 +471,11 @@ __global__ void __launch_bounds__(kWarpRowThreads, (P <= 4 ? 2 : 1)) row_pass_wa
       }
       // 4. forward FFT, then split each line's spectrum into the half
       //    spectra of its two components
-      warp_fft_fwd<P, 3, T>(z, tw, lane);
+      warp_fft_fwd_any<P, 3, T>(z, tw, lane);
 #pragma unroll
       for (int p = 0; p < 3; ++p)
 #pragma unroll
-        for (int q = 0; q < P; ++q) ws[wpad(p * L + q + P * brev)] = z[p][q];
+        for (int q = 0; q < P; ++q) ws[wpad(p * L + warp_freq<P>(lane, q))] = z[p][q];
       __syncwarp();
 #pragma unroll
       for (int p = 0; p < 3; ++p)
