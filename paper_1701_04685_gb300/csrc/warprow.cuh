@@ -295,6 +295,95 @@ __device__ __forceinline__ void load_rows<double>(const double* p, double (&d)[1
   }
 }
 
+// Two independent 32-point lines transformed together with the paired lane
+// exchange (line x in r0, line y in r1, lane l holding point l of each); after
+// the forward stages lane l, register r holds line (l < 16 ? x : y) at
+// frequency bitrev5(((l & 15) << 1) | r); the inverse undoes the stages.
+template <typename T>
+__device__ __forceinline__ void lane_pairs_fwd(cplx<T>& r0, cplx<T>& r1, const cplx<T>* tw, int lane) {
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool upper = (lane & h) != 0;
+    const T sgn = upper ? T(-1) : T(1);
+    const cplx<T> s = upper ? r1 : r0;
+    const cplx<T> t = shfl_xor_c<T>(upper ? r0 : r1, h);
+    r0 = cadd(s, t);
+    const cplx<T> d = csub(s, t);
+    if (h > 1) {
+      cplx<T> w = twl<-1, T>(tw, (lane & (h - 1)) * (16 / h));
+      w.x *= sgn;
+      w.y *= sgn;
+      r1 = cmul(d, w);
+    } else {
+      r1.x = sgn * d.x;
+      r1.y = sgn * d.y;
+    }
+  }
+}
+template <typename T>
+__device__ __forceinline__ void lane_pairs_inv(cplx<T>& r0, cplx<T>& r1, const cplx<T>* tw, int lane) {
+#pragma unroll
+  for (int h = 1; h <= 16; h <<= 1) {
+    const bool upper = (lane & h) != 0;
+    const T sgn = upper ? T(-1) : T(1);
+    cplx<T> u;
+    if (h > 1) {
+      cplx<T> w = twl<+1, T>(tw, (lane & (h - 1)) * (16 / h));
+      w.x *= sgn;
+      w.y *= sgn;
+      u = cmul(r1, w);
+    } else {
+      u.x = sgn * r1.x;
+      u.y = sgn * r1.y;
+    }
+    const cplx<T> s2 = cadd(r0, u);
+    const cplx<T> recv = shfl_xor_c<T>(csub(r0, u), h);
+    r0 = upper ? recv : s2;
+    r1 = upper ? s2 : recv;
+  }
+}
+
+// Lines of 32 points, two per warp at a time (the last one of an odd count
+// paired with zeros), in place; ends with a team barrier.
+template <int DIR, int PS, typename T>
+__device__ __forceinline__ void warp_lines32_pairs(cplx<T>* buf, int nlines, int ls, const cplx<T>* tw, int tid,
+                                                   int nthr) {
+  const int lane = tid & 31, nwarps = nthr >> 5;
+  const int half = lane >> 4;
+  const int fpos = bitrev5(((lane & 15) << 1));   // frequency of register 0; register 1: fpos + 16
+  for (int pr = tid >> 5; 2 * pr < nlines; pr += nwarps) {
+    cplx<T>* bx = buf + (size_t)(2 * pr) * ls;
+    const bool has_y = 2 * pr + 1 < nlines;
+    cplx<T>* by = has_y ? bx + ls : bx;
+    cplx<T>* mine = half ? by : bx;   // the line this lane holds after the forward stages
+    cplx<T> r0, r1;
+    if (DIR < 0) {
+      r0 = bx[padi<PS>(lane)];
+      if (has_y) r1 = by[padi<PS>(lane)];
+      else { r1.x = T(0); r1.y = T(0); }
+      lane_pairs_fwd<T>(r0, r1, tw, lane);
+      __syncwarp();
+      if (!half || has_y) {
+        mine[padi<PS>(fpos)] = r0;
+        mine[padi<PS>(fpos + 16)] = r1;
+      }
+    } else {
+      if (!half || has_y) {
+        r0 = mine[padi<PS>(fpos)];
+        r1 = mine[padi<PS>(fpos + 16)];
+      } else {
+        r0.x = r0.y = r1.x = r1.y = T(0);
+      }
+      lane_pairs_inv<T>(r0, r1, tw, lane);
+      __syncwarp();
+      bx[padi<PS>(lane)] = r0;
+      if (has_y) by[padi<PS>(lane)] = r1;
+    }
+    __syncwarp();
+  }
+  team_sync(nthr);
+}
+
 // In-place transform of `nlines` lines of length L = 32 P held in shared
 // memory (line q at buf + q * ls, entry i at padi<PS>(i)), one warp per line,
 // by the warps of a thread team (threads 0 .. nthr-1).  Forward takes natural
@@ -332,7 +421,7 @@ template <int DIR, int PS, typename T>
 __device__ __forceinline__ bool warp_lines_any(cplx<T>* buf, int nlines, int ls, int L, const cplx<T>* tw, int tid,
                                                int nthr) {
   switch (L) {
-    case 32: warp_lines<DIR, 1, PS, T>(buf, nlines, ls, tw, tid, nthr); return true;
+    case 32: warp_lines32_pairs<DIR, PS, T>(buf, nlines, ls, tw, tid, nthr); return true;
     case 64: warp_lines<DIR, 2, PS, T>(buf, nlines, ls, tw, tid, nthr); return true;
     case 128: warp_lines<DIR, 4, PS, T>(buf, nlines, ls, tw, tid, nthr); return true;
     case 256: warp_lines<DIR, 8, PS, T>(buf, nlines, ls, tw, tid, nthr); return true;
