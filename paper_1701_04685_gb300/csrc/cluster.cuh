@@ -167,6 +167,8 @@ __device__ __forceinline__ void cluster_solve_body(const GridInfo& g, const DevP
     cplx<T>* Z = W0;
     cplx<T>* Zo = W1;
     if (with_inverse) {
+      // rebuild Z = A + i B per line pair in natural order (conflict-free
+      // reads of the unpadded half spectra), then the inverse transform
       for (int idx = threadIdx.x; idx < npair * L; idx += blockDim.x) {
         const int p = fdiv(idx, fL), k = idx - p * L;
         const int fa = 2 * p, fb = 2 * p + 1;
@@ -220,20 +222,24 @@ __device__ __forceinline__ void cluster_solve_body(const GridInfo& g, const DevP
     if (nreal & 1)
       for (int x = threadIdx.x; x < L; x += blockDim.x) Z[(npair - 1) * Lp + padi<PS>(x)].y = T(0);
     __syncthreads();
-    bool warp_done = false;
-    if constexpr (POW2 && sizeof(T) == 4) warp_done = warp_lines_any<-1, PS, T>(Z, npair, Lp, L, tw1, threadIdx.x, blockDim.x);
-    cplx<T>* Zf = warp_done ? Z : fft_lines_pp<-1, T, PS, POW2>(Z, Zo, npair, Lp, plan1, tw1);
-    for (int idx = threadIdx.x; idx < npair * H; idx += blockDim.x) {
-      const int p = fdiv(idx, fH), k = idx - p * H;
-      const cplx<T> zk = Zf[p * Lp + padi<PS>(k)];
-      const cplx<T> zm = Zf[p * Lp + padi<PS>(k == 0 ? 0 : L - k)];
-      cplx<T> A, B;
-      A.x = T(0.5) * (zk.x + zm.x);
-      A.y = T(0.5) * (zk.y - zm.y);
-      B.x = T(0.5) * (zk.y + zm.y);
-      B.y = T(-0.5) * (zk.x - zm.x);
-      Sl[(2 * p) * H + k] = A;
-      if (2 * p + 1 < nreal) Sl[(2 * p + 1) * H + k] = B;
+    // FP32 power-of-two rows: forward transform and split by the owning warp
+    bool fused = false;
+    if constexpr (POW2 && sizeof(T) == 4)
+      fused = warp_rows_fwd_split_any<PS, T>(Z, npair, Lp, L, Sl, H, nreal, tw1, threadIdx.x, blockDim.x);
+    if (!fused) {
+      cplx<T>* Zf = fft_lines_pp<-1, T, PS, POW2>(Z, Zo, npair, Lp, plan1, tw1);
+      for (int idx = threadIdx.x; idx < npair * H; idx += blockDim.x) {
+        const int p = fdiv(idx, fH), k = idx - p * H;
+        const cplx<T> zk = Zf[p * Lp + padi<PS>(k)];
+        const cplx<T> zm = Zf[p * Lp + padi<PS>(k == 0 ? 0 : L - k)];
+        cplx<T> A, B;
+        A.x = T(0.5) * (zk.x + zm.x);
+        A.y = T(0.5) * (zk.y - zm.y);
+        B.x = T(0.5) * (zk.y + zm.y);
+        B.y = T(-0.5) * (zk.x - zm.x);
+        Sl[(2 * p) * H + k] = A;
+        if (2 * p + 1 < nreal) Sl[(2 * p + 1) * H + k] = B;
+      }
     }
   };
 

@@ -430,6 +430,58 @@ __device__ __forceinline__ bool warp_lines_any(cplx<T>* buf, int nlines, int ls,
   }
 }
 
+// Forward row transform of a 2-D cluster CTA with the split into half
+// spectra done by the warp that owns the line (no block barrier between
+// transform and split).  Line p carries the real rows 2p and 2p+1 (the last
+// one zero when nreal is odd) as real and imaginary parts: natural order in
+// `buf` -> forward transform -> A = (Z_k + conj Z_{L-k}) / 2 and
+// B = (Z_k - conj Z_{L-k}) / 2i written to `S` (rows of H entries, natural
+// order); `buf` serves as the warp's staging line.
+template <int P, int PS, typename T>
+__device__ __forceinline__ void warp_rows_fwd_split(cplx<T>* buf, int nlines, int ls, cplx<T>* S, int H, int nreal,
+                                                    const cplx<T>* tw, int tid, int nthr) {
+  constexpr int L = 32 * P;
+  const int lane = tid & 31, nwarps = nthr >> 5;
+  for (int line = tid >> 5; line < nlines; line += nwarps) {
+    cplx<T>* b = buf + (size_t)line * ls;
+    cplx<T> v[1][P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) v[0][j] = b[padi<PS>(lane + 32 * j)];
+    warp_fft_fwd_any<P, 1, T>(v, tw, lane);
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < P; ++q) b[padi<PS>(warp_freq<P>(lane, q))] = v[0][q];
+    __syncwarp();
+    const int fa = 2 * line, fb = fa + 1;
+    for (int k = lane; k < H; k += 32) {
+      const cplx<T> zk = b[padi<PS>(k)];
+      const cplx<T> zm = b[padi<PS>(k == 0 ? 0 : L - k)];
+      cplx<T> A, B;
+      A.x = T(0.5) * (zk.x + zm.x);
+      A.y = T(0.5) * (zk.y - zm.y);
+      B.x = T(0.5) * (zk.y + zm.y);
+      B.y = T(-0.5) * (zk.x - zm.x);
+      S[fa * H + k] = A;
+      if (fb < nreal) S[fb * H + k] = B;
+    }
+    __syncwarp();
+  }
+}
+
+// the above for a runtime row length L (32..512); false for other lengths
+template <int PS, typename T>
+__device__ __forceinline__ bool warp_rows_fwd_split_any(cplx<T>* buf, int nlines, int ls, int L, cplx<T>* S, int H,
+                                                        int nreal, const cplx<T>* tw, int tid, int nthr) {
+  switch (L) {
+    case 32: warp_rows_fwd_split<1, PS, T>(buf, nlines, ls, S, H, nreal, tw, tid, nthr); return true;
+    case 64: warp_rows_fwd_split<2, PS, T>(buf, nlines, ls, S, H, nreal, tw, tid, nthr); return true;
+    case 128: warp_rows_fwd_split<4, PS, T>(buf, nlines, ls, S, H, nreal, tw, tid, nthr); return true;
+    case 256: warp_rows_fwd_split<8, PS, T>(buf, nlines, ls, S, H, nreal, tw, tid, nthr); return true;
+    case 512: warp_rows_fwd_split<16, PS, T>(buf, nlines, ls, S, H, nreal, tw, tid, nthr); return true;
+    default: return false;
+  }
+}
+
 constexpr int kWarpRowThreads = 256;
 
 // Rows are dealt to the warps of the grid round-robin; a launch sizes its grid
