@@ -189,6 +189,17 @@ void fh_solver_destroy(fh_solver* s);
 fh_status fh_set_stiffness_phases(fh_solver* s, const uint8_t* phase, int nphase,
                                   const double* Cp);
 
+/* Stiffness given point by point (Sec. 3.1, C in SSym_d(L^inf), sampled at
+ * the pattern points): C[m*n_v*n_v] Mandel matrices in storage order (the
+ * order of fh_pattern_points), host or device memory, read once.  The
+ * kernels index the stiffness through a phase id per point and a table of at
+ * most 16 matrices, so the field is reduced to its distinct matrices (exact,
+ * bitwise comparison) and passed on as in fh_set_stiffness_phases; the result
+ * is identical to that call with the same matrices.  Errors: FH_ERR_ARG
+ * (non-finite or non-symmetric matrix), FH_ERR_UNSUPPORTED when the field
+ * holds more than 16 distinct matrices (nothing is changed then). */
+fh_status fh_set_stiffness_field(fh_solver* s, const double* C);
+
 /* Reference medium C0 (n_v x n_v Mandel, host).  NULL selects the rule of
  * Moulinec & Suquet (1998): isotropic with lambda0, mu0 the midpoints of the
  * phases' ranges (phases read as isotropic: lambda = C[0][1], 2 mu = C[n_v-1]

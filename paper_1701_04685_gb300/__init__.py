@@ -76,6 +76,7 @@ def library():
             "fh_solver_create": (I, [P, C.POINTER(fh_generator), I, P, C.POINTER(P)]),
             "fh_solver_destroy": (V, [P]),
             "fh_set_stiffness_phases": (I, [P, P, I, P]),
+            "fh_set_stiffness_field": (I, [P, P]),
             "fh_set_reference": (I, [P, P]),
             "fh_solve": (I, [P, I, P, C.POINTER(fh_solve_opts), C.POINTER(fh_result)]),
             "fh_get_strain": (I, [P, I, P]),
@@ -101,7 +102,7 @@ def exported_symbols():
     """Names of the C entry points the binding expects (all declared in fftHomog.h)."""
     return FNO_SYMBOLS + ["fh_pattern_create", "fh_pattern_destroy", "fh_pattern_info", "fh_pattern_points",
             "fh_pattern_numerators", "fh_pattern_half_freqs", "fh_solver_create", "fh_solver_destroy",
-            "fh_set_stiffness_phases", "fh_set_reference", "fh_solve", "fh_get_strain", "fh_set_strain",
+            "fh_set_stiffness_phases", "fh_set_stiffness_field", "fh_set_reference", "fh_solve", "fh_get_strain", "fh_set_strain",
             "fh_get_ceff", "fh_get_green", "fh_get_residuals", "fh_profile_passes", "fh_status_string",
             "fh_last_error", "fh_mean_stress_noalloc", "fh_solve_batch",
             "fh_get_tuning"]
@@ -245,6 +246,15 @@ class Solver:
         else:
             ph = np.ascontiguousarray(np.asarray(phase, dtype=np.uint8))
         _check(library().fh_set_stiffness_phases(self._h, _ptr(ph), int(Cp.shape[0]), _ptr(Cp)))
+
+    def set_stiffness_field(self, C):
+        """Point-by-point Mandel stiffness, shape (m, n_v, n_v) in storage order
+        (numpy array or a CUDA tensor of float64)."""
+        if hasattr(C, "data_ptr"):
+            Cf = C.contiguous()
+        else:
+            Cf = np.ascontiguousarray(np.asarray(C, dtype=np.float64))
+        _check(library().fh_set_stiffness_field(self._h, _ptr(Cf)))
 
     def set_reference(self, C0=None):
         if C0 is None:

@@ -958,6 +958,41 @@ fh_status fh_set_stiffness_phases(fh_solver* s, const uint8_t* phase, int nphase
   return FH_OK;
 }
 
+fh_status fh_set_stiffness_field(fh_solver* s, const double* C) {
+  if (!s || !C) { fh::set_error("null argument"); return FH_ERR_ARG; }
+  const int nv = s->g.nv;
+  const size_t per = (size_t)nv * nv;
+  const size_t m = (size_t)s->g.m;
+  // the field on the host (it may live in device memory)
+  std::vector<double> host;
+  const double* Ch = C;
+  cudaPointerAttributes attr{};
+  if (cudaPointerGetAttributes(&attr, C) == cudaSuccess && attr.type == cudaMemoryTypeDevice) {
+    host.resize(m * per);
+    CK(cudaMemcpy(host.data(), C, m * per * sizeof(double), cudaMemcpyDeviceToHost));
+    Ch = host.data();
+  }
+  cudaGetLastError();   // a host pointer may leave an error behind on some drivers
+  std::vector<uint8_t> ids(m);
+  double table[kMaxPhases * 36];
+  int nphase = 0;
+  for (size_t i = 0; i < m; ++i) {
+    const double* c = Ch + i * per;
+    int q = 0;
+    while (q < nphase && std::memcmp(table + q * per, c, per * sizeof(double)) != 0) ++q;
+    if (q == nphase) {
+      if (nphase == kMaxPhases) {
+        fh::set_error("stiffness field holds more than 16 distinct matrices");
+        return FH_ERR_UNSUPPORTED;
+      }
+      std::memcpy(table + q * per, c, per * sizeof(double));
+      ++nphase;
+    }
+    ids[i] = (uint8_t)q;
+  }
+  return fh_set_stiffness_phases(s, ids.data(), nphase, table);
+}
+
 fh_status fh_set_reference(fh_solver* s, const double* C0) {
   if (!s) { fh::set_error("null solver"); return FH_ERR_ARG; }
   if (!s->have_phases) { fh::set_error("set the stiffness before the reference medium"); return FH_ERR_STATE; }
