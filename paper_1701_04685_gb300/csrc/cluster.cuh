@@ -190,33 +190,55 @@ __device__ __forceinline__ void cluster_solve_body(const GridInfo& g, const DevP
       Z = warp_done ? W0 : fft_lines_pp<+1, T, PS, POW2>(W0, W1, npair, Lp, plan1, tw1);
       Zo = (Z == W0) ? W1 : W0;
     }
-    for (int idx = threadIdx.x; idx < nrow * L; idx += blockDim.x) {
-      const int r = fdiv(idx, fL), x = idx - r * L;
-      T en[NV];
+    // E update, residual sums and stress, two points per thread at a time
+    // with every shared-memory load of both issued before any store
+    for (int base = threadIdx.x; base < nrow * L; base += 2 * blockDim.x) {
+      T en[2][NV], eo[2][NV];
+      int ph[2], rr[2], xx[2];
+      bool ok[2];
 #pragma unroll
-      for (int c = 0; c < NV; ++c) {
-        const int f = r * NV + c;
-        T* ep = &El[f * L + x];
-        if (with_inverse) {
-          const cplx<T> zz = Z[(f >> 1) * Lp + padi<PS>(x)];
-          en[c] = ((f & 1) ? zz.y : zz.x) * scale;
-          if (incremental) en[c] += *ep;
-          acc_d.add_sq(en[c] - *ep);
-          acc_n.add_sq(en[c] + e0[c]);
-          *ep = en[c];
-        } else {
-          en[c] = *ep;
+      for (int u = 0; u < 2; ++u) {
+        const int idx = base + u * blockDim.x;
+        ok[u] = idx < nrow * L;
+        const int id = ok[u] ? idx : 0;
+        rr[u] = fdiv(id, fL);
+        xx[u] = id - rr[u] * L;
+        ph[u] = phl[id];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+          const int f = rr[u] * NV + c;
+          eo[u][c] = El[f * L + xx[u]];
+          if (with_inverse) {
+            const cplx<T> zz = Z[(f >> 1) * Lp + padi<PS>(xx[u])];
+            en[u][c] = ((f & 1) ? zz.y : zz.x) * scale;
+          }
         }
       }
-      const T* dc = dcs + phl[idx] * NV * NV;
 #pragma unroll
-      for (int a = 0; a < NV; ++a) {
-        T t = T(0);
+      for (int u = 0; u < 2; ++u) {
+        if (!ok[u]) continue;
+        const int r = rr[u], x = xx[u];
 #pragma unroll
-        for (int b = 0; b < NV; ++b) t += dc[a * NV + b] * (en[b] + e0[b]);
-        const int f = r * NV + a;
-        if (f & 1) Z[(f >> 1) * Lp + padi<PS>(x)].y = t;
-        else Z[(f >> 1) * Lp + padi<PS>(x)].x = t;
+        for (int c = 0; c < NV; ++c) {
+          if (with_inverse) {
+            if (incremental) en[u][c] += eo[u][c];
+            acc_d.add_sq(en[u][c] - eo[u][c]);
+            acc_n.add_sq(en[u][c] + e0[c]);
+            El[(r * NV + c) * L + x] = en[u][c];
+          } else {
+            en[u][c] = eo[u][c];
+          }
+        }
+        const T* dc = dcs + ph[u] * NV * NV;
+#pragma unroll
+        for (int a = 0; a < NV; ++a) {
+          T t = T(0);
+#pragma unroll
+          for (int b = 0; b < NV; ++b) t += dc[a * NV + b] * (en[u][b] + e0[b]);
+          const int f = r * NV + a;
+          if (f & 1) Z[(f >> 1) * Lp + padi<PS>(x)].y = t;
+          else Z[(f >> 1) * Lp + padi<PS>(x)].x = t;
+        }
       }
     }
     if (nreal & 1)
