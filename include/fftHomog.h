@@ -113,7 +113,9 @@ typedef struct {
                       case holds the fields in distributed shared memory and
                       runs every iteration in one launch).  Automatic picks 2
                       when the fields fit, else 1.                            */
-  int cluster;     /* cluster size for path 2: 0 = automatic, 8 or 16        */
+  int cluster;     /* cluster size for path 2: 0 = automatic (fh_solve: 16
+                      where the fields fit, else 8; fh_solve_batch: 8 where
+                      they fit, else 16), 8 or 16                            */
   int form;        /* 0: the Lippmann-Schwinger discretisation, Eq.
                       (pde_coefficients) of Thm. pde_discretization:
                       E <- -Gamma^p (C - C0)(E + eps0).
