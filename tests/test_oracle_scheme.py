@@ -124,6 +124,42 @@ def test_ceff_between_reuss_and_voigt():
     assert np.linalg.eigvalsh(voigt - Ce).max() > 1e-3   # not trivially equal
 
 
+def _hs_lower(K_a, mu_a, K_b, mu_b, f_a, f_b):
+    """Two-dimensional (plane strain) Hashin-Shtrikman bound on the in-plane bulk
+    modulus K = lambda + mu and the shear modulus mu of an isotropic two-phase
+    composite, taken with phase a as the reference (the lower bound when phase
+    a is the softer one in both moduli, the upper bound otherwise)."""
+    K = K_a + f_b / (1.0 / (K_b - K_a) + f_a / (K_a + mu_a))
+    mu = mu_a + f_b / (1.0 / (mu_b - mu_a) + f_a * (K_a + 2.0 * mu_a) / (2.0 * mu_a * (K_a + mu_a)))
+    return K, mu
+
+
+@pytest.mark.parametrize("count,rmin,rmax,seed,E2", [(40, 0.03, 0.06, 1, 10.0), (60, 0.02, 0.05, 2, 20.0)])
+def test_ceff_within_hashin_shtrikman_bounds(count, rmin, rmax, seed, E2):
+    """Many small disks give a nearly isotropic composite: the isotropic
+    projections of the converged C_eff (bulk (C11 + C22 + 2 C12) / 4, shear
+    (C11 + C22 - 2 C12) / 4 and C33 / 2 in Mandel form) lie between the
+    plane-strain Hashin-Shtrikman bounds of the sampled volume fractions.  A
+    soft check: the bounds hold for the continuum problem of an isotropic
+    composite, which the discrete, finitely many disks only approximate."""
+    rng = np.random.default_rng(seed)
+    c, r = W.random_inclusions(rng, 2, count, rmin, rmax)
+    M = [[64, 0], [0, 64]]
+    T, C, C0, Gp, ids, Cp = _setup(M, G.Generator("dirichlet"), [(1.0, 0.3), (E2, 0.3)],
+                                   lambda y: W.phase_ids(y, c, r))
+    out = scheme.solve(T, Gp, C, C0, np.eye(3), tol=1e-10, max_iter=20000)
+    Ce = scheme.effective_stiffness(out["mean_stress"], np.eye(3))
+    f2 = ids.mean()
+    f1 = 1.0 - f2
+    (l1, m1), (l2, m2) = material.lame(1.0, 0.3), material.lame(E2, 0.3)
+    K_lo, mu_lo = _hs_lower(l1 + m1, m1, l2 + m2, m2, f1, f2)
+    K_hi, mu_hi = _hs_lower(l2 + m2, m2, l1 + m1, m1, f2, f1)
+    K_e = (Ce[0, 0] + Ce[1, 1] + 2 * Ce[0, 1]) / 4
+    for mu_e in ((Ce[0, 0] + Ce[1, 1] - 2 * Ce[0, 1]) / 4, Ce[2, 2] / 2):
+        assert mu_lo < mu_e < mu_hi
+    assert K_lo < K_e < K_hi
+
+
 @pytest.mark.parametrize("gen", GENS2[:2] + GENS2[3:], ids=lambda g: g.kind)
 def test_converged_iterate_solves_discrete_equation(gen):
     """At the fixed point, E + Gamma^p (C - C0)(E + eps0) = 0 (Eq. (pde_coefficients)),
