@@ -1,7 +1,7 @@
 #!/usr/bin/env python
 """Benchmark of the Basic-Scheme solver on the anisotropic dlVP workload.
 
-Workload (BASELINE metric configuration): M = [[128,32],[0,128]] (m = 16384,
+Workload (the configuration the headline metric is quoted on): M = [[128,32],[0,128]] (m = 16384,
 Smith grid 32 x 512), de la Vallee Poussin generator with plateau |u| <= 0.25
 and ramp to 0.75, 20 random non-overlapping disks (radii U[0.03,0.08], seed 2)
 at contrast 100, nu = 0.3, the 3 Mandel unit strains, Cauchy tolerance 1e-6.
@@ -34,7 +34,14 @@ import sys
 import tempfile
 import time
 
-import numpy as np
+# The FP64 CPU oracle (the reference arm and the cpu_baseline leg) is timed on
+# one host thread: pin numpy's BLAS before numpy loads, so that "cores": 1 in
+# the JSON line is what actually ran (its threaded GEMMs on small tiles were
+# slower anyway).
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
