@@ -22,7 +22,13 @@ periodic anisotropic translation invariant spaces" (arXiv 1701.04685):
 * ``scheme``     -- fixed-point iteration on Eq. (pde_coefficients), Cauchy
                     residual (Sec. 4) and the effective stiffness (Sec. 3.1).
 
-Parity status: every function is pinned by ``tests/test_oracle_*.py`` except
-the reference-medium rule (``material.reference_medium_ms``), which the paper
-never states: parity unpinned.
+* ``fno``        -- forward pass and loss of the learned start (a Fourier
+                    neural operator; not part of the paper's method); the GPU
+                    gradients are checked against central finite differences
+                    of this loss.
+
+Parity status: every function is pinned by ``tests/test_oracle_*.py``.  The
+reference-medium rule (``material.reference_medium_ms``) is a reading, since
+the paper never states C0: it is pinned to its defining property (phase
+spectra of C0^-1 C centred on 1) and the contraction bound that follows.
 """

@@ -93,8 +93,9 @@ def lame(E, nu):
 def reference_medium_ms(lams, mus):
     """Reference medium of Moulinec & Suquet (1998): midpoints of the phase Lame ranges.
 
-    The paper never states C0 (parity unpinned); this is the reading shared with
-    the product.
+    The paper never states C0; this is the reading shared with the product.
+    Pinned to its defining property: per isotropic eigenspace the eigenvalues
+    of C0^-1 C over the phases span an interval centred on 1.
     """
     return 0.5 * (min(lams) + max(lams)), 0.5 * (min(mus) + max(mus))
 

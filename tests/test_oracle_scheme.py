@@ -124,6 +124,59 @@ def test_ceff_between_reuss_and_voigt():
     assert np.linalg.eigvalsh(voigt - Ce).max() > 1e-3   # not trivially equal
 
 
+@pytest.mark.parametrize("phases", [[(1.0, 0.3), (10.0, 0.3)], [(2.0, 0.2), (50.0, 0.35), (7.0, 0.3)]])
+def test_reference_medium_centres_the_phase_spectra(phases):
+    """Defining property of the Moulinec-Suquet reference medium: per isotropic
+    eigenspace (the dilatational one with eigenvalue d lambda + 2 mu, the
+    deviatoric one with 2 mu) the eigenvalues of C0^-1 C over the phases span
+    an interval centred on 1, so the spread max |eig - 1| is the smallest any
+    isotropic C0 can give; for two phases of equal Poisson ratio and contrast
+    kappa, C0^-1 C_i = (1 -+ rho) I with rho = (kappa - 1) / (kappa + 1)."""
+    for d in (2, 3):
+        lm = [material.lame(E, nu) for E, nu in phases]
+        l0, m0 = material.reference_medium_ms([l for l, _ in lm], [m for _, m in lm])
+        C0 = material.isotropic_mandel(l0, m0, d)
+        eigs = [np.linalg.eigvals(np.linalg.solve(C0, material.isotropic_mandel(l, m, d))).real
+                for l, m in lm]
+        bulk = np.array([(d * l + 2 * m) / (d * l0 + 2 * m0) for l, m in lm])
+        dev = np.array([m / m0 for _, m in lm])
+        for e, b, v in zip(eigs, bulk, dev):
+            assert np.sort(e) == pytest.approx(np.sort([b] + [v] * (len(e) - 1)), rel=1e-12)
+        for sp in (bulk, dev):
+            assert sp.min() + sp.max() == pytest.approx(2.0, rel=1e-12)
+        if len(phases) == 2 and phases[0][1] == phases[1][1]:
+            kappa = phases[1][0] / phases[0][0]
+            rho = (kappa - 1) / (kappa + 1)
+            for (l, m), sgn in zip(lm, (-1, 1)):
+                A = np.linalg.solve(C0, material.isotropic_mandel(l, m, d))
+                assert np.abs(A - (1 + sgn * rho) * np.eye(len(A))).max() < 1e-12
+
+
+@pytest.mark.parametrize("kappa", [10.0, 100.0])
+def test_dirichlet_error_contracts_by_contrast_ratio(kappa):
+    """With the Dirichlet kernel Gamma^p C0 is the C0-orthogonal projection onto
+    compatible zero-mean strains, and for equal Poisson ratios C - C0 = s(x) C0
+    with |s| = rho = (kappa - 1) / (kappa + 1) under the Moulinec-Suquet C0.  The
+    error e_n = E_n - E* of the fixed point therefore shrinks in the C0 energy
+    norm by at least rho per step (e_{n+1} = -Gamma^p C0 (s e_n)); a wrong sign,
+    table or C0 breaks the bound or the monotone decay."""
+    M = [[24, 5], [0, 20]]
+    T, C, C0, Gp, _, _ = _setup(M, G.Generator("dirichlet"), [(1.0, 0.3), (kappa, 0.3)], _disk_phase(0.3))
+    e0 = np.array([[0.3, -0.2, 0.5]])
+    star = scheme.solve(T, Gp, C, C0, e0, tol=1e-15, max_iter=20000)["E"][0]
+    rho = (kappa - 1) / (kappa + 1)
+    energy = lambda e: float(np.sqrt(np.einsum("ma,ab,mb->", e, C0, e)))
+    E = np.zeros_like(star)
+    err = [energy(E - star)]
+    for _ in range(25):
+        E = scheme.solve(T, Gp, C, C0, e0, max_iter=1, E_init=E[None])["E"][0]
+        err.append(energy(E - star))
+    for a, b in zip(err, err[1:]):
+        assert b <= rho * a * (1 + 1e-9) + 1e-12 * err[0]
+    # the rate is not far below the bound: the ratio settles within a factor 2 of rho
+    assert err[-1] / err[-2] > 0.5 * rho
+
+
 def _hs_lower(K_a, mu_a, K_b, mu_b, f_a, f_b):
     """Two-dimensional (plane strain) Hashin-Shtrikman bound on the in-plane bulk
     modulus K = lambda + mu and the shear modulus mu of an isotropic two-phase
