@@ -262,22 +262,4 @@ __device__ cplx<T>* fft_lines_pp(cplx<T>* buf, cplx<T>* tmp, int nlines, int ls,
   return in;
 }
 
-// As fft_lines_pp, with the result copied back into buf when it ended in tmp.
-template <int DIR, typename T>
-__device__ void fft_lines(cplx<T>* buf, cplx<T>* tmp, int nlines, int ls, const DevPlan& plan,
-                          const cplx<T>* __restrict__ tw) {
-  cplx<T>* in = fft_lines_pp<DIR, T>(buf, tmp, nlines, ls, plan, tw);
-  if (in != buf) {
-    const int L = plan.L;
-    const int total = nlines * L;
-    const FDiv fl = make_fdiv(L);
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-      const int line = fdiv(idx, fl);
-      const int x = idx - line * L;
-      buf[line * ls + x] = in[line * ls + x];
-    }
-    __syncthreads();
-  }
-}
-
 }  // namespace fh
