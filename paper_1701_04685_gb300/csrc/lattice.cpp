@@ -93,8 +93,24 @@ void col_bezout(int64_t A[3][3], int64_t T[3][3], int d, int p, int q, int64_t x
   }
 }
 
-// Smith normal form by Bezout eliminations: U A V = diag.
-bool smith(const int64_t M[3][3], int d, int64_t U[3][3], int64_t V[3][3], int64_t S[3]) {
+// Bezout coefficients for eliminating b against the pivot a: g = x a + y b.
+// With divisor_first, a pivot that divides b gives the plain elimination
+// step (x, y, g) = (1, 0, a), which leaves the pivot's row or column as it is.
+// The extended-gcd step alone can return (0, +-1) when |a| = |b|, a swap that
+// the following column (row) step undoes, so the elimination can cycle.
+int64_t bezout(int64_t a, int64_t b, bool divisor_first, int64_t* x, int64_t* y) {
+  if (divisor_first && b % a == 0) { *x = 1; *y = 0; return a; }
+  return ext_gcd(a, b, x, y);
+}
+
+// Smith normal form by Bezout eliminations: U A V = diag.  Returns false for a
+// singular matrix or when the elimination did not finish within its guard.
+// With divisor_first every step either clears its entry without touching
+// the pivot's row (column) or replaces the pivot by a gcd of strictly smaller
+// magnitude, and a divisibility fix-up is followed by such a step, so the
+// elimination ends.
+bool smith(const int64_t M[3][3], int d, bool divisor_first, int64_t U[3][3], int64_t V[3][3],
+           int64_t S[3]) {
   int64_t A[3][3];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
@@ -102,7 +118,8 @@ bool smith(const int64_t M[3][3], int d, int64_t U[3][3], int64_t V[3][3], int64
       U[i][j] = V[i][j] = (i == j);
     }
   for (int t = 0; t < d; ++t) {
-    for (int guard = 0; guard < 10000; ++guard) {
+    bool done = false;
+    for (int guard = 0; guard < 10000 && !done; ++guard) {
       // bring a nonzero entry of the trailing block to (t,t)
       if (A[t][t] == 0) {
         int bi = -1, bj = -1;
@@ -117,14 +134,14 @@ bool smith(const int64_t M[3][3], int d, int64_t U[3][3], int64_t V[3][3], int64
       for (int i = t + 1; i < d; ++i) {
         if (A[i][t] == 0) continue;
         int64_t x, y, a = A[t][t], b = A[i][t];
-        int64_t g = ext_gcd(a, b, &x, &y);
+        int64_t g = bezout(a, b, divisor_first, &x, &y);
         row_bezout<0>(A, U, d, t, i, x, y, b / g, a / g);
       }
       // clear row t right of the pivot
       for (int j = t + 1; j < d; ++j) {
         if (A[t][j] == 0) continue;
         int64_t x, y, a = A[t][t], b = A[t][j];
-        int64_t g = ext_gcd(a, b, &x, &y);
+        int64_t g = bezout(a, b, divisor_first, &x, &y);
         col_bezout<0>(A, V, d, t, j, x, y, b / g, a / g);
       }
       bool clean = true;
@@ -135,9 +152,10 @@ bool smith(const int64_t M[3][3], int d, int64_t U[3][3], int64_t V[3][3], int64
       for (int i = t + 1; i < d && bad < 0; ++i)
         for (int j = t + 1; j < d; ++j)
           if (A[i][j] % A[t][t] != 0) { bad = i; break; }
-      if (bad < 0) break;
+      if (bad < 0) { done = true; break; }
       for (int c = 0; c < d; ++c) { A[t][c] += A[bad][c]; U[t][c] += U[bad][c]; }
     }
+    if (!done) return false;
     if (A[t][t] < 0)
       for (int c = 0; c < d; ++c) { A[t][c] = -A[t][c]; U[t][c] = -U[t][c]; }
   }
@@ -218,7 +236,13 @@ fh_status build_pattern(int d, const int64_t* Min, Pattern* out) {
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) Mt[i][j] = P.M[j][i];
   adjugate(Mt, d, P.adjT);
-  if (!smith(P.M, d, P.U, P.V, P.snf)) { set_error("Smith normal form failed"); return FH_ERR_INTERNAL; }
+  // The extended-gcd elimination first (it fixes the storage layout of every
+  // pattern it handles); the divisor-first variant for the matrices on which
+  // it cycles, e.g. [[6, 4], [14, 10]].
+  if (!smith(P.M, d, false, P.U, P.V, P.snf) && !smith(P.M, d, true, P.U, P.V, P.snf)) {
+    set_error("Smith normal form failed");
+    return FH_ERR_INTERNAL;
+  }
   int64_t du = det3(P.U, d), dv = det3(P.V, d);
   if ((du != 1 && du != -1) || (dv != 1 && dv != -1)) { set_error("SNF transforms not unimodular"); return FH_ERR_INTERNAL; }
   adjugate(P.U, d, P.Uinv);

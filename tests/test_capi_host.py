@@ -76,6 +76,66 @@ def test_storage_grid_carries_the_pattern_dft(fh, M, rng):
         assert lhs == rhs
 
 
+def _unimodular(rng, d):
+    U = np.eye(d, dtype=np.int64)
+    for _ in range(6):
+        i, j = rng.choice(d, size=2, replace=False)
+        E = np.eye(d, dtype=np.int64)
+        E[i, j] = int(rng.integers(-2, 3))
+        U = U @ E
+    return U
+
+
+def _random_matrices(rng, count):
+    """Random integer matrices (mostly one Smith axis), plus U diag(s) V with
+    random unimodular U, V and divisor chains s, which have 2 or 3 Smith axes."""
+    out = []
+    while len(out) < count:
+        d = int(rng.integers(2, 4))
+        M = rng.integers(-9, 10, size=(d, d))
+        det = abs(lattice.det_int(M.tolist()))
+        if 0 < det <= 1500:
+            out.append(M.tolist())
+    for _ in range(count // 2):
+        d = int(rng.integers(2, 4))
+        s = [int(rng.integers(2, 5))]
+        while len(s) < d:
+            s.append(s[-1] * int(rng.integers(1, 4)))
+        M = _unimodular(rng, d) @ np.diag(s) @ _unimodular(rng, d)
+        out.append(M.tolist())
+    return out
+
+
+def test_random_integer_matrices_match_oracle(fh):
+    """The exact int64 Smith-form map on random unimodular-equivalence classes:
+    the library's points and half-spectrum frequencies are P(M) and a subset of
+    G(M^T) as the oracle enumerates them by brute force, the storage grid has
+    |det M| points, and the DFT phase identity of Eq. (Fouriermatrix) holds on
+    sampled pairs."""
+    rng = np.random.default_rng(77)
+    for M in _random_matrices(rng, 40):
+        p = fh.Pattern(M)
+        D = abs(lattice.det_int(M))
+        assert p.m == D and int(np.prod(p.dims)) == D
+        A = p.numerators()
+        ref, _ = lattice.pattern(M)
+        assert sorted(map(tuple, A.tolist())) == sorted(map(tuple, ref.tolist()))
+        H = p.half_freqs()
+        G = set(map(tuple, lattice.generating_set(M).tolist()))
+        assert all(tuple(h) in G for h in H)
+        dims = p.dims
+        assert len(H) == int(np.prod(dims[:-1])) * (dims[-1] // 2 + 1)
+        half_shape = dims[:-1] + [dims[-1] // 2 + 1]
+        for _ in range(50):
+            i = int(rng.integers(D))
+            f = int(rng.integers(len(H)))
+            n = np.unravel_index(i, dims)
+            l = np.unravel_index(f, half_shape)
+            lhs = int(H[f].astype(object).dot(A[i].astype(object))) % D
+            rhs = sum(int(l[k]) * int(n[k]) * (D // dims[k]) for k in range(len(dims))) % D
+            assert lhs == rhs
+
+
 def test_error_codes_without_gpu(fh):
     with pytest.raises(fh.FhError) as e:
         fh.Pattern([[2, 4], [1, 2]])
