@@ -154,3 +154,13 @@ def test_error_codes_without_gpu(fh):
     with pytest.raises(fh.FhError) as e:
         fh.Solver(p, fh.generator("dirichlet"), 17)
     assert e.value.status == -1          # nload_max > FH_MAX_LOADS
+
+
+def test_status_strings(fh):
+    """Every status of the header has its own message; other values map to one fallback."""
+    lib = fh.library()
+    codes = range(-9, 4)
+    msgs = [lib.fh_status_string(c).decode() for c in codes]
+    assert all(msgs) and len(set(msgs)) == len(msgs)
+    assert lib.fh_status_string(0).decode() == "ok"
+    assert lib.fh_status_string(99).decode() == lib.fh_status_string(-99).decode() not in msgs
