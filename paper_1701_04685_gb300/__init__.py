@@ -125,6 +125,31 @@ def _ptr(a):
     return C.c_void_p(a.ctypes.data)
 
 
+def _buf(x, count, dtype, what, writable=False):
+    """A buffer of exactly `count` elements of `dtype` for a C entry point.
+
+    A torch tensor (host or CUDA) is checked and passed as it is.  A numpy
+    array that the call writes (`writable`) is checked too; any other host
+    input is converted to a contiguous `dtype` array.  A mismatch raises
+    ValueError before the C call, which would otherwise read or write past
+    the buffer."""
+    dt = np.dtype(dtype)
+    if hasattr(x, "data_ptr"):
+        tdt = str(x.dtype).replace("torch.", "")
+        if x.numel() != count or tdt != dt.name or not x.is_contiguous():
+            raise ValueError(f"{what}: need a contiguous {dt.name} tensor of {count} elements, "
+                             f"got {tdt} of shape {tuple(x.shape)}")
+        return x
+    if writable:
+        if not isinstance(x, np.ndarray) or x.dtype != dt or x.size != count or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{what}: need a C-contiguous {dt.name} array of {count} elements")
+        return x
+    a = np.ascontiguousarray(np.asarray(x, dtype=dt))
+    if a.size != count:
+        raise ValueError(f"{what}: need {count} elements, got shape {a.shape}")
+    return a
+
+
 def nv_of(d):
     return 3 if d == 2 else 6
 
@@ -240,27 +265,31 @@ class Solver:
     __del__ = close
 
     def set_stiffness_phases(self, phase, Cp):
+        """phase: m uint8 ids in storage order (numpy, or a host or CUDA tensor);
+        Cp: (nphase, n_v, n_v) Mandel matrices."""
         Cp = np.ascontiguousarray(np.asarray(Cp, dtype=np.float64))
+        if Cp.ndim != 3 or Cp.shape[1:] != (self.nv, self.nv):
+            raise ValueError(f"Cp: need shape (nphase, {self.nv}, {self.nv}), got {Cp.shape}")
         if hasattr(phase, "data_ptr"):
-            ph = phase
+            ph = _buf(phase, self.m, np.uint8, "phase")
         else:
-            ph = np.ascontiguousarray(np.asarray(phase, dtype=np.uint8))
+            ph = np.asarray(phase)
+            if ph.dtype != np.uint8 and ph.size and (ph.min() < 0 or ph.max() > 255):
+                raise ValueError("phase: ids must lie in 0..255")
+            ph = _buf(ph, self.m, np.uint8, "phase")
         _check(library().fh_set_stiffness_phases(self._h, _ptr(ph), int(Cp.shape[0]), _ptr(Cp)))
 
     def set_stiffness_field(self, C):
         """Point-by-point Mandel stiffness, shape (m, n_v, n_v) in storage order
         (numpy array or a CUDA tensor of float64)."""
-        if hasattr(C, "data_ptr"):
-            Cf = C.contiguous()
-        else:
-            Cf = np.ascontiguousarray(np.asarray(C, dtype=np.float64))
+        Cf = _buf(C, self.m * self.nv * self.nv, np.float64, "stiffness field")
         _check(library().fh_set_stiffness_field(self._h, _ptr(Cf)))
 
     def set_reference(self, C0=None):
         if C0 is None:
             _check(library().fh_set_reference(self._h, None))
         else:
-            C0 = np.ascontiguousarray(np.asarray(C0, dtype=np.float64))
+            C0 = _buf(C0, self.nv * self.nv, np.float64, "C0")
             _check(library().fh_set_reference(self._h, _ptr(C0)))
 
     def solve(self, eps0, tol=1e-8, max_iter=1000, precision=FH_PREC_FP64, init=0, chunk=0, path=0, cluster=0,
@@ -269,6 +298,8 @@ class Solver:
         form: 0 Eq. (pde_coefficients), 1 the variational discretisation;
         tune: 1 picks path and cluster size by timing them (see fh_get_tuning)."""
         eps0 = np.ascontiguousarray(np.atleast_2d(np.asarray(eps0, dtype=np.float64)))
+        if eps0.ndim != 2 or eps0.shape[1] != self.nv:
+            raise ValueError(f"eps0: need shape (n_L, {self.nv}), got {eps0.shape}")
         opts = fh_solve_opts(float(tol), int(max_iter), int(precision), int(init), int(chunk), int(path),
                              int(cluster), int(form), int(tune))
         res = fh_result()
@@ -291,12 +322,12 @@ class Solver:
         """E of one load as (n_v, m) float64 (numpy, or into a given CUDA tensor)."""
         if out is None:
             out = np.empty((self.nv, self.m))
+        out = _buf(out, self.nv * self.m, np.float64, "strain", writable=True)
         _check(library().fh_get_strain(self._h, int(load), _ptr(out)))
         return out
 
     def set_strain(self, load, E):
-        if not hasattr(E, "data_ptr"):
-            E = np.ascontiguousarray(np.asarray(E, dtype=np.float64))
+        E = _buf(E, self.nv * self.m, np.float64, "strain")
         _check(library().fh_set_strain(self._h, int(load), _ptr(E)))
 
     def get_ceff(self, voigt=False):
@@ -336,8 +367,13 @@ def solve_batch(solvers, eps0s, tol=1e-6, max_iter=20000, precision=FH_PREC_MIXE
     """fh_solve_batch over Solver objects; eps0s[i] is solver i's (n_L, n_v) strains.  With path and
     cluster automatic, solvers tuned before (Solver.solve(..., tune=1)) keep their tuned choice."""
     n = len(solvers)
-    hs = (C.c_void_p * n)(*[sv._h.value for sv in solvers])
+    if len(eps0s) != n:
+        raise ValueError("one eps0 array per solver")
     e0 = [np.ascontiguousarray(np.atleast_2d(np.asarray(e, dtype=np.float64))) for e in eps0s]
+    for e, sv in zip(e0, solvers):
+        if e.ndim != 2 or e.shape[1] != sv.nv:
+            raise ValueError(f"eps0: need shape (n_L, {sv.nv}), got {e.shape}")
+    hs = (C.c_void_p * n)(*[sv._h.value for sv in solvers])
     nl = (C.c_int * n)(*[e.shape[0] for e in e0])
     ptrs = (C.c_void_p * n)(*[e.ctypes.data for e in e0])
     opts = fh_solve_opts(float(tol), int(max_iter), int(precision), int(init), int(chunk), int(path), int(cluster),
@@ -411,8 +447,7 @@ class FNO:
     __del__ = close
 
     def set_params(self, flat):
-        flat = np.ascontiguousarray(np.asarray(flat, dtype=np.float32))
-        assert flat.size == self.nparam
+        flat = _buf(flat, self.nparam, np.float32, "params")
         _check(library().fh_fno_set_params(self._h, _ptr(flat)))
 
     def get_params(self):
@@ -428,29 +463,46 @@ class FNO:
     def zero_grad(self):
         _check(library().fh_fno_zero_grad(self._h))
 
+    def _io(self, x, other, ch, what):
+        """Batch size of device input x (batch, cin, n^3) and the checked `other` (batch, ch, n^3)."""
+        if not hasattr(x, "data_ptr") or not hasattr(other, "data_ptr"):
+            raise ValueError("FNO inputs and outputs are device tensors")
+        b = int(x.shape[0])
+        _buf(x, b * self.cin * self.n ** 3, np.float32, "x")
+        _buf(other, b * ch * self.n ** 3, np.float32, what)
+        return b
+
     def forward(self, x, y):
-        _check(library().fh_fno_forward(self._h, int(x.shape[0]), _ptr(x), _ptr(y)))
+        b = self._io(x, y, self.cout, "y")
+        _check(library().fh_fno_forward(self._h, b, _ptr(x), _ptr(y)))
         return y
 
     def loss_grad(self, x, target):
+        b = self._io(x, target, self.cout, "target")
         loss = C.c_double()
-        _check(library().fh_fno_loss_grad(self._h, int(x.shape[0]), _ptr(x), _ptr(target), C.byref(loss)))
+        _check(library().fh_fno_loss_grad(self._h, b, _ptr(x), _ptr(target), C.byref(loss)))
         return loss.value
 
     def adam_step(self, lr, step, beta1=0.9, beta2=0.999, eps=1e-8):
         _check(library().fh_fno_adam_step(self._h, float(lr), float(beta1), float(beta2), float(eps), int(step)))
 
     def make_input(self, phase, phase_logE, eps0, x):
-        plE = np.ascontiguousarray(np.asarray(phase_logE, dtype=np.float64))
-        e0 = np.ascontiguousarray(np.asarray(eps0, dtype=np.float64))
+        if not hasattr(phase, "data_ptr") or not hasattr(x, "data_ptr"):
+            raise ValueError("phase and x are device tensors")
+        _buf(phase, self.n ** 3, np.uint8, "phase")
+        _buf(x, self.cin * self.n ** 3, np.float32, "x")
+        plE = np.ascontiguousarray(np.asarray(phase_logE, dtype=np.float64)).ravel()
+        e0 = _buf(eps0, 6, np.float64, "eps0")
         _check(library().fh_fno_make_input(self._h, _ptr(phase), len(plE), _ptr(plE), _ptr(e0), _ptr(x)))
         return x
 
 
 def get_strain_f32(solver, load, out):
+    out = _buf(out, solver.nv * solver.m, np.float32, "strain", writable=True)
     _check(_sig_fno().fh_get_strain_f32(solver._h, int(load), _ptr(out)))
     return out
 
 
 def set_strain_f32(solver, load, E):
+    E = _buf(E, solver.nv * solver.m, np.float32, "strain")
     _check(_sig_fno().fh_set_strain_f32(solver._h, int(load), _ptr(E)))
