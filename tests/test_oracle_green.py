@@ -81,6 +81,28 @@ def test_boxspline_closed_form_sums(rng):
     assert np.allclose(G.symbol(gen, unum, D), np.sinc(0.137) ** 2 * np.sinc(-0.411) ** 2)
 
 
+def test_three_direction_boxspline_alias_sum(rng):
+    """Non-tensor directions: for Xi = (e1, e2, e1 + e2) (the Courant hat on the
+    three-direction mesh) Poisson summation turns sum_z g(u + z)^2 into the
+    Fourier series of the hat's autocorrelation sampled on Z^2: 1/2 at 0 and
+    1/12 at the six neighbours +-e1, +-e2, +-(e1 + e2), i.e.
+    1/2 + (cos 2 pi u1 + cos 2 pi u2 + cos 2 pi (u1 + u2)) / 6.  The sum over
+    |z_i| <= 150 misses a tail below 1e-8 (largest along z1 = -z2, where the
+    terms fall like 1 / (pi^4 k^4))."""
+    xi = np.array([[1.0, 0.0, 1.0], [0.0, 1.0, 1.0]])
+    gen = G.Generator("boxspline", xi=xi, radius=4)
+    D, R = 1000, 150
+    z = np.stack(np.meshgrid(np.arange(-R, R + 1), np.arange(-R, R + 1), indexing="ij"), -1).reshape(-1, 2)
+    for _ in range(6):
+        un = rng.integers(-D // 2, D // 2, size=2)
+        g = G.symbol(gen, un[None, :] + D * z, D)
+        u = un / D
+        closed = 0.5 + (np.cos(2 * np.pi * u[0]) + np.cos(2 * np.pi * u[1]) + np.cos(2 * np.pi * u.sum())) / 6
+        assert 0 <= closed - np.sum(g * g) < 1e-8
+        _, w = G.alias_weights(gen, un, D)
+        assert np.all(w >= 0) and abs(w.sum() - 1) < 1e-14
+
+
 @pytest.mark.parametrize("d", [2, 3])
 def test_weights_orthonormalise(d, rng):
     """Lemma FI:Props (iii): after normalisation sum_z |c_{h+M^T z}|^2 = 1/m."""
