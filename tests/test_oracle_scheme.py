@@ -100,6 +100,42 @@ def test_laminate_matches_lamination_formulas(axis):
     assert np.abs(Ceff - expect).max() / np.abs(expect).max() < 1e-10
 
 
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_laminate_3d_matches_block_lamination_formula(axis):
+    """3-D laminate normal to e_axis (Dirichlet, diag(8,8,8)): the in-plane strain
+    components T and the normal traction components N (Mandel indices of nn and
+    of the two shears involving the normal) are continuous across the layers,
+    which gives, on the Mandel matrix split into these blocks,
+        C*_NN = <C_NN^-1>^-1,  C*_TN = <C_TN C_NN^-1> C*_NN,
+        C*_TT = <C_TT - C_TN C_NN^-1 C_NT> + <C_TN C_NN^-1> C*_NN <C_NN^-1 C_NT>.
+    A wrong shear index or sqrt(2) factor in the 3-D Mandel layout breaks it."""
+    M = [[8, 0, 0], [0, 8, 0], [0, 0, 8]]
+    phases = [(1.0, 0.3), (9.0, 0.2)]
+    T, C, C0, Gp, ids, Cp = _setup(M, G.Generator("dirichlet"), phases,
+                                   lambda y: W.laminate_ids(y, axis, 0.4))
+    out = scheme.solve(T, Gp, C, C0, np.eye(6), tol=1e-14, max_iter=3000)
+    Ceff = scheme.effective_stiffness(out["mean_stress"], np.eye(6))
+    shear_of = {(1, 2): 3, (0, 2): 4, (0, 1): 5}
+    N = [axis] + [k for (i, j), k in shear_of.items() if axis in (i, j)]
+    Tset = [k for k in range(6) if k not in N]
+    f = np.array([np.mean(ids == p) for p in range(len(phases))])
+    avg = lambda fn: sum(f[p] * fn(Cp[p]) for p in range(len(phases)))
+    inv = np.linalg.inv
+    blk = lambda A, R, S: A[np.ix_(R, S)]
+    CNN = inv(avg(lambda A: inv(blk(A, N, N))))
+    TNinv = avg(lambda A: blk(A, Tset, N) @ inv(blk(A, N, N)))
+    NinvNT = avg(lambda A: inv(blk(A, N, N)) @ blk(A, N, Tset))
+    CTT = avg(lambda A: blk(A, Tset, Tset) - blk(A, Tset, N) @ inv(blk(A, N, N)) @ blk(A, N, Tset)) \
+        + TNinv @ CNN @ NinvNT
+    expect = np.zeros((6, 6))
+    expect[np.ix_(N, N)] = CNN
+    expect[np.ix_(Tset, N)] = TNinv @ CNN
+    expect[np.ix_(N, Tset)] = (TNinv @ CNN).T
+    expect[np.ix_(Tset, Tset)] = CTT
+    assert 0.2 < f[1] < 0.6
+    assert np.abs(Ceff - expect).max() / np.abs(expect).max() < 1e-10
+
+
 @pytest.mark.parametrize("gen", GENS2, ids=lambda g: g.kind + str(g.alpha))
 def test_ceff_symmetric(gen):
     M = [[16, 0], [0, 16]] if gen.kind == "dirichlet" else [[15, 4], [0, 17]]
