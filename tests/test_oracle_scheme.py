@@ -249,6 +249,37 @@ def test_ceff_within_hashin_shtrikman_bounds(count, rmin, rmax, seed, E2):
     assert K_lo < K_e < K_hi
 
 
+@pytest.mark.parametrize("seed,count,E2", [(5, 30, 10.0), (6, 40, 5.0)])
+def test_ceff_3d_within_hashin_shtrikman_bounds(seed, count, E2):
+    """Random spheres on diag(16,16,16): the isotropic projection of the 6 x 6
+    Mandel C_eff (bulk K = sum of the normal block / 9, shear
+    mu = (trace - 3 K) / 10) lies between the 3-D Hashin-Shtrikman bounds of
+    the sampled volume fractions (soft check, as in 2-D)."""
+    rng = np.random.default_rng(seed)
+    c, r = W.random_inclusions(rng, 3, count, 0.08, 0.14)
+    M = [[16, 0, 0], [0, 16, 0], [0, 0, 16]]
+    T, C, C0, Gp, ids, Cp = _setup(M, G.Generator("dirichlet"), [(1.0, 0.3), (E2, 0.3)],
+                                   lambda y: W.phase_ids(y, c, r))
+    out = scheme.solve(T, Gp, C, C0, np.eye(6), tol=1e-9, max_iter=5000)
+    Ce = scheme.effective_stiffness(out["mean_stress"], np.eye(6))
+    f2 = ids.mean()
+    f1 = 1.0 - f2
+    (l1, m1), (l2, m2) = material.lame(1.0, 0.3), material.lame(E2, 0.3)
+
+    def hs(K_a, mu_a, K_b, mu_b, f_a, f_b):
+        K = K_a + f_b / (1.0 / (K_b - K_a) + 3.0 * f_a / (3.0 * K_a + 4.0 * mu_a))
+        mu = mu_a + f_b / (1.0 / (mu_b - mu_a) + 6.0 * f_a * (K_a + 2.0 * mu_a) / (5.0 * mu_a * (3.0 * K_a + 4.0 * mu_a)))
+        return K, mu
+
+    K1, K2 = l1 + 2 * m1 / 3, l2 + 2 * m2 / 3
+    K_lo, mu_lo = hs(K1, m1, K2, m2, f1, f2)
+    K_hi, mu_hi = hs(K2, m2, K1, m1, f2, f1)
+    K_e = Ce[:3, :3].sum() / 9
+    mu_e = (np.trace(Ce) - 3 * K_e) / 10
+    assert 0.1 < f2 < 0.4
+    assert K_lo < K_e < K_hi and mu_lo < mu_e < mu_hi
+
+
 @pytest.mark.parametrize("gen", GENS2[:2] + GENS2[3:], ids=lambda g: g.kind)
 def test_converged_iterate_solves_discrete_equation(gen):
     """At the fixed point, E + Gamma^p (C - C0)(E + eps0) = 0 (Eq. (pde_coefficients)),
