@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 from oracle import lattice
+from test_oracle_lattice import determinantal_divisors
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -124,6 +125,7 @@ def test_random_integer_matrices_match_oracle(fh):
         G = set(map(tuple, lattice.generating_set(M).tolist()))
         assert all(tuple(h) in G for h in H)
         dims = p.dims
+        assert dims == [s for s in determinantal_divisors(M) if s > 1]
         assert len(H) == int(np.prod(dims[:-1])) * (dims[-1] // 2 + 1)
         half_shape = dims[:-1] + [dims[-1] // 2 + 1]
         for _ in range(50):

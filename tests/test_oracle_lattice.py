@@ -94,6 +94,38 @@ def test_smith_form(M):
     assert int(np.prod(dims)) == abs(lattice.det_int(M))
 
 
+def determinantal_divisors(M):
+    """Smith invariants from their definition: d_1 ... d_k = gcd of all k x k minors."""
+    import itertools
+    from math import gcd
+    d = len(M)
+    out, prev = [], 1
+    for k in range(1, d + 1):
+        g = 0
+        for rows in itertools.combinations(range(d), k):
+            for cols in itertools.combinations(range(d), k):
+                g = gcd(g, abs(lattice.det_int([[M[i][j] for j in cols] for i in rows])))
+        out.append(g // prev)
+        prev = g
+    return out
+
+
+def test_smith_form_equals_determinantal_divisors(rng):
+    """Random integer matrices: the diagonal of the oracle's Smith form is the
+    sequence of determinantal divisor quotients, and U M V = diag."""
+    n = 0
+    while n < 200:
+        d = int(rng.integers(2, 4))
+        M = rng.integers(-15, 16, size=(d, d)).tolist()
+        if lattice.det_int(M) == 0:
+            continue
+        n += 1
+        U, dims, V = lattice.smith(M)
+        assert dims == determinantal_divisors(M)
+        A = np.array(U, dtype=object) @ np.array(M, dtype=object) @ np.array(V, dtype=object)
+        assert np.all(A == np.diag(dims))
+
+
 def test_paper_snf_shapes():
     assert lattice.smith([[128, 32], [0, 128]])[1] == [32, 512]
     assert lattice.smith([[64, 64], [-64, 64]])[1] == [64, 128]
