@@ -138,6 +138,25 @@ def test_random_integer_matrices_match_oracle(fh):
             assert lhs == rhs
 
 
+@pytest.mark.parametrize("M", [[[1, 0], [0, 1]], [[1, 0, 0], [0, 1, 0], [0, 0, 1]], [[0, 1], [1, 0]],
+                               [[2, 1], [1, 1]], [[1, 0], [0, 7]], [[-3, 0, 0], [0, 1, 0], [0, 0, -5]]])
+def test_degenerate_patterns(fh, M):
+    """Unimodular M (a single point, det +-1) and patterns with trivial Smith
+    factors or negative determinants: one storage axis (of length 1 for m = 1)
+    and the oracle's points and frequencies."""
+    p = fh.Pattern(M)
+    D = abs(lattice.det_int(M))
+    assert p.m == D and int(np.prod(p.dims)) == D and len(p.dims) >= 1
+    ref, _ = lattice.pattern(M)
+    assert sorted(map(tuple, p.numerators().tolist())) == sorted(map(tuple, ref.tolist()))
+    H = p.half_freqs()
+    assert len(H) == int(np.prod(p.dims[:-1])) * (p.dims[-1] // 2 + 1)
+    G = set(map(tuple, lattice.generating_set(M).tolist()))
+    assert all(tuple(h) in G for h in H)
+    if D == 1:
+        assert p.dims == [1] and np.all(p.points() == 0) and np.all(H == 0)
+
+
 def test_error_codes_without_gpu(fh):
     with pytest.raises(fh.FhError) as e:
         fh.Pattern([[2, 4], [1, 2]])
