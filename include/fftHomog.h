@@ -178,7 +178,8 @@ fh_status fh_pattern_half_freqs(const fh_pattern* p, int64_t* h, int64_t* nh);
  * NULL = legacy default stream).  Allocates device work memory for up to
  * nload_max load cases (1..FH_MAX_LOADS).  The pattern may be destroyed
  * afterwards.  Errors: FH_ERR_ARG, FH_ERR_UNSUPPORTED (an SNF axis longer
- * than 4096 or with a prime factor > 13), FH_ERR_CUDA. */
+ * than 4096 or with a prime factor > 13, or |det M| = 1: a single point has
+ * no fluctuation, E = 0 and C_eff = C there), FH_ERR_CUDA. */
 fh_status fh_solver_create(const fh_pattern* p, const fh_generator* gen,
                            int nload_max, void* cuda_stream, fh_solver** out);
 void fh_solver_destroy(fh_solver* s);

@@ -811,6 +811,10 @@ fh_status fh_solver_create(const fh_pattern* p, const fh_generator* gen, int nlo
   if (nload_max < 1 || nload_max > FH_MAX_LOADS) { fh::set_error("nload_max out of range"); return FH_ERR_ARG; }
   if (gen->kind < FH_GEN_DIRICHLET || gen->kind > FH_GEN_BOXSPLINE) { fh::set_error("unknown generator"); return FH_ERR_ARG; }
   const int d = p->p.d;
+  if (p->p.D < 2) {
+    fh::set_error("single-point pattern (|det M| = 1): E = 0 and C_eff = C(0), nothing to iterate");
+    return FH_ERR_UNSUPPORTED;
+  }
   if (gen->kind == FH_GEN_DLVP)
     for (int i = 0; i < d; ++i)
       if (!(gen->alpha[i] >= 0.0 && gen->alpha[i] <= 0.5)) { fh::set_error("dlVP alpha outside [0, 1/2]"); return FH_ERR_ARG; }

@@ -168,6 +168,10 @@ def test_error_codes_without_gpu(fh):
     with pytest.raises(fh.FhError) as e:
         fh.Solver(p, fh.generator("dirichlet"), 3)
     assert e.value.status == -8          # FH_ERR_UNSUPPORTED
+    for M in ([[1, 0], [0, 1]], [[2, 1], [1, 1]]):   # |det M| = 1: one point, nothing to solve
+        with pytest.raises(fh.FhError) as e:
+            fh.Solver(fh.Pattern(M), fh.generator("dirichlet"), 3)
+        assert e.value.status == -8
     p = fh.Pattern([[8, 0], [0, 8]])
     with pytest.raises(fh.FhError) as e:
         fh.Solver(p, fh.generator("dlvp", alpha=[0.7, 0.1]), 3)
