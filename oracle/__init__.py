@@ -22,8 +22,8 @@ periodic anisotropic translation invariant spaces" (arXiv 1701.04685):
 * ``scheme``     -- fixed-point iteration on Eq. (pde_coefficients), Cauchy
                     residual (Sec. 4) and the effective stiffness (Sec. 3.1).
 
-* ``krylov``     -- conjugate gradients (Dirichlet, Galerkin form) and GMRES
-                    on the same discrete equation as ``scheme`` (Krylov
+* ``krylov``     -- conjugate gradients (Dirichlet, Galerkin form), GMRES and
+                    BiCGStab on the same discrete equation as ``scheme`` (Krylov
                     solvers that the paper cites; not its iteration).
 * ``fno``        -- forward pass and loss of the learned start (a Fourier
                     neural operator; not part of the paper's method); the GPU

@@ -5,7 +5,7 @@ Test infrastructure (see ``oracle/__init__.py``): not used by the product.
 
 The paper solves Eq. (pde_coefficients) with the fixed point of Sec. 4 and
 names Krylov methods, in its introduction, as faster solvers of the same
-discretised Lippmann-Schwinger equation.  Both functions here return the unique
+discretised Lippmann-Schwinger equation.  The functions here return the unique
 solution E of the linear system that the fixed point converges to, so they
 are pinned against ``scheme.solve``:
 
@@ -24,6 +24,14 @@ are pinned against ``scheme.solve``:
   by GMRES (Saad & Schultz, 1986) without restarts: an Arnoldi basis by
   modified Gram-Schmidt, the coefficients from the small least-squares problem
   min |beta e_1 - H y|, stopping when its residual is <= tol |b|.
+* ``bicgstab`` -- the same system as ``gmres`` with BiCGStab (van der Vorst,
+  1992), which keeps a fixed number of fields instead of a growing basis:
+      r_0 = b - A E_0, rhat = r_0, rho = alpha = omega = 1, v = p = 0;
+      rho' = rhat . r,  beta = (rho' / rho)(alpha / omega),
+      p = r + beta (p - omega v),  v = A p,  alpha = rho' / (rhat . v),
+      s = r - alpha v,  t = A s,  omega = (t . s) / (t . t),
+      E += alpha p + omega s,  r = s - omega t;
+  stopping when |r| <= tol |b|.  Two operator applications per iteration.
 
 Fields are real (m, n_v) Mandel arrays in the transform's point order; the dot
 product is the Euclidean one over all points and components (Sec. 3.1's
@@ -109,4 +117,41 @@ def gmres(transform, Gp, C, C0m, eps0, tol=1e-10, max_iter=500):
             break
         V.append(w / H[k, k - 1])
     E = sum(y[i] * V[i] for i in range(len(y)))
+    return {"E": E, "iters": k, "resid": np.array(hist)}
+
+
+def bicgstab(transform, Gp, C, C0m, eps0, tol=1e-10, max_iter=1000):
+    """BiCGStab on (I + Gamma^p (C - C0)) E = -Gamma^p (C - C0) eps0, one load
+    case.  Returns {"E", "iters", "resid"} with resid[k] = |r_k| / |b|."""
+    m = transform.m
+    e0 = np.asarray(eps0, dtype=float)[None, :]
+    dC = C - C0m[None, :, :]
+    A = lambda x: x + apply_multiplier(transform, Gp, _stress(dC, x))
+    b = -apply_multiplier(transform, Gp, _stress(dC, np.broadcast_to(e0, (m, e0.shape[1])).copy()))
+    bn = np.sqrt(float(np.sum(b * b)))
+    E = np.zeros_like(b)
+    if bn == 0.0:
+        return {"E": E, "iters": 0, "resid": np.array([0.0])}
+    r = b.copy()
+    rhat = r.copy()
+    rho = alpha = omega = 1.0
+    v = np.zeros_like(b)
+    p = np.zeros_like(b)
+    hist = [1.0]
+    k = 0
+    for k in range(1, max_iter + 1):
+        rho_new = float(np.sum(rhat * r))
+        beta = (rho_new / rho) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        v = A(p)
+        alpha = rho_new / float(np.sum(rhat * v))
+        s = r - alpha * v
+        t = A(s)
+        omega = float(np.sum(t * s)) / float(np.sum(t * t))
+        E += alpha * p + omega * s
+        r = s - omega * t
+        rho = rho_new
+        hist.append(np.sqrt(float(np.sum(r * r))) / bn)
+        if hist[-1] <= tol:
+            break
     return {"E": E, "iters": k, "resid": np.array(hist)}

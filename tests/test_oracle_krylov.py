@@ -53,6 +53,18 @@ def test_gmres_reaches_the_fixed_points_solution(gen):
     assert np.abs(out["E"] - star).max() / np.abs(star).max() < 1e-10
 
 
+@pytest.mark.parametrize("gen", [G.Generator("dirichlet"), G.Generator("dlvp", alpha=[0.25, 0.25]),
+                                 G.Generator("boxspline", xi=G.tensor_boxspline_xi(2, 2), radius=3)],
+                         ids=lambda g: g.kind)
+def test_bicgstab_reaches_the_fixed_points_solution(gen):
+    """BiCGStab reaches the fixed point's solution for every generator."""
+    T, C, C0, Gp = _problem(M_ODD, gen, 20.0)
+    star = _fixed_point(T, C, C0, Gp)
+    out = krylov.bicgstab(T, Gp, C, C0, E0, tol=1e-13, max_iter=500)
+    assert out["resid"][-1] <= 1e-13
+    assert np.abs(out["E"] - star).max() / np.abs(star).max() < 1e-10
+
+
 def test_cg_error_energy_decreases_monotonically():
     """CG minimises the energy norm sqrt(e . C e) of the error over the growing
     Krylov space, so it never increases (a wrong step length or direction
