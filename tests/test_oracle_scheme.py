@@ -300,6 +300,42 @@ def test_converged_iterate_solves_discrete_equation(gen):
         assert np.abs(res).max() < 1e-11
 
 
+def _form_b_limit(T, Gp, C, e0):
+    """Dense solve of form B's limit: E = Gamma^p y with Gamma^p C (E + eps0) = 0
+    (the iterates stay in range(Gamma^p), where Gamma^p C Gamma^p is definite)."""
+    m = T.m
+    G_ = np.stack([scheme.apply_operator(T, Gp, v.reshape(m, 3)).real.ravel() for v in np.eye(3 * m)], axis=1)
+    Cb = np.zeros((3 * m, 3 * m))
+    for i in range(m):
+        Cb[3 * i:3 * i + 3, 3 * i:3 * i + 3] = C[i]
+    y = np.linalg.lstsq(G_ @ Cb @ G_, -G_ @ Cb @ np.tile(e0, m), rcond=None)[0]
+    return (G_ @ y).reshape(m, 3)
+
+
+@pytest.mark.parametrize("gen", GENS2[:2] + GENS2[3:], ids=lambda g: g.kind)
+def test_form_b_iterates_approach_the_variational_solution(gen):
+    """Form B (E <- E - Gamma^p C (E + eps0)) tends to the solution of
+    Gamma^p C (E + eps0) = 0 in range(Gamma^p) (the variational discretisation,
+    Thm. ls_discretization): the dense solve satisfies that equation, the
+    iterates' distance to it decreases, and its C_eff equals form A's exactly
+    when Gamma^p C0 is a projection (Dirichlet on an odd determinant)."""
+    M = [[5, 2], [0, 3]]                                       # det 15: no boundary frequencies
+    T, C, C0, Gp, _, _ = _setup(M, gen, [(1.0, 0.3), (8.0, 0.3)], _disk_phase(0.3, (0.0, 0.0)))
+    e0 = np.array([1.0, 0.0, 0.0])
+    Estar = _form_b_limit(T, Gp, C, e0)
+    sig = np.einsum("mab,mb->ma", C, Estar + e0)
+    assert np.abs(scheme.apply_operator(T, Gp, sig).real).max() < 1e-11
+    dist = [np.abs(scheme.solve(T, Gp, C, C0, e0[None], tol=0.0, max_iter=n, form="B")["E"][0] - Estar).max()
+            for n in (25, 50, 100, 200)]
+    assert all(b < a for a, b in zip(dist, dist[1:]))
+    ceB = np.mean(sig, axis=0)
+    ceA = scheme.solve(T, Gp, C, C0, e0[None], tol=1e-14, max_iter=20000)["mean_stress"][0]
+    if gen.kind == "dirichlet":
+        assert np.abs(ceB - ceA).max() < 1e-10
+    else:
+        assert np.abs(ceB - ceA).max() > 1e-4
+
+
 def test_literal_dirichlet_complex_iterate():
     """Literal half-open Dirichlet symbol: real iterate on odd det, complex on even det."""
     ph = _disk_phase(0.3)
