@@ -124,7 +124,10 @@ typedef struct {
                       ls_discretization, whose fixed point solves
                       C0 Gamma^p C (E + eps0) = 0: E <- E - Gamma^p C (E + eps0).
                       The two coincide for the Dirichlet kernel only (Remark
-                      constants).                                            */
+                      constants).  For dlVP and box splines Gamma^p(h) is
+                      invertible at most frequencies, so form 1's limit has
+                      zero stress there and its iterates contract slowly
+                      (thousands of iterations at contrast 8).               */
   int tune;        /* 1 with path = cluster = 0 and init = 0: on the first such
                       solve of each bulk precision, time every eligible launch
                       configuration (passes; clusters of 8 and 16) for 24
