@@ -127,7 +127,9 @@ typedef struct {
                       constants).  For dlVP and box splines Gamma^p(h) is
                       invertible at most frequencies, so form 1's limit has
                       zero stress there and its iterates contract slowly
-                      (thousands of iterations at contrast 8).               */
+                      (thousands of iterations at contrast 8); E is kept in
+                      range(Gamma^p), not restricted to the compatible fields
+                      of V^f_M that the theorem assumes.                     */
   int tune;        /* 1 with path = cluster = 0 and init = 0: on the first such
                       solve of each bulk precision, time every eligible launch
                       configuration (passes; clusters of 8 and 16) for 24
