@@ -336,6 +336,26 @@ def test_form_b_iterates_approach_the_variational_solution(gen):
         assert np.abs(ceB - ceA).max() > 1e-4
 
 
+def test_literal_and_modified_dirichlet_differ_only_on_boundary_frequencies():
+    """Reading 4: the two Dirichlet symbols differ only where a coordinate of
+    M^-T h is -1/2, which needs an even determinant.  Odd det: identical
+    iterates.  Even det: the iterates differ, and the real part of the literal
+    C_eff stays close to the modified one (the boundary set is a thin shell)."""
+    ph = _disk_phase(0.3)
+    for M, same in [([[7, 0], [0, 9]], True), ([[8, 0], [0, 8]], False)]:
+        outs = []
+        for kind in ("dirichlet", "dirichlet_literal"):
+            T, C, C0, Gp, _, _ = _setup(M, G.Generator(kind), [(1.0, 0.3), (10.0, 0.3)], ph, scheme.BruteTransform)
+            outs.append(scheme.solve(T, Gp, C, C0, np.eye(3), tol=0.0, max_iter=60, complex_iterate=True))
+        dE = np.abs(outs[0]["E"] - outs[1]["E"]).max()
+        ce = [scheme.effective_stiffness(o["mean_stress"].real, np.eye(3)) for o in outs]
+        if same:
+            assert dE < 1e-13
+        else:
+            assert dE > 1e-6
+            assert np.abs(ce[0] - ce[1]).max() / np.abs(ce[0]).max() < 0.01       # 0.19 % measured on 8 x 8
+
+
 def test_literal_dirichlet_complex_iterate():
     """Literal half-open Dirichlet symbol: real iterate on odd det, complex on even det."""
     ph = _disk_phase(0.3)
