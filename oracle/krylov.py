@@ -58,7 +58,12 @@ def cg(transform, P_table, C, eps0, tol=1e-10, max_iter=1000):
     """Conjugate gradients on P C (E + eps0) = 0, E in range(P), one load case.
 
     P_table: Gamma^p of the Dirichlet kernel built with C0 = I; C: (m, n_v, n_v);
-    eps0: (n_v,).  Returns {"E", "iters", "resid"} with resid[k] = |r_k| / |r_0|."""
+    eps0: (n_v,).  Returns {"E", "iters", "resid"} with resid[k] = |r_k| / |r_0|.
+    The table must be a projection at every frequency (Dirichlet kernel, odd
+    determinant: on even determinants the boundary frequencies average two
+    aliases and CG does not reach the solution); otherwise ValueError."""
+    if np.abs(np.einsum("mab,mbc->mac", P_table, P_table) - P_table).max() > 1e-12:
+        raise ValueError("cg needs Gamma^p (C0 = I) to be a projection: Dirichlet kernel, odd determinant")
     e0 = np.asarray(eps0, dtype=float)[None, :]
     K = lambda x: apply_multiplier(transform, P_table, _stress(C, x))
     r = -K(np.broadcast_to(e0, (transform.m, e0.shape[1])).copy())

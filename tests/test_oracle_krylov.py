@@ -65,6 +65,21 @@ def test_bicgstab_reaches_the_fixed_points_solution(gen):
     assert np.abs(out["E"] - star).max() / np.abs(star).max() < 1e-10
 
 
+def test_cg_refuses_tables_that_are_not_projections():
+    """On an even determinant the Dirichlet table averages two aliases at the
+    boundary frequencies, Gamma^p (C0 = I) is no projection, and CG is refused;
+    BiCGStab still reaches the fixed point's solution there."""
+    gen = G.Generator("dirichlet")
+    M = [[16, 0], [0, 16]]
+    T, C, C0, Gp = _problem(M, gen, 100.0)
+    P = green.gamma_p_table(M, gen, np.eye(3), T.freqs)
+    with pytest.raises(ValueError):
+        krylov.cg(T, P, C, E0)
+    star = _fixed_point(T, C, C0, Gp)
+    out = krylov.bicgstab(T, Gp, C, C0, E0, tol=1e-12, max_iter=500)
+    assert np.abs(out["E"] - star).max() / np.abs(star).max() < 1e-9
+
+
 def test_cg_error_energy_decreases_monotonically():
     """CG minimises the energy norm sqrt(e . C e) of the error over the growing
     Krylov space, so it never increases (a wrong step length or direction
