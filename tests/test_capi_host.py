@@ -168,6 +168,13 @@ def test_error_codes_without_gpu(fh):
     with pytest.raises(fh.FhError) as e:
         fh.Solver(p, fh.generator("dirichlet"), 3)
     assert e.value.status == -8          # FH_ERR_UNSUPPORTED
+    with pytest.raises(fh.FhError) as e:
+        fh.Pattern([[1 << 16, 0], [0, 1 << 16]])          # |det M| = 2^32
+    assert e.value.status == -3
+    for M in ([[8192, 0], [0, 1]], [[64, 0], [0, 8192]]):   # a Smith axis longer than 4096
+        with pytest.raises(fh.FhError) as e:
+            fh.Solver(fh.Pattern(M), fh.generator("dirichlet"), 3)
+        assert e.value.status == -8
     for M in ([[1, 0], [0, 1]], [[2, 1], [1, 1]]):   # |det M| = 1: one point, nothing to solve
         with pytest.raises(fh.FhError) as e:
             fh.Solver(fh.Pattern(M), fh.generator("dirichlet"), 3)
