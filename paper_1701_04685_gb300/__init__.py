@@ -210,6 +210,8 @@ class Pattern:
 
     def __init__(self, M):
         M = np.ascontiguousarray(np.asarray(M, dtype=np.int64))
+        if M.ndim != 2 or M.shape[0] != M.shape[1] or M.shape[0] not in (2, 3):
+            raise ValueError(f"M: need a square 2 x 2 or 3 x 3 integer matrix, got shape {M.shape}")
         self.d = M.shape[0]
         self.M = M
         h = C.c_void_p()

@@ -89,3 +89,9 @@ def test_valid_buffers_pass_unchanged():
     assert fh._buf(a, 192, np.float64, "a", writable=True) is a
     b = fh._buf([[1, 2], [3, 4]], 4, np.float64, "b")
     assert b.dtype == np.float64 and b.flags["C_CONTIGUOUS"]
+
+
+def test_pattern_matrix_shape():
+    for M in ([[1, 2, 3], [4, 5, 6]], [[1, 0], [0, 1], [1, 1]], [4], [[[1]]], np.eye(4, dtype=int)):
+        with pytest.raises(ValueError):
+            fh.Pattern(M)
