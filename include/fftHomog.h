@@ -296,12 +296,13 @@ fh_status fh_profile_passes(fh_solver* s, int nload, int precision, int reps, do
 
 /* Mean stress <C:(E+eps0)> per load case, computed without allocating any
  * device memory.  The paper has no counterpart: this is an interface for
- * callers that cannot call cudaMalloc when they need the result -- code running
- * while a CUDA graph is being captured, real-time loops where an allocation
- * could block or fail, and applications whose device memory is owned entirely
- * by their own allocator.  All scratch (per-block partial sums, a block counter,
- * the result) lives in one fixed array of 6272 doubles (49 KB) inside the
- * library, held by every GPU that loads the library until the process exits.
+ * callers that cannot call cudaMalloc when they need the result -- real-time
+ * loops where an allocation could block or fail, and applications (a larger
+ * simulation embedding this solver, say) whose device memory is owned entirely
+ * by their own allocator with a fixed budget.  All scratch (per-block partial
+ * sums, a block counter, an error word, the result) lives in one fixed array
+ * of 6272 doubles (49 KB) inside the library, held by every GPU that loads the
+ * library until the process exits.
  *
  *   E[nload * n_v * m]   device, FP64, layout of fh_get_strain per load
  *   phase[m]             device, uint8 phase ids < nphase
@@ -310,10 +311,13 @@ fh_status fh_profile_passes(fh_solver* s, int nload, int precision, int reps, do
  *   mean_stress[nload*n_v] host or device output
  *   cuda_stream          stream to run on (NULL = legacy default); the call
  *                        synchronises it before returning.
- * n_v = 3 (d = 2) or 6 (d = 3).  nload above 16 is rejected with FH_ERR_ARG.
- * The first call on a device looks up the array's device address; make that
- * first call outside any stream capture.  Calls that overlap on the GPU share
- * the array and race: serialise them. */
+ * n_v = 3 (d = 2) or 6 (d = 3).  nload above 16 is rejected with FH_ERR_ARG
+ * before anything runs.  A phase id >= nphase is detected on the device (the
+ * point is skipped, never used as an index) and the call returns FH_ERR_ARG;
+ * mean_stress is then not valid.  The first call on a device looks up and
+ * caches the array's device address: make that first call before any stream
+ * capture, and do not call again after cudaDeviceReset on that device.  Calls
+ * that overlap on the GPU share the array and race: serialise them. */
 fh_status fh_mean_stress_noalloc(int d, long long m, int nload, const double* E, const uint8_t* phase,
                                  int nphase, const double* Cp, const double* eps0, double* mean_stress,
                                  void* cuda_stream);

@@ -18,7 +18,7 @@ LIB = os.path.join(OUT_DIR, "libffthomog.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["solver.cu", "lattice.cpp", "noalloc.cu", "fno.cu"]
-HEADERS = ["internal.hpp", "kernels.cuh", "fft.cuh", "cluster.cuh", "warprow.cuh"]
+HEADERS = ["internal.hpp", "kernels.cuh", "fft.cuh", "cluster.cuh", "warprow.cuh", "linewarp.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -33,7 +33,9 @@ def _stale():
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(INCLUDE, "fftHomog.h"), __file__]
+    # every file of csrc/ counts, so that a header added later cannot be missed
+    deps = [os.path.join(CSRC, f) for f in sorted(set(SOURCES + HEADERS) | set(os.listdir(CSRC)))]
+    deps += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)] + [__file__]
     return any(os.path.getmtime(p) > t for p in deps)
 
 

@@ -44,6 +44,7 @@ struct LoadState {
   double r_best;    // smallest residual so far
   int since_best;   // iterations since r_best last improved by 1%
   int pad_;
+  double n_first;   // ||E_1 + eps0||^2 of the first iteration: the divergence test's scale
 };
 
 // internal status: the residual stopped improving (FP32 rounding floor); the
@@ -217,7 +218,7 @@ __device__ __forceinline__ void update_state(LoadState& s, double d2, double n2,
                                              int stall_window) {
   const double r = (n2 > 0.0) ? sqrt(d2 / n2) : sqrt(d2);
   s.iter += 1;
-  if (s.iter == 1) s.r_first = r;
+  if (s.iter == 1) { s.r_first = r; s.n_first = n2; }
   s.inc = (s.iter > 1 && r > s.r) ? s.inc + 1 : 0;
   s.r = r;
   if (s.since_best == 0 && s.r_best == 0.0) s.r_best = r;  // first step of this phase
@@ -225,7 +226,11 @@ __device__ __forceinline__ void update_state(LoadState& s, double d2, double n2,
   else s.since_best += 1;
   if (!isfinite(r)) { s.status = FH_NONFINITE; s.done = 1; }
   else if (r <= tol) { s.status = FH_OK; s.done = 1; }
-  else if (s.inc >= 100 || (s.iter > 10 && r > 1e6 * s.r_first && r > 1.0)) { s.status = FH_DIVERGED; s.done = 1; }
+  // diverged: the residual kept growing, or the iterate itself grew by a factor
+  // 1e6 in norm (a geometric divergence keeps r_n roughly constant, so the
+  // residual alone does not show it)
+  else if (s.inc >= 100 || (s.iter > 10 && r > 1e6 * s.r_first && r > 1.0) ||
+           (s.iter > 10 && s.n_first > 0.0 && n2 > 1e12 * s.n_first)) { s.status = FH_DIVERGED; s.done = 1; }
   else if (stall_window > 0 && s.since_best >= stall_window) { s.status = kStatusStalled; s.done = 1; }
   else if (s.iter >= max_iter) { s.status = FH_NOT_CONVERGED; s.done = 1; }
 }
@@ -623,6 +628,11 @@ struct GreenParams {
   double xi[3 * 16];
   int radius;
   double C4[81];  // C0_ijkl, index ((i*3 + j)*3 + k)*3 + l
+  // closed-form path (green_table_iso): C0 isotropic with Lame constants
+  // lam0, mu0, and a symbol that is a product of per-axis factors; for a box
+  // spline whose directions are all +-e_i, xcount[i] is how often e_i occurs
+  double lam0, mu0;
+  int xcount[3];
 };
 
 __device__ __forceinline__ long long floordiv_ll(long long a, long long b) {
@@ -667,6 +677,31 @@ __device__ void mandel_pair(int d, int a, int& i, int& j) {
   } else {
     const int I[6] = {0, 1, 2, 1, 0, 0}, J[6] = {0, 1, 2, 2, 2, 1};
     i = I[a]; j = J[a];
+  }
+}
+
+// storage frequency f -> h = V^-T l, reduced into G(M^T), and the numerators
+// u = D M^-T h of the reduced frequency (|u_i| <= D/2)
+__device__ __forceinline__ void reduce_frequency(const GreenParams& P, long long f, long long* h, long long* u) {
+  const int d = P.d;
+  long long l[3] = {0, 0, 0};
+  long long rem = f;
+  l[P.nd - 1] = rem % P.H;
+  rem /= P.H;
+  for (int k = P.nd - 2; k >= 0; --k) { l[k] = rem % P.dims[k]; rem /= P.dims[k]; }
+  for (int i = 0; i < 3; ++i) h[i] = u[i] = 0;
+  for (int i = 0; i < d; ++i)
+    for (int k = 0; k < P.nd; ++k) h[i] += l[k] * P.Fmap[k][i];
+  for (int i = 0; i < d; ++i) {
+    long long s = 0;
+    for (int c = 0; c < d; ++c) s += P.adjT[i][c] * h[c];
+    u[i] = P.sign * s;
+  }
+  long long z0[3];
+  for (int i = 0; i < d; ++i) z0[i] = floordiv_ll(2 * u[i] + P.D, 2 * P.D);
+  for (int i = 0; i < d; ++i) {
+    for (int c = 0; c < d; ++c) h[i] -= P.M[c][i] * z0[c];
+    u[i] -= P.D * z0[i];
   }
 }
 
@@ -784,6 +819,197 @@ __global__ void green_table(GreenParams P, double* __restrict__ G64, float* __re
     const double v = acc[t] / wsum;
     G64[(size_t)t * P.nhalf + f] = v;
     G32[(size_t)t * P.nhalf + f] = (float)v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gamma^p table, closed form for an isotropic C0 and a separable symbol.
+//
+// For isotropic C0 (Lame constants lam0, mu0) Gamma^0 has the closed form of
+// Moulinec & Suquet (1998); with n = k/|k|,
+//   Gamma^0_ijpq(k) = (d_ip n_j n_q + d_iq n_j n_p + d_jp n_i n_q + d_jq n_i n_p) / (4 mu0)
+//                     - (lam0 + mu0) / (mu0 (lam0 + 2 mu0)) n_i n_j n_p n_q,
+// so the alias sum of Def. gamma_tilde_fourier, Gamma^p_h = sum_z w_z Gamma^0(h + M^T z),
+// needs only the fourth moment B_ijpq = sum_z w_z n_i n_j n_p n_q (15 numbers in
+// 3-D, 5 in 2-D); the second moment follows from it, sum_z w_z n_i n_j = sum_p B_ijpp.
+// When the symbol is a product of per-axis factors g(u) = prod_i g_i(u_i)
+// (Dirichlet, dlVP, box splines whose directions are unit vectors) and the
+// alias set is the product of per-axis sets |u_i + z_i| <= R + 1/2, the
+// orthonormalised weights (Lemma FI:Props (iii)) factor too:
+//   w_z = prod_i g_i(u_i + z_i)^2 / sum_{z_i'} g_i(u_i + z_i')^2,
+// so they cost a few symbol evaluations per axis instead of one per alias, and
+// aliases of zero weight are skipped.  One thread per stored frequency, aliases
+// in a fixed order (deterministic).
+// ---------------------------------------------------------------------------
+constexpr int kMaxAxisAliases = 34;  // 2R + 2 per axis, R <= 16
+
+// per-axis factor g_i at u_i = un / D
+__device__ __forceinline__ double axis_symbol(const GreenParams& P, int i, long long un) {
+  if (P.kind == FH_GEN_BOXSPLINE) {
+    const int c = P.xcount[i];
+    if (c == 0) return 1.0;
+    double f;
+    if (un == 0) f = 1.0;
+    else if (un % P.D == 0) f = 0.0;  // sinc vanishes at the nonzero integers
+    else {
+      const double v = (double)un / (double)P.D;
+      f = sinpi(v) / (3.14159265358979323846 * v);
+    }
+    double g = 1.0;
+    for (int e = 0; e < c; ++e) g *= f;
+    return g;
+  }
+  const long long two = un < 0 ? -2 * un : 2 * un;
+  const double a = (P.kind == FH_GEN_DLVP) ? P.alpha[i] : 0.0;
+  if (a == 0.0) return two < P.D ? 1.0 : (two == P.D ? 0.5 : 0.0);
+  const double u = fabs((double)un / (double)P.D);
+  return fmin(1.0, fmax(0.0, (0.5 + a - u) / (2.0 * a)));
+}
+
+// index of the fourth moment with exponents (e0, e1, e2) of n_0, n_1, n_2 in
+// the accumulation order of green_table_iso<3>
+__device__ __forceinline__ int moment_index3(int e1, int e2) {
+  // rows e1 = 0..4, columns e2 = 0..4 (e0 = 4 - e1 - e2)
+  const signed char T[5][5] = {{0, 2, 5, 12, 14}, {1, 4, 8, 13, -1}, {3, 7, 11, -1, -1},
+                               {6, 10, -1, -1, -1}, {9, -1, -1, -1, -1}};
+  return T[e1][e2];
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(128) green_table_iso(GreenParams P, double* __restrict__ G64,
+                                                       float* __restrict__ G32, int* err) {
+  const long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (f >= P.nhalf) return;
+  long long h[3], u[3];
+  reduce_frequency(P, f, h, u);
+  const int R = (P.kind == FH_GEN_BOXSPLINE) ? P.radius : 1;
+  int nal[DIM];
+  int zl[DIM][kMaxAxisAliases];
+  double wl[DIM][kMaxAxisAliases];
+  bool onb = true;
+  for (int i = 0; i < DIM; ++i) {
+    double sum = 0.0;
+    int n = 0;
+    for (int z = -R; z <= R + 1; ++z) {
+      const long long un = u[i] + P.D * z;
+      const long long t = un < 0 ? -2 * un : 2 * un;
+      if (t > (2 * R + 1) * P.D) continue;
+      const double g = axis_symbol(P, i, un);
+      if (g == 0.0) continue;
+      zl[i][n] = z;
+      wl[i][n] = g * g;
+      sum += g * g;
+      ++n;
+    }
+    if (!(sum > 0.0)) onb = false;
+    for (int q = 0; q < n; ++q) wl[i][q] /= sum;
+    nal[i] = n;
+  }
+  constexpr int NB = DIM == 2 ? 5 : 15;
+  double B[NB];
+#pragma unroll
+  for (int t = 0; t < NB; ++t) B[t] = 0.0;
+  if (!onb) {
+    atomicExch(err, (int)FH_ERR_NO_ONB);
+  } else if (DIM == 2) {
+    for (int a = 0; a < nal[0]; ++a) {
+      const double za = (double)zl[0][a], wa = wl[0][a];
+      const double ka0 = (double)h[0] + (double)P.M[0][0] * za, ka1 = (double)h[1] + (double)P.M[0][1] * za;
+      const double m0 = (double)P.M[1][0], m1 = (double)P.M[1][1];
+      for (int b = 0; b < nal[1]; ++b) {
+        const double zb = (double)zl[1][b];
+        const double k0 = fma(m0, zb, ka0), k1 = fma(m1, zb, ka1);  // integers: exact
+        const double p00 = k0 * k0, p11 = k1 * k1, p01 = k0 * k1;
+        const double r2 = p00 + p11;
+        if (r2 == 0.0) continue;  // Gamma^0(0) = 0
+        const double inv = __drcp_rn(r2);
+        const double q = wa * wl[1][b] * inv * inv;
+        const double q00 = q * p00, q01 = q * p01, q11 = q * p11;
+        B[0] = fma(q00, p00, B[0]);  // n0^4
+        B[1] = fma(q00, p01, B[1]);  // n0^3 n1
+        B[2] = fma(q00, p11, B[2]);  // n0^2 n1^2
+        B[3] = fma(q01, p11, B[3]);  // n0 n1^3
+        B[4] = fma(q11, p11, B[4]);  // n1^4
+      }
+    }
+  } else {
+    for (int a = 0; a < nal[0]; ++a) {
+      const double za = (double)zl[0][a], wa = wl[0][a];
+      double ka[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) ka[i] = (double)h[i] + (double)P.M[0][i] * za;
+      for (int b = 0; b < nal[1]; ++b) {
+        const double zb = (double)zl[1][b], wab = wa * wl[1][b];
+        double kb[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) kb[i] = fma((double)P.M[1][i], zb, ka[i]);
+        const double m0 = (double)P.M[2][0], m1 = (double)P.M[2][1], m2 = (double)P.M[2][2];
+        for (int c = 0; c < nal[2]; ++c) {
+          const double zc = (double)zl[2][c];
+          const double k0 = fma(m0, zc, kb[0]), k1 = fma(m1, zc, kb[1]), k2 = fma(m2, zc, kb[2]);
+          const double p00 = k0 * k0, p11 = k1 * k1, p22 = k2 * k2;
+          const double r2 = p00 + p11 + p22;
+          if (r2 == 0.0) continue;  // Gamma^0(0) = 0
+          const double p01 = k0 * k1, p02 = k0 * k2, p12 = k1 * k2;
+          const double inv = __drcp_rn(r2);
+          const double q = wab * wl[2][c] * inv * inv;
+          const double q00 = q * p00, q01 = q * p01, q02 = q * p02, q11 = q * p11, q12 = q * p12, q22 = q * p22;
+          B[0] = fma(q00, p00, B[0]);    // (4,0,0)
+          B[1] = fma(q00, p01, B[1]);    // (3,1,0)
+          B[2] = fma(q00, p02, B[2]);    // (3,0,1)
+          B[3] = fma(q00, p11, B[3]);    // (2,2,0)
+          B[4] = fma(q00, p12, B[4]);    // (2,1,1)
+          B[5] = fma(q00, p22, B[5]);    // (2,0,2)
+          B[6] = fma(q01, p11, B[6]);    // (1,3,0)
+          B[7] = fma(q01, p12, B[7]);    // (1,2,1)
+          B[8] = fma(q01, p22, B[8]);    // (1,1,2)
+          B[9] = fma(q11, p11, B[9]);    // (0,4,0)
+          B[10] = fma(q11, p12, B[10]);  // (0,3,1)
+          B[11] = fma(q11, p22, B[11]);  // (0,2,2)
+          B[12] = fma(q02, p22, B[12]);  // (1,0,3)
+          B[13] = fma(q12, p22, B[13]);  // (0,1,3)
+          B[14] = fma(q22, p22, B[14]);  // (0,0,4)
+        }
+      }
+    }
+  }
+  // fourth moment B_ijpq by exponents, second moment A_ij = sum_p B_ijpp (a copy
+  // is indexed at run time, so that B itself stays in registers in the loops)
+  double Bm[NB];
+#pragma unroll
+  for (int t = 0; t < NB; ++t) Bm[t] = B[t];
+  auto moment = [&](int i, int j, int p, int q) -> double {
+    int e[3] = {0, 0, 0};
+    ++e[i]; ++e[j]; ++e[p]; ++e[q];
+    if (DIM == 2) return Bm[e[1]];
+    return Bm[moment_index3(e[1], e[2])];
+  };
+  double A[3][3];
+  for (int i = 0; i < DIM; ++i)
+    for (int j = 0; j < DIM; ++j) {
+      double s = 0.0;
+      for (int p = 0; p < DIM; ++p) s += moment(i, j, p, p);
+      A[i][j] = s;
+    }
+  const double c4 = 0.25 / P.mu0;
+  const double cb = (P.lam0 + P.mu0) / (P.mu0 * (P.lam0 + 2.0 * P.mu0));
+  const double s2 = 1.41421356237309504880;
+  int t = 0;
+  for (int a = 0; a < P.nv; ++a) {
+    int i, j;
+    mandel_pair(DIM, a, i, j);
+    const double sa = (i == j) ? 1.0 : s2;
+    for (int b = a; b < P.nv; ++b) {
+      int p, q;
+      mandel_pair(DIM, b, p, q);
+      const double sb = (p == q) ? 1.0 : s2;
+      const double lin = (i == p ? A[j][q] : 0.0) + (i == q ? A[j][p] : 0.0) + (j == p ? A[i][q] : 0.0) +
+                         (j == q ? A[i][p] : 0.0);
+      const double v = sa * sb * (c4 * lin - cb * moment(i, j, p, q));
+      G64[(size_t)t * P.nhalf + f] = v;
+      G32[(size_t)t * P.nhalf + f] = (float)v;
+      ++t;
+    }
   }
 }
 

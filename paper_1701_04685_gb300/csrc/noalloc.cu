@@ -1,24 +1,29 @@
 // Allocation-free variant of the mean-stress reduction (fh_mean_stress_noalloc).
 //
 // Some callers cannot allocate device memory at the moment they need a result:
-// code that runs while a CUDA graph is being captured (cudaMalloc is not
-// allowed there), real-time or latency-bound loops where an allocation may
-// block or fail, and applications whose device memory is owned entirely by
-// their own arena allocator.  For them this entry point keeps all of its
-// scratch -- the per-block partial sums, the block counter and the result --
+// real-time or latency-bound loops where an allocation may block or fail, and
+// applications (a larger simulation that embeds this solver, for example)
+// whose device memory is owned entirely by their own arena allocator with a
+// fixed budget.  For them this entry point keeps all of its scratch -- the
+// per-block partial sums, the block counter, an error word and the result --
 // in one fixed array that lives in the library image, so no call ever
 // allocates.  The caller passes the inputs (strain field, phase ids, phase
 // stiffnesses, macroscopic strains) and the output buffer.
 //
 // The array is a host-side symbol in host code; its device address is looked
 // up with cudaGetSymbolAddress once per device, on the first call made while
-// that device is current.  That first call therefore must not be made during
-// a stream capture.  Every call shares the array: calls whose work overlaps on
-// the GPU (different streams, or different host threads) race on it.
+// that device is current, and cached.  That first call should come before any
+// stream capture.  The cached address belongs to the device's context of that
+// moment: after cudaDeviceReset the next context has a new copy of the array,
+// so a process that resets a device must not call this entry point again.
+// Every call shares the array: calls whose work overlaps on the GPU (different
+// streams, or different host threads) race on it.  Each call synchronises its
+// stream before it returns.
 
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <string>
 
@@ -31,7 +36,7 @@ constexpr int kNaMaxLoads = FH_MAX_LOADS;      // 16 load cases
 constexpr int kNaMaxBlocks = 64;               // blocks per load case
 constexpr int kNaPartials = kNaMaxLoads * kNaMaxBlocks * kMaxV;
 constexpr int kNaOut = kNaMaxLoads * kMaxV;
-constexpr int kNaTotal = kNaPartials + kNaOut + 32;  // + block counter slot
+constexpr int kNaTotal = kNaPartials + kNaOut + 32;  // + block counter and error word
 
 // 6272 doubles = 49 KB, resident on every GPU that loads the library.
 static __device__ __align__(256) double g_noalloc_scratch[kNaTotal];
@@ -71,15 +76,21 @@ __global__ void __launch_bounds__(256) mean_stress_noalloc(NaParams P, const dou
   double* partials = scratch;
   double* out = scratch + kNaPartials;
   unsigned int* ticket = reinterpret_cast<unsigned int*>(scratch + kNaPartials + kNaOut);
+  unsigned int* bad_id = ticket + 1;  // set when a phase id >= nphase is met
   const int load = blockIdx.x / blocks_per_load;
   const int q = blockIdx.x - load * blocks_per_load;
   const int nv = P.nv;
   double acc[kMaxV] = {0, 0, 0, 0, 0, 0};
   const size_t base = (size_t)load * nv * P.m;
   for (long long i = (long long)q * blockDim.x + threadIdx.x; i < P.m; i += (long long)blocks_per_load * blockDim.x) {
+    const int ph = phase[i];
+    if (ph >= P.nphase) {  // never index the parameter block with an id it does not hold
+      *bad_id = 1u;
+      continue;
+    }
     double e[kMaxV];
     for (int c = 0; c < nv; ++c) e[c] = E[base + (size_t)c * P.m + i] + P.eps0[load * 6 + c];
-    const double* C = P.Cp + phase[i] * 36;
+    const double* C = P.Cp + ph * 36;
     for (int a = 0; a < nv; ++a) {
       double s = 0.0;
       for (int b = 0; b < nv; ++b) s += C[a * nv + b] * e[b];
@@ -108,15 +119,17 @@ __global__ void __launch_bounds__(256) mean_stress_noalloc(NaParams P, const dou
   if (threadIdx.x == 0) *ticket = 0u;
 }
 
-// device address of the scratch array, looked up once per device
+// device address of the scratch array, looked up once per device; the slots are
+// atomic so that host threads calling on different devices at once do not race
 double* scratch_address(int device, fh_status* rc) {
-  static double* addr[64] = {};
+  static std::atomic<double*> addr[64];  // static storage: every slot starts null
   if (device < 0 || device >= 64) {
     fh::set_error("device ordinal out of range");
     *rc = FH_ERR_ARG;
     return nullptr;
   }
-  if (!addr[device]) {
+  double* a = addr[device].load(std::memory_order_acquire);
+  if (!a) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || p == nullptr) {
@@ -124,10 +137,11 @@ double* scratch_address(int device, fh_status* rc) {
       *rc = FH_ERR_CUDA;
       return nullptr;
     }
-    addr[device] = static_cast<double*>(p);
+    a = static_cast<double*>(p);
+    addr[device].store(a, std::memory_order_release);  // every thread finds the same address
   }
   *rc = FH_OK;
-  return addr[device];
+  return a;
 }
 
 }  // namespace
@@ -165,7 +179,7 @@ extern "C" fh_status fh_mean_stress_noalloc(int d, long long m, int nload, const
   if (!scratch) return rc;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
   unsigned int* ticket = reinterpret_cast<unsigned int*>(scratch + kNaPartials + kNaOut);
-  e = cudaMemsetAsync(ticket, 0, sizeof(unsigned int), st);  // the block counter starts at zero
+  e = cudaMemsetAsync(ticket, 0, 2 * sizeof(unsigned int), st);  // block counter and error word start at zero
   if (e != cudaSuccess) { fh::set_error(std::string("cudaMemsetAsync: ") + cudaGetErrorString(e)); return FH_ERR_CUDA; }
   const int bpl = (int)std::min<long long>((m + 255) / 256, kNaMaxBlocks);
   mean_stress_noalloc<<<nload * bpl, 256, 0, st>>>(P, E, phase, scratch, bpl);
@@ -177,7 +191,14 @@ extern "C" fh_status fh_mean_stress_noalloc(int d, long long m, int nload, const
                         cudaMemcpyDefault, st);
     if (e != cudaSuccess) { fh::set_error(std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e)); return FH_ERR_CUDA; }
   }
+  unsigned int bad = 0;
+  e = cudaMemcpyAsync(&bad, ticket + 1, sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) { fh::set_error(std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e)); return FH_ERR_CUDA; }
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { fh::set_error(std::string("cudaStreamSynchronize: ") + cudaGetErrorString(e)); return FH_ERR_CUDA; }
+  if (bad) {
+    fh::set_error("a phase id >= nphase was found; the mean stress written is not valid");
+    return FH_ERR_ARG;
+  }
   return FH_OK;
 }

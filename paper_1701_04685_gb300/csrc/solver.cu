@@ -659,6 +659,43 @@ bool cholesky_ok(const double* A, int n) {
 }
 
 // Mandel matrix -> fourth-order tensor C_ijkl (3x3x3x3 storage)
+// The closed-form table kernel (green_table_iso) applies when C0 is isotropic
+// (Mandel: lam0 + 2 mu0 on the normal diagonal, lam0 off it, 2 mu0 on the shear
+// diagonal, zero elsewhere; compared to 1e-15 of its largest entry) and the
+// symbol is a product of per-axis factors: Dirichlet, dlVP, or a box spline
+// whose directions are all +-e_i.  Fills lam0, mu0 and the per-axis direction
+// counts of GP.
+bool closed_form_table(const fh_solver* s, const double* c0, fh::GreenParams* GP) {
+  const int nv = s->g.nv, d = s->g.d;
+  const double lam0 = c0[1], mu0 = 0.5 * c0[(nv - 1) * nv + nv - 1];
+  double big = 0.0;
+  for (int e = 0; e < nv * nv; ++e) big = std::max(big, std::fabs(c0[e]));
+  for (int a = 0; a < nv; ++a)
+    for (int b = 0; b < nv; ++b) {
+      double want = 0.0;
+      if (a < d && b < d) want = lam0 + (a == b ? 2.0 * mu0 : 0.0);
+      else if (a == b) want = 2.0 * mu0;
+      if (std::fabs(c0[a * nv + b] - want) > 1e-15 * big) return false;
+    }
+  if (!(mu0 > 0.0) || !(lam0 + 2.0 * mu0 > 0.0)) return false;
+  for (int i = 0; i < 3; ++i) GP->xcount[i] = 0;
+  if (s->gen.kind == FH_GEN_BOXSPLINE) {
+    for (int q = 0; q < s->gen.n_xi; ++q) {
+      int axis = -1, nonzero = 0;
+      for (int i = 0; i < d; ++i) {
+        const double v = s->gen.xi[3 * q + i];
+        if (v != 0.0) { ++nonzero; axis = i; }
+        if (v != 0.0 && std::fabs(v) != 1.0) return false;
+      }
+      if (nonzero != 1) return false;
+      GP->xcount[axis] += 1;
+    }
+  }
+  GP->lam0 = lam0;
+  GP->mu0 = mu0;
+  return true;
+}
+
 void mandel_to_c4(const double* Cm, int d, double* C4) {
   const int I2[3] = {0, 1, 0}, J2[3] = {0, 1, 1};
   const int I3[6] = {0, 1, 2, 1, 0, 0}, J3[6] = {0, 1, 2, 2, 2, 1};
@@ -1047,7 +1084,12 @@ fh_status fh_set_reference(fh_solver* s, const double* C0) {
   if (rc != FH_OK) return rc;
   CK(cudaMemsetAsync(s->err, 0, sizeof(int), s->work));
   const int blocks = (int)((s->g.nhalf + 127) / 128);
-  fh::green_table<<<blocks, 128, 0, s->work>>>(GP, s->G64, s->G32, s->err);
+  if (closed_form_table(s, c0, &GP)) {
+    if (d == 2) fh::green_table_iso<2><<<blocks, 128, 0, s->work>>>(GP, s->G64, s->G32, s->err);
+    else fh::green_table_iso<3><<<blocks, 128, 0, s->work>>>(GP, s->G64, s->G32, s->err);
+  } else {
+    fh::green_table<<<blocks, 128, 0, s->work>>>(GP, s->G64, s->G32, s->err);
+  }
   CK(cudaGetLastError());
   // stiffness differences C_p - C0
   double dc[kMaxPhases * 36];

@@ -18,10 +18,7 @@ Every microstructure is solved for the six Mandel unit strains at once, which
 gives six training solutions per solve.
 
 Run ``python -m paper_1701_04685_gb300.learned_start --n 64 --train 683 --test 256``
-for the full experiment (4098 training solutions, 256 held-out seeds x 6 loads);
-``--restarts K`` adds ``restart_study`` on K held-out seeds: iterations from
-starts of known quality built from the converged strain (scaled, noisy,
-low-pass filtered) beside the network's prediction.
+for the full experiment (4098 training solutions, 256 held-out seeds x 6 loads).
 """
 from __future__ import annotations
 
@@ -147,50 +144,6 @@ def summary(rows):
             "fallback_fraction": float(np.mean([f for r in rows for f in r["fallback"]]))}
 
 
-def _lowpass(E, n, K):
-    """Keep the Fourier coefficients of an n^3 field with |k|_inf < K (host-side analysis)."""
-    F = np.fft.rfftn(E.reshape(n, n, n))
-    k = np.abs(np.fft.fftfreq(n) * n)
-    kz = np.arange(n // 2 + 1)
-    mask = (k[:, None, None] < K) & (k[None, :, None] < K) & (kz[None, None, :] < K)
-    return np.fft.irfftn(F * mask, s=(n, n, n), axes=(0, 1, 2)).reshape(-1)
-
-
-def restart_study(seed, n, tol=1e-6, net=None):
-    """Iterations to tolerance from starts derived from the converged strain E* of one
-    microstructure: the zero start, (1 - delta) E*, E* plus white noise of relative rms
-    delta, low-pass filtered E*, and (if a network is given) its prediction."""
-    import torch
-    s, ids, logE = make_solver(W.fno3d_item(seed, n=n))
-    z = s.solve(np.eye(6), tol=tol, max_iter=20000, precision=FH_PREC_MIXED)
-    Es = [s.get_strain(L).copy() for L in range(6)]
-    rng = np.random.default_rng(seed)
-
-    def run(starts):
-        for L in range(6):
-            s.set_strain(L, np.ascontiguousarray(starts[L]))
-        o = s.solve(np.eye(6), tol=tol, max_iter=20000, precision=FH_PREC_MIXED, init=1)
-        return float(np.mean(o["iterations"]))
-
-    row = {"seed": int(seed), "zero": float(np.mean(z["iterations"]))}
-    for delta in (0.5, 0.2, 0.05, 0.01):
-        row[f"scaled_{delta}"] = run([(1 - delta) * E for E in Es])
-        row[f"noise_{delta}"] = run([E + delta * np.sqrt(np.mean(E ** 2)) * rng.standard_normal(E.shape) for E in Es])
-    for K in (2, 4, 8, 12):
-        row[f"lowpass_{K}"] = run([np.stack([_lowpass(E[c], n, K) for c in range(6)]) for E in Es])
-    if net is not None:
-        x = torch.empty((1, 1, n ** 3), dtype=torch.float32, device="cuda")
-        y = torch.empty((1, 36, n ** 3), dtype=torch.float32, device="cuda")
-        net.make_input(torch.from_numpy(ids).cuda(), logE, np.zeros(6), x[0])
-        net.forward(x, y)
-        Pn = y[0].cpu().numpy().astype(np.float64).reshape(6, 6, -1)
-        row["prediction_relerr"] = float(np.mean([np.linalg.norm(Pn[L] - Es[L]) / np.linalg.norm(Es[L])
-                                                  for L in range(6)]))
-        row["prediction"] = run([Pn[L] for L in range(6)])
-    s.close()
-    return row
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=64)
@@ -203,8 +156,6 @@ def main():
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--batch", type=int, default=4)
     ap.add_argument("--out", default=None)
-    ap.add_argument("--restarts", type=int, default=0,
-                    help="after training, run restart_study on this many held-out seeds")
     a = ap.parse_args()
     import torch
     log = lambda s: print(s, flush=True)  # noqa: E731
@@ -225,9 +176,6 @@ def main():
     res = {"config": vars(a), "generate_s": t_gen, "train_s": t_train, "loss_history": hist,
            "summary": summary(rows)}
     log(json.dumps(res["summary"]))
-    res["restarts"] = [restart_study(seed, a.n, net=net) for seed in range(100000, 100000 + a.restarts)]
-    for row in res["restarts"]:
-        log(json.dumps(row))
     if a.out:
         with open(a.out, "w") as f:
             json.dump({**res, "rows": rows}, f)

@@ -51,7 +51,8 @@ def test_batch_matches_oracle(fh):
 
 def test_batch_mixed_converges(fh):
     """Mixed-precision batch to r <= 1e-6: every load converges, C_eff symmetric and
-    positive definite, each item's FP64 polishing step leaves a small Cauchy residual."""
+    positive definite, and every load's last (FP64) Cauchy residual meets the tolerance
+    the batch was solved to."""
     ws = _items(range(12))
     cases = [Case.from_workload(w) for w in ws]
     solvers = [c.product(fh) for c in cases]
@@ -60,7 +61,7 @@ def test_batch_mixed_converges(fh):
     assert rc == 0
     for s, o in zip(solvers, outs):
         assert np.all(o["load_status"] == 0)
-        assert np.all(o["residual"] < 1e-4)
+        assert np.all(o["residual"] <= 1e-6)
         C = s.get_ceff()
         assert rel(C, C.T) < 1e-5
         assert np.linalg.eigvalsh(0.5 * (C + C.T)).min() > 0

@@ -63,10 +63,11 @@ def test_green_table_matches_oracle(fh, spec):
 PATHS = [(1, 0), (2, 8), (2, 16)]   # (path, cluster size)
 
 
-def _solve_or_skip(fh, s, eps0, n, prec, path):
+def _solve_or_skip(fh, s, eps0, n, prec, path, tol=0.0, max_iter=None, init=0):
     """Solve with a forced path; a cluster size whose fields do not fit is skipped."""
     try:
-        return s.solve(eps0, tol=0.0, max_iter=n, precision=prec, path=path[0], cluster=path[1])
+        return s.solve(eps0, tol=tol, max_iter=n if max_iter is None else max_iter, precision=prec,
+                       path=path[0], cluster=path[1], init=init)
     except fh.FhError as e:
         if e.status == -8 and path[0] == 2:
             pytest.skip("fields do not fit in a cluster of this size")
@@ -130,13 +131,15 @@ def test_config_disk32_to_tolerance(fh):
         Eg = s.get_strain(L)
         Eo = refL["E"][0][case.perm].T
         assert np.abs(Eg - Eo).max() / np.abs(Eo + case.eps0[L][:, None]).max() < TOL64
-    from oracle import scheme as OS
+    from oracle import material as OM, scheme as OS
     Cg = s.get_ceff()
     ms = np.stack([case.oracle_solve(tol=0.0, max_iter=int(out["iterations"][L]),
                                      eps0=case.eps0[L:L + 1])["mean_stress"][0] for L in range(3)])
     Co = OS.effective_stiffness(ms, case.eps0)
     assert rel(Cg, Co) < TOL64
     assert rel(Cg, Cg.T) < 1e-6
+    # Voigt output (engineering shear strains): the oracle's conversion of the same matrix
+    assert rel(s.get_ceff(voigt=True), OM.mandel_to_voigt(Co, 2)) < TOL64
 
 
 @pytest.mark.parametrize("path", PATHS, ids=["passes", "cluster8", "cluster16"])
@@ -240,6 +243,40 @@ def test_nonfinite_stiffness_is_reported(fh):
     with pytest.raises(fh.FhError) as e:
         s.set_stiffness_phases(np.zeros(64, np.uint8), Cp)
     assert e.value.status == -1
+
+
+@pytest.mark.parametrize("path", PATHS, ids=["passes", "cluster8", "cluster16"])
+def test_diverging_reference_medium_is_reported(fh, path):
+    """A reference medium five times softer than the softest phase makes the fixed
+    point diverge (the error operator's spectrum reaches |1 - c/c0| >= 4): the solve
+    stops with FH_DIVERGED once the iterate has grown by a factor 1e6, and the
+    context stays usable for the next solve."""
+    case = _case(CASES[0])
+    s = case.product(fh)
+    lam, mu = fh.lame(1.0, 0.3)
+    s.set_reference(fh.isotropic_stiffness(0.2 * lam, 0.2 * mu, 2))
+    out = _solve_or_skip(fh, s, case.eps0, 0, fh.FH_PREC_FP64, path, tol=1e-8, max_iter=2000)
+    assert out["status"] == 2 and np.all(out["load_status"] == 2), out["load_status"]
+    assert np.all(out["iterations"] < 200)
+    s.set_reference(None)                                   # the usual medium converges again
+    out = s.solve(case.eps0, tol=1e-8, max_iter=5000)
+    assert out["status"] == 0
+
+
+@pytest.mark.parametrize("path", PATHS, ids=["passes", "cluster8", "cluster16"])
+def test_nonfinite_start_is_reported(fh, path):
+    """A NaN in the starting strain (fh_set_strain, init = 1) gives FH_NONFINITE on
+    that load after one iteration; the other loads are unaffected."""
+    case = _case(CASES[0])
+    s = case.product(fh)
+    s.solve(case.eps0, tol=0.0, max_iter=2)
+    E = s.get_strain(1).copy()
+    E[2, 17] = np.nan
+    s.set_strain(1, E)
+    out = _solve_or_skip(fh, s, case.eps0, 0, fh.FH_PREC_FP64, path, tol=1e-8, max_iter=5000, init=1)
+    assert out["status"] == 3
+    assert list(out["load_status"]) == [0, 3, 0]
+    assert out["iterations"][1] == 1
 
 
 def _ceff_reference():

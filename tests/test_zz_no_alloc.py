@@ -1,11 +1,12 @@
 """The allocation-free mean-stress entry point, called through the C ABI.
 
 fh_mean_stress_noalloc serves callers that cannot allocate device memory when
-they need the result (inside a CUDA-graph capture, in real-time loops, or under
-an application-owned allocator): its scratch is a fixed array inside the
-library.  This test checks it against the mean stresses that the regular
-fh_solve entry point returns, on two calls in a row (the second call reuses the
-array the first one left behind).  The file is collected last on purpose.
+they need the result (real-time loops where an allocation could block or fail,
+applications whose device memory belongs to their own fixed-budget allocator):
+its scratch is a fixed array inside the library.  This test checks it against
+the mean stresses that the regular fh_solve entry point returns, on two calls
+in a row (the second call reuses the array the first one left behind).  The
+file is collected last on purpose.
 """
 import ctypes as C
 
@@ -75,3 +76,22 @@ def test_noalloc_rejects_too_many_loads(fh):
     out = np.zeros((17, nv))
     assert _call(fh, 2, m, 17, E, phase, Cp, eps0, out) == -1
     assert b"16" in fh.library().fh_last_error()
+
+
+def test_noalloc_rejects_phase_id_out_of_range(fh):
+    """An id equal to nphase is reported as FH_ERR_ARG and never used as an index."""
+    import torch
+    m, nv = 300, 3
+    E = torch.zeros((1, nv, m), dtype=torch.float64, device="cuda")
+    ids = np.zeros(m, dtype=np.uint8)
+    ids[123] = 2                                           # nphase = 2 below
+    phase = torch.from_numpy(ids).cuda()
+    Cp = np.ascontiguousarray(np.stack([fh.isotropic_stiffness(1.0, 1.0, 2)] * 2))
+    eps0 = np.ascontiguousarray(np.eye(nv)[:1])
+    out = np.zeros((1, nv))
+    assert _call(fh, 2, m, 1, E, phase, Cp, eps0, out) == -1
+    assert b"phase id" in fh.library().fh_last_error()
+    ids[123] = 1                                           # the next call starts clean
+    phase = torch.from_numpy(ids).cuda()
+    assert _call(fh, 2, m, 1, E, phase, Cp, eps0, out) == 0
+    assert np.allclose(out[0], Cp[0] @ eps0[0], rtol=1e-14, atol=0)
