@@ -1,27 +1,24 @@
 #!/usr/bin/env python
-"""Benchmark of the Basic-Scheme solver on the anisotropic dlVP workload.
+"""Benchmark of the Basic-Scheme solver (Moulinec-Suquet fixed point on the pattern P(M)).
 
-Workload (the configuration the headline metric is quoted on): M = [[128,32],[0,128]] (m = 16384,
-Smith grid 32 x 512), de la Vallee Poussin generator with plateau |u| <= 0.25
-and ramp to 0.75, 20 random non-overlapping disks (radii U[0.03,0.08], seed 2)
-at contrast 100, nu = 0.3, the 3 Mandel unit strains, Cauchy tolerance 1e-6.
+Headline workload, the largest configuration that fits one GPU: M = diag(128,128,128)
+(m = 2 097 152, Smith grid 128^3), tensor-product box spline of order 2 with alias radius 4
+(729 aliases per frequency), 50 random non-overlapping spheres (radii U[0.05,0.1], seed 3) at
+contrast 50, nu = 0.3, the 6 Mandel unit strains, Cauchy tolerance 1e-6.
 
-One step = one complete solve of that workload: the Gamma^p table build
-(fh_set_reference), every fixed-point iteration of all 3 load cases until each
-reaches r <= 1e-6, and the FP64 mean-stress / C_eff reduction.  The metric is
-voxel-iterations/s = sum over loads of m * iterations / time; time-to-1e-6 is
-the per-step time.  Three precision modes are run: plain FP64, FP32 bulk
-stages, and mixed (FP32 iterations, then one FP64 step); each reports its C_eff
-error against the converged FP64 oracle (tests/golden/ceff_dlvp_sheared.txt).
-The headline is the mode selected with --mode (default: mixed, the fastest mode
-whose C_eff meets 1e-6).
+One step = one complete solve of that workload: the Gamma^p table build (fh_set_reference,
+FP64 on the device), every fixed-point iteration of all 6 loads until each reaches r <= 1e-6,
+and the FP64 mean-stress / C_eff reduction.  The metric is voxel-iterations/s = sum over loads
+of m * iterations / step time; time-to-1e-6 is the step time.  Modes: plain FP64, FP32 bulk
+stages, and mixed (FP32 iterations, then FP64 iterations to the same tolerance: the headline,
+--mode).  Each reports its C_eff error against the converged FP64 oracle
+(tests/golden/ceff_box3d.txt, written by a script that calls only the oracle).
 
-The line also carries the batched 2-D workload (512 microstructures) and the
-3-D box-spline workload (M = diag(128,128,128), 6 loads: time to 1e-6 per
-precision mode and the HBM roofline of each pass of one iteration).
+The line also carries the 2-D anisotropic workload (M = [[128,32],[0,128]], dlVP, 3 loads) and
+the batched 2-D workload (512 microstructures), each with its own modes.
 
-Prints one JSON line (rank 0).  --impl reference runs the FP64 CPU oracle on a
-bounded sample of the same workload instead.
+Prints one JSON line (rank 0).  --impl reference runs the FP64 CPU oracle on a bounded sample of
+the headline workload instead.
 """
 from __future__ import annotations
 
@@ -34,14 +31,7 @@ import sys
 import tempfile
 import time
 
-# The FP64 CPU oracle (the reference arm and the cpu_baseline leg) is timed on
-# one host thread: pin numpy's BLAS before numpy loads, so that "cores": 1 in
-# the JSON line is what actually ran (its threaded GEMMs on small tiles were
-# slower anyway).
-os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
-os.environ.setdefault("MKL_NUM_THREADS", "1")
-
-import numpy as np  # noqa: E402
+import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
@@ -51,8 +41,18 @@ import workloads as W  # noqa: E402
 
 METRIC = "voxel-iterations/s & time-to-1e-6 residual: batched/mixed/learned vs plain FP64"
 UNIT = "voxel-iterations/s"
-WORKLOAD = ("dlvp_sheared: M=[[128,32],[0,128]] (m=16384, grid 32x512), dlVP plateau 0.25 ramp 0.5, "
-            "20 disks r~U[0.03,0.08] contrast 100, 3 Mandel unit loads, Cauchy tol 1e-6")
+WORKLOAD = ("box3d: M=diag(128,128,128) (m=2097152, grid 128^3), tensor box spline order 2, alias radius 4 "
+            "(729 aliases), 50 spheres r~U[0.05,0.1] seed 3, contrast 50, nu 0.3, 6 Mandel unit loads, "
+            "Cauchy tol 1e-6; step = Gamma^p table build + solve of all 6 loads + C_eff")
+WORKLOAD_2D = ("dlvp_sheared: M=[[128,32],[0,128]] (m=16384, grid 32x512), dlVP plateau 0.25 ramp 0.5, "
+               "20 disks r~U[0.03,0.08] contrast 100, 3 Mandel unit loads, Cauchy tol 1e-6")
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+PROFILES = os.path.join(ROOT, "profiles")
+
+# Nominal GB300 arithmetic peaks (no measured FP32/FP64 figure exists for this machine):
+# FP32 = 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz; FP64 = the vendor's 1.25 TFLOP/s.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
 
 
 def parse():
@@ -64,74 +64,139 @@ def parse():
     ap.add_argument("--mode", default="mixed", choices=["fp64", "fp32", "mixed"])
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-2d", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-cluster", type=int, default=0)
-    ap.add_argument("--no-box3d", action="store_true")
-    ap.add_argument("--only-box3d", action="store_true",
-                    help="run only the 3-D box-spline section (prints its JSON object)")
-    ap.add_argument("--box3d-n", type=int, default=128, help="grid size of the 3-D section")
-    ap.add_argument("--box3d-modes", default="mixed,fp32,fp64",
-                    help="precision modes of the 3-D section (comma-separated)")
+    ap.add_argument("--modes", default="mixed,fp32,fp64", help="precision modes of the headline workload")
+    ap.add_argument("--only-headline", action="store_true", help="skip every extra section")
+    ap.add_argument("--ncu-iteration", action="store_true",
+                    help="profiling aid: set up the headline workload, run 3 FP32 iterations, then launch each "
+                         "pass of one FP32 iteration twice (fh_profile_passes, reps=1) and exit")
     return ap.parse_args()
+
+
+def golden_ceff(name, block):
+    """A block of a stored oracle result (tests/golden/); plain file parsing."""
+    sys.path.insert(0, GOLDEN)
+    from golden_io import read_golden_blocks
+    path = os.path.join(GOLDEN, name)
+    if not os.path.exists(path):
+        return None
+    return read_golden_blocks(path)[block]
+
+
+def frob_rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
 # ---------------------------------------------------------------------------
 # CPU oracle (the reference arm and the cpu_baseline leg)
 # ---------------------------------------------------------------------------
 
-def oracle_problem(w):
+def host_cpu():
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return os.cpu_count() or 1, model
+
+
+def _oracle_setup(workers):
     from oracle import generators as OG, green as OGr, material as OM, scheme as OS
-    T = OS.SNFTransform(w["M"])
+    w = W.box3d()
+    T = OS.SNFTransform(w["M"], workers=workers)
     ids = W.phase_ids(T.points / T.D, w["centres"], w["radii"])
     lm = [OM.lame(E, nu) for E, nu in w["phases"]]
-    Cp = np.stack([OM.isotropic_mandel(l, m, 2) for l, m in lm])
+    Cp = np.stack([OM.isotropic_mandel(l, m, 3) for l, m in lm])
     l0, m0 = OM.reference_medium_ms([l for l, _ in lm], [m for _, m in lm])
-    C0 = OM.isotropic_mandel(l0, m0, 2)
-    Gp = OGr.gamma_p_table(w["M"], OG.Generator("dlvp", alpha=w["generator"]["alpha"]), C0, T.freqs)
-    return T, Gp, Cp[ids], C0
+    C0 = OM.isotropic_mandel(l0, m0, 3)
+    gen = OG.Generator("boxspline", xi=OG.tensor_boxspline_xi(3, 2), radius=4)
+    return w, T, Cp[ids], C0, gen
 
 
-def oracle_sample(w, seconds, max_iter=5000):
-    """Time the oracle as it stands on one load case, iterating until `seconds` elapse."""
+def _oracle_table_chunk(args):
+    """Worker: the oracle's Gamma^p table on one chunk of frequencies, timed inside the worker."""
+    M, C0, freqs = args
+    from oracle import generators as OG, green as OGr
+    gen = OG.Generator("boxspline", xi=OG.tensor_boxspline_xi(3, 2), radius=4)
+    t0 = time.perf_counter()
+    OGr.gamma_p_table(M, gen, C0, freqs)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_box3d():
+    """The FP64 oracle as it stands, on all host cores, over a bounded sample of the headline
+    workload, extrapolated to the whole solve: the Gamma^p table on nproc chunks of 1024
+    frequencies computed by nproc processes at once (the slowest worker's time), and 2
+    fixed-point iterations of load 1 with scipy.fft on nproc threads; each timed 3 times
+    (median).  Time to 1e-6 = table time scaled to all m frequencies + the oracle's own
+    iteration counts to 1e-6 (golden file) x the time per iteration."""
+    import multiprocessing as mp
     from oracle import scheme as OS
-    T, Gp, C, C0 = oracle_problem(w)
-    e0 = np.eye(3)[:1]
-    n = 8
-    t0 = time.perf_counter()
-    OS.solve(T, Gp, C, C0, e0, tol=0.0, max_iter=n)
-    dt = time.perf_counter() - t0
-    n = int(min(max_iter, max(8, seconds / max(dt / 8, 1e-6))))
-    t0 = time.perf_counter()
-    OS.solve(T, Gp, C, C0, e0, tol=0.0, max_iter=n)
-    dt = time.perf_counter() - t0
-    return {"value": T.m * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"load 1 of 3, {n} fixed-point iterations of the FP64 oracle (numpy FFT on the "
-                      f"Smith grid), {dt:.1f} s single-threaded"}
+    nproc, model = host_cpu()
+    ref = golden_ceff("ceff_box3d.txt", "box3d")
+    iters = ref["iterations_to_1e-6"] if ref is not None else [167] * 6
+    w, T, C, C0, gen = _oracle_setup(nproc)
+    chunk = 1024
+    ctx = mp.get_context("spawn")
+    t_tab = []
+    with ctx.Pool(nproc) as pool:
+        for rep in range(3):
+            jobs = [(w["M"], C0, np.array(T.freqs[(rep * nproc + k) * chunk:(rep * nproc + k + 1) * chunk]))
+                    for k in range(nproc)]
+            t_tab.append(max(pool.map(_oracle_table_chunk, jobs)) * T.m / (nproc * chunk))
+    Gp = np.zeros((T.m, 6, 6))     # iteration cost does not depend on the table's values
+    t_it = []
+    e0 = np.eye(6)[:1]
+    for _ in range(3):
+        t0 = time.perf_counter()
+        OS.solve(T, Gp, C, C0, e0, tol=0.0, max_iter=2)
+        t_it.append((time.perf_counter() - t0) / 2)
+    tt, ti = float(np.median(t_tab)), float(np.median(t_it))
+    total = tt + ti * sum(iters)
+    return {"value": T.m * sum(iters) / total, "unit": UNIT, "cores": nproc, "kind": "oracle",
+            "cpu_model": model,
+            "sample": (f"FP64 oracle on {nproc} host cores: Gamma^p table of {nproc} x {chunk} frequencies "
+                       f"by {nproc} processes ({tt:.1f} s scaled to all {T.m}), 2 fixed-point iterations "
+                       f"of one load with scipy.fft workers={nproc} ({ti:.2f} s per iteration), medians "
+                       f"of 3; extrapolated to the oracle's {sum(iters)} iterations to 1e-6 over 6 loads: "
+                       f"{total:.0f} s per solve"),
+            "time_to_tol_s": total, "table_s": tt, "iteration_s": ti}
 
 
 def run_reference(args, rank):
+    """Reference arm: the FP64 oracle as it stands on all host cores.  One step = one
+    fixed-point iteration of one load of the headline workload (scipy.fft with nproc
+    workers); the Gamma^p table of the box spline takes the oracle tens of minutes, and an
+    iteration's cost does not depend on its values, so the sample iterates with a zero
+    table and reports the iteration throughput."""
     if rank != 0:
         return
-    w = W.dlvp_sheared()
     from oracle import scheme as OS
-    T, Gp, C, C0 = oracle_problem(w)
-    e0 = np.eye(3)[:1]
-    iters = 30
+    nproc, model = host_cpu()
+    w, T, C, C0, gen = _oracle_setup(nproc)
+    Gp = np.zeros((T.m, 6, 6))
+    e0 = np.eye(6)[:1]
     for _ in range(args.warmup):
-        OS.solve(T, Gp, C, C0, e0, tol=0.0, max_iter=iters)
+        OS.solve(T, Gp, C, C0, e0, tol=0.0, max_iter=1)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        OS.solve(T, Gp, C, C0, e0, tol=0.0, max_iter=iters)
+        OS.solve(T, Gp, C, C0, e0, tol=0.0, max_iter=1)
     dt = time.perf_counter() - t0
-    value = T.m * iters * args.steps / dt
+    value = T.m * args.steps / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "step": f"{iters} oracle iterations of one load case (bounded sample)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{iters} iterations x {args.steps} steps, load 1 of 3"},
+            "config": {"workload": WORKLOAD, "step": "one FP64 oracle fixed-point iteration of one load case "
+                                                    "(bounded sample; iteration throughput)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nproc, "kind": "oracle", "cpu_model": model,
+                             "sample": f"{args.steps} oracle iterations of load 1, scipy.fft workers={nproc}"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -196,15 +261,169 @@ def reduce_over_ranks(dist, total_ms, vox, device):
     return float(t.item()), int(v.item())
 
 
-def ceff_reference():
-    path = os.path.join(ROOT, "tests", "golden", "ceff_dlvp_sheared.txt")
-    return np.loadtxt(path) if os.path.exists(path) else None
+def hbm_peak():
+    """Measured copy bandwidth of this pool's GB300s (GB/s), else the fallback figure."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s (of fallback)"
 
 
-def flops_per_launch(g, nload, kind):
-    """Algorithmic FLOPs of one launch of a pass (5 N log2 N per complex FFT of
-    length N, half that for a real one; n_v^2 FMAs per point for the stress,
-    4 n_v^2 flops per half-spectrum frequency for the Green step)."""
+def profile_traffic(name):
+    """DRAM bytes per iteration of the FP32 passes from a committed ncu summary
+    (the line 'traffic_bytes_per_iteration: N'), or None."""
+    path = os.path.join(PROFILES, name)
+    try:
+        for line in open(path):
+            if line.strip().startswith("traffic_bytes_per_iteration:"):
+                return int(line.split(":", 1)[1].split()[0])
+    except OSError:
+        pass
+    return None
+
+
+def timed_steps(step, steps, warmup, flush, clocks_index=None):
+    """Run warm-up steps, then `steps` timed ones (CUDA events, L2 flushed before each)."""
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(clocks_index) if clocks_index is not None else None
+    times, outs = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = step()
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        outs.append(out)
+    torch.cuda.synchronize()
+    return times, outs, (clocks.stop() if clocks is not None else None)
+
+
+def run_headline(fh, args, dist, local_rank):
+    import torch
+    w = W.box3d()
+    p = fh.Pattern(w["M"])
+    ids = W.phase_ids(p.points(), w["centres"], w["radii"])
+    Cp = np.stack([fh.isotropic_stiffness(*fh.lame(E, nu), 3) for E, nu in w["phases"]])
+    stream = torch.cuda.current_stream().cuda_stream
+    s = fh.Solver(p, fh.tensor_boxspline(3, 2, 4), 6, stream)
+    s.set_stiffness_phases(ids, Cp)
+    eps0 = np.eye(6)
+    prec = {"fp64": fh.FH_PREC_FP64, "fp32": fh.FH_PREC_FP32, "mixed": fh.FH_PREC_MIXED}
+    ref = golden_ceff("ceff_box3d.txt", "box3d")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
+
+    def step_fn(mode):
+        def step():
+            s.set_reference(None)                 # Gamma^p table (FP64, on the device)
+            return s.solve(eps0, tol=args.tol, max_iter=20000, precision=prec[mode])
+        return step
+
+    modes = [m for m in args.modes.split(",") if m]
+    if args.mode not in modes:
+        modes.insert(0, args.mode)
+    results, clocks = {}, None
+    for mode in [args.mode] + [m for m in modes if m != args.mode]:
+        head = mode == args.mode
+        steps = args.steps if head else (1 if mode == "fp64" else min(args.steps, 3))
+        warm = args.warmup if head else 1
+        if dist:
+            dist.barrier()
+        times, outs, ck = timed_steps(step_fn(mode), steps, warm, flush,
+                                      local_rank if (head and local_rank == 0) else None)
+        if head:
+            clocks = ck
+        total_ms = float(np.sum(times))
+        vox = sum(int(np.sum(o["iterations"])) * p.m for o in outs)
+        if dist:
+            total_ms, vox = reduce_over_ranks(dist, total_ms, vox, "cuda")
+        ce = s.get_ceff()
+        last = outs[-1]
+        results[mode] = {"value": vox / (total_ms * 1e-3), "ms_per_step": total_ms / steps, "steps": steps,
+                         "iterations": [int(x) for x in last["iterations"]], "status": int(last["status"]),
+                         "gpu_launches_per_step": int(last["kernel_launches"]) + 1,
+                         "ceff_rel_err_vs_converged_oracle": None if ref is None else frob_rel(ce, ref["ceff_converged"]),
+                         "ceff": ce.tolist()}
+
+    # the table build alone (one launch; FP64 ALU bound)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tab = []
+    for _ in range(5):
+        e0.record()
+        s.set_reference(None)
+        e1.record()
+        e1.synchronize()
+        tab.append(e0.elapsed_time(e1))
+    table_ms = float(np.median(tab))
+
+    # e2e through the public API: phase ids from pinned host memory in, every load's strain
+    # field and C_eff out to pinned host memory, copies inside the timed region
+    head = args.mode
+    ph_host = torch.from_numpy(ids).pin_memory()
+    E_host = torch.empty((6, 6, p.m), dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        s.set_stiffness_phases(ph_host, Cp)
+        step_fn(head)()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_vox = 0
+    for _ in range(args.steps):
+        s.set_stiffness_phases(ph_host, Cp)     # H2D: phase ids
+        out = step_fn(head)()
+        for L in range(6):
+            s.get_strain(L, E_host[L])          # D2H: strain fields
+        s.get_ceff()
+        e2e_vox += int(np.sum(out["iterations"])) * p.m
+    torch.cuda.synchronize()
+    e2e_t = time.perf_counter() - t0
+    e2e = {"value": e2e_vox / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(p.m + Cp.nbytes),
+           "d2h_bytes_per_step": int(E_host.numel() * 8 + 36 * 8)}
+
+    # HBM roofline of one FP32 iteration, its passes timed live with CUDA events on the
+    # solver's stream (fh_profile_passes); algorithmic bytes = read and write every
+    # strain field once + phase ids + the FP32 table
+    nhalf = len(p.half_freqs())
+    peak, peak_src = hbm_peak()
+    s.solve(eps0, tol=0.0, max_iter=3, precision=prec["fp32"])
+    ms = s.profile_passes(6, prec["fp32"], reps=20)
+    spec, field, tab32 = 6 * 6 * nhalf * 8, 6 * 6 * p.m * 4, 21 * nhalf * 4
+    pass_bytes = {"row_pass_warp6": 2 * spec + 2 * field + p.m, "line_pass_warp6_axis0_green": 2 * spec + tab32,
+                  "line_pass_warp6_axis1_forward": 2 * spec, "line_pass_warp6_axis1_inverse": 2 * spec}
+    passes = {k: {"ms": float(ms[i]), "bytes": int(b), "gbs": b / (ms[i] * 1e-3) / 1e9,
+                  "frac_of_hbm": b / (ms[i] * 1e-3) / 1e9 / peak} for i, (k, b) in enumerate(pass_bytes.items())}
+    it_ms = float(sum(ms[:4]))
+    algo = 2 * field + p.m + tab32
+    traffic = profile_traffic("ncu_iteration_fp32_box3d.md")
+    roofline = {"bound": "hbm", "kernel": "one FP32 iteration: row_pass_warp6 + line_pass_warp6 (axis 1 forward, "
+                "axis 0 + Green, axis 1 inverse)",
+                "achieved": algo / (it_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                "frac": algo / (it_ms * 1e-3) / 1e9 / peak, "traffic": traffic,
+                "algorithmic_bytes": int(algo), "moved_bytes_by_design": int(sum(pass_bytes.values())),
+                "moved_frac_of_hbm": sum(pass_bytes.values()) / (it_ms * 1e-3) / 1e9 / peak,
+                "duration_ms": it_ms, "peak_source": peak_src, "passes": passes,
+                "table_build": {"ms": table_ms, "bound": "alu (FP64)", "peak_tflops": FP64_PEAK_TFLOPS,
+                                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s"}}
+    # FP64 passes, for the plain-FP64 mode's bound
+    if "fp64" in modes:
+        s.solve(eps0, tol=0.0, max_iter=2, precision=prec["fp64"])
+        ms64 = s.profile_passes(6, prec["fp64"], reps=5)
+        roofline["fp64_iteration_ms"] = float(sum(ms64[:4]))
+    launches = results[head]["gpu_launches_per_step"] * args.steps
+    s.close()
+    return results, e2e, roofline, clocks, launches, table_ms
+
+
+def flops_per_launch_2d(g, nload, kind):
+    """Algorithmic FLOPs of one launch of a 2-D pass (5 N log2 N per complex FFT of
+    length N, half that for a real one; n_v^2 FMAs per point for the stress, 4 n_v^2
+    flops per half-spectrum frequency for the Green step)."""
     nv, L, dims = g["nv"], g["L"], g["dims"]
     m = g["m"]
     nrows = m // L
@@ -218,119 +437,47 @@ def flops_per_launch(g, nload, kind):
     return nload * (fft + nhalf * 4 * nv * nv)
 
 
-def run_gpu(args, rank, world, local_rank):
+def run_2d(fh, args):
+    """The anisotropic 2-D workload (dlvp_sheared): one step = table build + solve of the 3
+    loads to r <= tol, per precision mode; C_eff against tests/golden/ceff_dlvp_sheared.txt."""
     import torch
-    torch.cuda.set_device(local_rank)
-    import paper_1701_04685_gb300 as fh
-    fh.library()
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
     w = W.dlvp_sheared()
     p = fh.Pattern(w["M"])
     ids = W.phase_ids(p.points(), w["centres"], w["radii"])
     Cp = np.stack([fh.isotropic_stiffness(*fh.lame(E, nu), 2) for E, nu in w["phases"]])
-    eps0 = np.eye(3)
-    stream = torch.cuda.current_stream().cuda_stream
-    s = fh.Solver(p, fh.generator("dlvp", alpha=w["generator"]["alpha"]), 3, stream)
+    s = fh.Solver(p, fh.generator("dlvp", alpha=w["generator"]["alpha"]), 3, torch.cuda.current_stream().cuda_stream)
     s.set_stiffness_phases(ids, Cp)
     prec = {"fp64": fh.FH_PREC_FP64, "fp32": fh.FH_PREC_FP32, "mixed": fh.FH_PREC_MIXED}
-    Cref = ceff_reference()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
-
-    def step(mode):
-        s.set_reference(None)                     # Gamma^p table (FP64, on the device)
-        return s.solve(eps0, tol=args.tol, max_iter=20000, precision=prec[mode])
-
-    results = {}
-    clocks = None
+    path = os.path.join(GOLDEN, "ceff_dlvp_sheared.txt")
+    Cref = np.loadtxt(path) if os.path.exists(path) else None
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    steps = min(args.steps, 10)
+    out = {"workload": WORKLOAD_2D, "modes": {}}
     for mode in ("fp64", "fp32", "mixed"):
-        for _ in range(args.warmup):
-            step(mode)
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        if mode == args.mode and local_rank == 0:
-            clocks = Clocks(local_rank)
-        times, vox, launches, iters, path = [], 0, 0, None, None
-        t_wall = time.perf_counter()
-        for _ in range(args.steps):
-            flush.zero_()                         # L2 flushed between timed steps
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            out = step(mode)
-            e1.record()
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-            vox += int(np.sum(out["iterations"])) * p.m
-            launches += out["kernel_launches"] + 1  # + the table-build kernel
-            iters = out["iterations"]
-            path = (out["path"], out["cluster"])
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t_wall
-        if mode == args.mode and clocks is not None:
-            clocks = clocks.stop()
-        total_ms = float(np.sum(times))
-        if dist:
-            total_ms, vox = reduce_over_ranks(dist, total_ms, vox, "cuda")
+        def step():
+            s.set_reference(None)
+            return s.solve(np.eye(3), tol=args.tol, max_iter=20000, precision=prec[mode])
+        times, outs, _ = timed_steps(step, steps, min(args.warmup, 2), flush)
+        tot = float(np.sum(times))
+        vox = sum(int(np.sum(o["iterations"])) * p.m for o in outs)
         ce = s.get_ceff()
-        results[mode] = {"value": vox / (total_ms * 1e-3), "ms_per_step": total_ms / args.steps,
-                         "iterations": [int(x) for x in iters], "gpu_launches": launches,
-                         "path": "cluster-resident" if path[0] == 2 else "whole-GPU passes",
-                         "cluster_size": path[1], "ceff": ce.tolist(), "wall_s": wall,
-                         "ceff_rel_err_vs_converged_oracle":
-                             None if Cref is None else float(np.linalg.norm(ce - Cref) / np.linalg.norm(Cref))}
-
-    # e2e: through the public API with host buffers (pinned), copies inside the timed region
-    head = args.mode
-    ph_host = torch.from_numpy(ids).pin_memory()
-    E_host = torch.empty((3, 3, p.m), dtype=torch.float64).pin_memory()
-    for _ in range(2):
-        s.set_stiffness_phases(ph_host, Cp)
-        step(head)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    e2e_vox = 0
-    for _ in range(args.steps):
-        s.set_stiffness_phases(ph_host, Cp)     # H2D: phase ids
-        out = step(head)
-        for L in range(3):
-            s.get_strain(L, E_host[L])          # D2H: strain fields
-        s.get_ceff()
-        e2e_vox += int(np.sum(out["iterations"])) * p.m
-    torch.cuda.synchronize()
-    e2e_t = time.perf_counter() - t0
-    e2e = {"value": e2e_vox / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(p.m + 9 * 8 * 2 + Cp.nbytes),
-           "d2h_bytes_per_step": int(E_host.numel() * 8 + 9 * 8)}
-
-    # roofline of the dominant kernel of the headline mode, timed live with CUDA
-    # events on the solver's stream (fh_solve's elapsed_ms, or fh_profile_passes)
-    bulk = "fp64" if head == "fp64" else "fp32"
+        out["modes"][mode] = {"value": vox / (tot * 1e-3), "ms_per_step": tot / steps,
+                              "iterations": [int(x) for x in outs[-1]["iterations"]],
+                              "path": "cluster-resident" if outs[-1]["path"] == 2 else "whole-GPU passes",
+                              "cluster_size": int(outs[-1]["cluster"]),
+                              "ceff_rel_err_vs_converged_oracle": None if Cref is None else frob_rel(ce, Cref)}
+    # FP32 ALU roofline of the cluster kernel (one launch per solve)
     g = {"nv": 3, "L": p.dims[-1], "dims": p.dims, "m": p.m, "nhalf": len(p.half_freqs())}
-    per_iter = flops_per_launch(g, 1, "row") + flops_per_launch(g, 1, "green")
-    peak = measured_fp_peak(bulk)
-    if results[bulk]["path"] == "cluster-resident":
-        out = s.solve(eps0, tol=args.tol, max_iter=20000, precision=prec[bulk])
-        flops = per_iter * float(np.sum(out["iterations"]))
-        dur_ms = out["elapsed_ms"]
-        kernel = f"cluster_solve_2d<{'float' if bulk == 'fp32' else 'double'},3,{out['cluster']}> (one launch per solve, one cluster per load)"
-        passes = None
-    else:
-        step(bulk)
-        ms = s.profile_passes(3, prec[bulk], reps=50)
-        kinds = [("row_pass", ms[0], flops_per_launch(g, 3, "row")),
-                 ("line_pass_green", ms[1], flops_per_launch(g, 3, "green"))]
-        dom = max(kinds, key=lambda k: k[1])
-        kernel, dur_ms, flops = dom[0], dom[1], dom[2]
-        passes = {k[0]: k[1] for k in kinds}
-    achieved = flops / (dur_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak["tflops"],
-                "unit": "TFLOP/s", "frac": achieved / peak["tflops"], "traffic": None,
-                "peak_source": peak["source"] + " (of measured)", "duration_ms": dur_ms,
-                "algorithmic_flops": flops, "passes_ms": passes}
-    return results, e2e, roofline, clocks
+    per_iter = flops_per_launch_2d(g, 1, "row") + flops_per_launch_2d(g, 1, "green")
+    o = s.solve(np.eye(3), tol=args.tol, max_iter=20000, precision=prec["fp32"])
+    flops = per_iter * float(np.sum(o["iterations"]))
+    ach = flops / (o["elapsed_ms"] * 1e-3) / 1e12
+    out["roofline_fp32_cluster"] = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                    "frac": ach / FP32_PEAK_TFLOPS, "duration_ms": o["elapsed_ms"],
+                                    "peak_source": "nominal: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                                    "kernel": f"cluster_solve_2d<float,3,{o['cluster']}>"}
+    s.close()
+    return out
 
 
 def run_batched(fh, steps, cluster):
@@ -385,127 +532,6 @@ def run_batched(fh, steps, cluster):
                       "loads, working set > L2)", "gpu_launches": launches}
 
 
-def hbm_peak():
-    """Measured copy bandwidth of this pool's GB300s (GB/s), else the fallback figure."""
-    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    try:
-        with open(path) as f:
-            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (of measured)"
-    except (OSError, KeyError, ValueError):
-        return 6800.0, "fallback 6.8 TB/s (of fallback)"
-
-
-def run_box3d(fh, args):
-    """The 3-D workload: M = diag(n,n,n) (n = 128: m = 2 097 152), tensor-product
-    box spline of order 2 with alias radius 4, 50 spheres (seed 3) at contrast
-    50, the 6 Mandel unit loads.  The Gamma^p table is built once (a one-off
-    precompute, timed separately); one step is one solve of all 6 loads to
-    r <= tol.  Mixed and FP32 run `steps` steps, FP64 one.  Then the passes of
-    one iteration are timed alone (fh_profile_passes, CUDA events) and divided
-    into the bytes each must move: the HBM roofline of the 3-D kernels."""
-    import torch
-    n = args.box3d_n
-    w = W.box3d(n=n)
-    p = fh.Pattern(w["M"])
-    ids = W.phase_ids(p.points(), w["centres"], w["radii"])
-    Cp = np.stack([fh.isotropic_stiffness(*fh.lame(E, nu), 3) for E, nu in w["phases"]])
-    stream = torch.cuda.current_stream().cuda_stream
-    s = fh.Solver(p, fh.tensor_boxspline(3, 2, 4), 6, stream)
-    s.set_stiffness_phases(ids, Cp)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    s.set_reference(None)
-    e1.record()
-    e1.synchronize()
-    table_ms = e0.elapsed_time(e1)
-    eps0 = np.eye(6)
-    prec = {"fp64": fh.FH_PREC_FP64, "fp32": fh.FH_PREC_FP32, "mixed": fh.FH_PREC_MIXED}
-    modes, launches = {}, 0
-    wanted = [m for m in ("mixed", "fp32", "fp64") if m in args.box3d_modes.split(",")]
-    for mode, steps in [(m, args.steps if m != "fp64" else 1) for m in wanted]:
-        s.solve(eps0, tol=0.0, max_iter=5, precision=prec[mode])      # warm-up (graph capture)
-        times, out = [], None
-        for _ in range(steps):
-            e0.record()
-            out = s.solve(eps0, tol=args.tol, max_iter=20000, precision=prec[mode])
-            e1.record()
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-        it = [int(x) for x in out["iterations"]]
-        modes[mode] = {"time_to_tol_ms": float(np.median(times)), "iterations": it,
-                       "ms_per_iteration": float(np.median(times)) / max(it),
-                       "voxel_iterations_per_s": p.m * sum(it) / (float(np.median(times)) * 1e-3),
-                       "status": int(out["status"]), "load_status": [int(x) for x in out["load_status"]],
-                       "ceff": s.get_ceff().tolist()}
-        if mode == "mixed":
-            launches = out["kernel_launches"]
-    if "fp64" in modes:
-        C64 = np.array(modes["fp64"]["ceff"])
-        for mode in modes:
-            if mode != "fp64":
-                modes[mode]["ceff_rel_err_vs_fp64"] = float(np.linalg.norm(np.array(modes[mode]["ceff"]) - C64)
-                                                            / np.linalg.norm(C64))
-    # per-pass roofline
-    nhalf = len(p.half_freqs())
-    peak, peak_src = hbm_peak()
-    passes = {}
-    for mode, rb, cb in [x for x in (("fp32", 4, 8), ("fp64", 8, 16)) if x[0] in wanted]:
-        s.solve(eps0, tol=0.0, max_iter=3, precision=prec[mode])
-        ms = s.profile_passes(6, prec[mode], reps=20)
-        spec = 6 * 6 * nhalf * cb                       # all loads' half spectra, one way
-        field = 6 * 6 * p.m * rb                        # all loads' strain fields, one way
-        table = 21 * nhalf * rb
-        bytes_ = {"row_pass": 2 * spec + 2 * field + p.m, "axis0_green_pass": 2 * spec + table,
-                  "axis1_forward_pass": 2 * spec, "axis1_inverse_pass": 2 * spec}
-        names = list(bytes_)
-        passes[mode] = {k: {"ms": float(ms[i]), "bytes": int(bytes_[k]),
-                            "gbs": bytes_[k] / (ms[i] * 1e-3) / 1e9,
-                            "frac_of_hbm": bytes_[k] / (ms[i] * 1e-3) / 1e9 / peak} for i, k in enumerate(names)}
-        tot_b = sum(bytes_.values())
-        tot_ms = float(sum(ms))
-        # the method's own minimum per iteration: read and write every strain
-        # field once, the phase ids and the table once
-        algo = 6 * 6 * p.m * rb * 2 + p.m + table
-        passes[mode]["iteration"] = {"ms": tot_ms, "bytes": int(tot_b), "gbs": tot_b / (tot_ms * 1e-3) / 1e9,
-                                     "frac_of_hbm": tot_b / (tot_ms * 1e-3) / 1e9 / peak,
-                                     "algorithmic_bytes": int(algo),
-                                     "algorithmic_gbs": algo / (tot_ms * 1e-3) / 1e9}
-    s.close()
-    return {"workload": f"box3d: M=diag({n},{n},{n}) (m={p.m}, grid {p.dims}), box spline order 2 alias radius 4 "
-                        f"(729 aliases), 50 spheres r~U[0.05,0.1] seed 3, contrast 50, 6 Mandel unit loads, "
-                        f"tol {args.tol}",
-            "table_build_ms": table_ms, "modes": modes, "passes": passes, "hbm_peak_gbs": peak,
-            "hbm_peak_source": peak_src, "gpu_launches_mixed_step": launches,
-            "timing": "CUDA events on the solver's stream; working set (1.2 GB FP32) larger than L2"}
-
-
-def measured_fp_peak(mode):
-    """Dense peak of the arithmetic type measured here with cuBLAS (DGEMM / SGEMM without TF32)."""
-    import torch
-    dt = torch.float64 if mode == "fp64" else torch.float32
-    prev = torch.backends.cuda.matmul.allow_tf32
-    torch.backends.cuda.matmul.allow_tf32 = False
-    n = 8192 if mode == "fp64" else 8192
-    a = torch.randn(n, n, dtype=dt, device="cuda")
-    b = torch.randn(n, n, dtype=dt, device="cuda")
-    for _ in range(2):
-        torch.matmul(a, b)
-    torch.cuda.synchronize()
-    best = 1e30
-    for _ in range(5):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        torch.matmul(a, b)
-        e1.record()
-        e1.synchronize()
-        best = min(best, e0.elapsed_time(e1))
-    torch.backends.cuda.matmul.allow_tf32 = prev
-    del a, b
-    return {"tflops": 2 * n ** 3 / (best * 1e-3) / 1e12,
-            "source": f"measured here: cuBLAS {'DGEMM' if mode == 'fp64' else 'SGEMM (no TF32)'} {n}^3, best of 5"}
-
-
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -514,35 +540,41 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank)
         return
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist = None
     if world > 1:
-        import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     from paper_1701_04685_gb300 import build
     build.build()
-    if args.only_box3d:
-        import torch
-        torch.cuda.set_device(local_rank)
-        import paper_1701_04685_gb300 as fh
-        box = run_box3d(fh, args)
-        if rank == 0:
-            print(json.dumps({"box3d": box}), flush=True)
+    import paper_1701_04685_gb300 as fh
+    fh.library()
+    if args.ncu_iteration:
+        w = W.box3d()
+        p = fh.Pattern(w["M"])
+        s = fh.Solver(p, fh.tensor_boxspline(3, 2, 4), 6, torch.cuda.current_stream().cuda_stream)
+        s.set_stiffness_phases(W.phase_ids(p.points(), w["centres"], w["radii"]),
+                               np.stack([fh.isotropic_stiffness(*fh.lame(E, nu), 3) for E, nu in w["phases"]]))
+        s.set_reference(None)
+        s.solve(np.eye(6), tol=0.0, max_iter=3, precision=fh.FH_PREC_FP32)
+        s.profile_passes(6, fh.FH_PREC_FP32, reps=1)
+        torch.cuda.synchronize()
+        s.close()
         return
-    results, e2e, roofline, clocks = run_gpu(args, rank, world, local_rank)
-    batched = None
-    if not args.no_batched:
-        import paper_1701_04685_gb300 as fh
+    results, e2e, roofline, clocks, launches, table_ms = run_headline(fh, args, dist, local_rank)
+    two_d = batched = None
+    if not args.only_headline and not args.no_2d:
+        two_d = run_2d(fh, args)
+    if not args.only_headline and not args.no_batched:
         batched = run_batched(fh, min(args.steps, 3), args.batch_cluster)
-    box = None
-    if not args.no_box3d:
-        import paper_1701_04685_gb300 as fh
-        box = run_box3d(fh, args)
     if rank != 0:
+        if dist:
+            dist.destroy_process_group()
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = oracle_sample(W.dlvp_sheared(), args.cpu_seconds)
+        cpu = cpu_baseline_box3d()
     head = results[args.mode]
     line = {
         "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -551,22 +583,21 @@ def main():
         "precision_mode": args.mode,
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "mode": args.mode, "tol": args.tol,
-                   "l2": "flushed between timed steps (256 MB write)",
+                   "l2": "flushed between timed steps (256 MB write); working set 1.2 GB > L2",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "iterations_per_load": head["iterations"]},
+                   "iterations_per_load": head["iterations"], "table_build_ms": table_ms},
         "time_to_tol_ms": head["ms_per_step"],
         "modes": results,
-        "batched": batched,
-        "box3d": box,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": head["gpu_launches"],
+        "gpu_launches": launches,
         "clocks": clocks,
+        "dlvp_sheared_2d": two_d,
+        "batched": batched,
     }
     print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
+    if dist:
         dist.destroy_process_group()
 
 

@@ -52,24 +52,34 @@ class BruteTransform:
 
 
 class SNFTransform:
-    """Pattern DFT as a d-dimensional FFT on the Smith-normal-form grid."""
+    """Pattern DFT as a d-dimensional FFT on the Smith-normal-form grid.
 
-    def __init__(self, M):
+    ``workers`` = None uses numpy's FFT; an integer uses scipy.fft (the same
+    pocketfft algorithm) with that many threads, for timing the oracle on all
+    host cores.  Both compute the same plain DFT."""
+
+    def __init__(self, M, workers=None):
         g = lattice.snf_grid(M)
         self.dims = g["dims"]
         self.points = g["points"]
         self.freqs = g["freqs"]
         self.D = g["D"]
         self.m = self.D
+        self.workers = workers
+
+    def _fftn(self, x, inverse):
+        axes = tuple(range(len(self.dims)))
+        if self.workers is None:
+            return (np.fft.ifftn if inverse else np.fft.fftn)(x, axes=axes)
+        import scipy.fft
+        return (scipy.fft.ifftn if inverse else scipy.fft.fftn)(x, axes=axes, workers=self.workers)
 
     def fwd(self, x):
-        nd = len(self.dims)
-        y = np.fft.fftn(x.reshape(self.dims + list(x.shape[1:])), axes=tuple(range(nd)))
+        y = self._fftn(x.reshape(self.dims + list(x.shape[1:])), False)
         return y.reshape(x.shape)
 
     def inv(self, X):
-        nd = len(self.dims)
-        y = np.fft.ifftn(X.reshape(self.dims + list(X.shape[1:])), axes=tuple(range(nd)))
+        y = self._fftn(X.reshape(self.dims + list(X.shape[1:])), True)
         return y.reshape(X.shape)
 
 

@@ -875,11 +875,31 @@ __device__ __forceinline__ int moment_index3(int e1, int e2) {
   return T[e1][e2];
 }
 
+// mirror: M diagonal and the Smith grid's axes are M's axes (Fmap a signed
+// permutation, mirror_geo[k] = the geometric axis of storage axis k).  The
+// symbols are even per axis and the alias sets mirror with u_i -> -u_i, so
+// reflecting h_g -> -h_g multiplies the Mandel entry of (i,j),(p,q) by
+// (-1)^(how often g occurs among i, j, p, q).  Threads then cover only the
+// storage frequencies with l_k <= dims_k / 2 on the full (non-half) axes and
+// write every mirror image: 1/2 (2-D) or 1/4 (3-D) of the alias sums.
 template <int DIM>
 __global__ void __launch_bounds__(128) green_table_iso(GreenParams P, double* __restrict__ G64,
-                                                       float* __restrict__ G32, int* err) {
-  const long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (f >= P.nhalf) return;
+                                                       float* __restrict__ G32, int* err, int mirror,
+                                                       int mirror_geo0, int mirror_geo1) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long f = idx;
+  long long l0 = 0, l1 = 0, l2 = 0;  // storage coordinates when mirroring
+  if (mirror) {
+    const long long n0 = P.dims[0] / 2 + 1, n1 = DIM == 3 ? P.dims[1] / 2 + 1 : 1;
+    if (idx >= n0 * n1 * P.H) return;
+    l2 = idx % P.H;
+    const long long t = idx / P.H;
+    l1 = DIM == 3 ? t % n1 : 0;
+    l0 = DIM == 3 ? t / n1 : t;
+    f = DIM == 3 ? (l0 * P.dims[1] + l1) * P.H + l2 : l0 * P.H + l2;
+  } else if (f >= P.nhalf) {
+    return;
+  }
   long long h[3], u[3];
   reduce_frequency(P, f, h, u);
   const int R = (P.kind == FH_GEN_BOXSPLINE) ? P.radius : 1;
@@ -994,6 +1014,22 @@ __global__ void __launch_bounds__(128) green_table_iso(GreenParams P, double* __
   const double c4 = 0.25 / P.mu0;
   const double cb = (P.lam0 + P.mu0) / (P.mu0 * (P.lam0 + 2.0 * P.mu0));
   const double s2 = 1.41421356237309504880;
+  // mirror images (s0, s1) of the storage frequency; (0, 0) is f itself
+  long long fm[4];
+  fm[0] = f;
+  fm[1] = fm[2] = fm[3] = -1;
+  if (mirror) {
+    const long long m0 = (P.dims[0] - l0) % P.dims[0];
+    const long long m1 = DIM == 3 ? (P.dims[1] - l1) % P.dims[1] : 0;
+    const bool d0 = m0 != l0, d1 = DIM == 3 && m1 != l1;
+    if (DIM == 3) {
+      if (d0) fm[1] = (m0 * P.dims[1] + l1) * P.H + l2;
+      if (d1) fm[2] = (l0 * P.dims[1] + m1) * P.H + l2;
+      if (d0 && d1) fm[3] = (m0 * P.dims[1] + m1) * P.H + l2;
+    } else if (d0) {
+      fm[1] = m0 * P.H + l2;
+    }
+  }
   int t = 0;
   for (int a = 0; a < P.nv; ++a) {
     int i, j;
@@ -1006,8 +1042,15 @@ __global__ void __launch_bounds__(128) green_table_iso(GreenParams P, double* __
       const double lin = (i == p ? A[j][q] : 0.0) + (i == q ? A[j][p] : 0.0) + (j == p ? A[i][q] : 0.0) +
                          (j == q ? A[i][p] : 0.0);
       const double v = sa * sb * (c4 * lin - cb * moment(i, j, p, q));
-      G64[(size_t)t * P.nhalf + f] = v;
-      G32[(size_t)t * P.nhalf + f] = (float)v;
+      const int c0 = (i == mirror_geo0) + (j == mirror_geo0) + (p == mirror_geo0) + (q == mirror_geo0);
+      const int c1 = (i == mirror_geo1) + (j == mirror_geo1) + (p == mirror_geo1) + (q == mirror_geo1);
+      for (int r = 0; r < 4; ++r) {
+        if (fm[r] < 0) continue;
+        const int flips = ((r & 1) ? c0 : 0) + ((r & 2) ? c1 : 0);
+        const double vr = (flips & 1) ? -v : v;
+        G64[(size_t)t * P.nhalf + fm[r]] = vr;
+        G32[(size_t)t * P.nhalf + fm[r]] = (float)vr;
+      }
       ++t;
     }
   }

@@ -696,6 +696,28 @@ bool closed_form_table(const fh_solver* s, const double* c0, fh::GreenParams* GP
   return true;
 }
 
+// Mirror symmetry of the table (green_table_iso): M diagonal and every Smith
+// axis one of M's axes (each row of Fmap a single +-1), all d axes non-trivial.
+// geo[k] receives the geometric axis of the full storage axes k = 0 .. d-2.
+bool mirror_axes(const fh_solver* s, int* geo) {
+  const int d = s->g.d;
+  if (s->g.nd != d) return false;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j)
+      if (i != j && s->P.M[i][j] != 0) return false;
+  for (int k = 0; k < d; ++k) {
+    int axis = -1, nonzero = 0;
+    for (int i = 0; i < d; ++i) {
+      const long long v = s->P.Fmap[k][i];
+      if (v != 0) { ++nonzero; axis = i; }
+      if (v != 0 && v != 1 && v != -1) return false;
+    }
+    if (nonzero != 1) return false;
+    if (k < d - 1) geo[k] = axis;
+  }
+  return true;
+}
+
 void mandel_to_c4(const double* Cm, int d, double* C4) {
   const int I2[3] = {0, 1, 0}, J2[3] = {0, 1, 1};
   const int I3[6] = {0, 1, 2, 1, 0, 0}, J3[6] = {0, 1, 2, 2, 2, 1};
@@ -1085,8 +1107,15 @@ fh_status fh_set_reference(fh_solver* s, const double* C0) {
   CK(cudaMemsetAsync(s->err, 0, sizeof(int), s->work));
   const int blocks = (int)((s->g.nhalf + 127) / 128);
   if (closed_form_table(s, c0, &GP)) {
-    if (d == 2) fh::green_table_iso<2><<<blocks, 128, 0, s->work>>>(GP, s->G64, s->G32, s->err);
-    else fh::green_table_iso<3><<<blocks, 128, 0, s->work>>>(GP, s->G64, s->G32, s->err);
+    int geo[2] = {-1, -1};
+    const bool mirror = mirror_axes(s, geo);
+    long long nthreads = s->g.nhalf;
+    if (mirror) nthreads = (long long)(s->g.dims[0] / 2 + 1) * (d == 3 ? s->g.dims[1] / 2 + 1 : 1) * s->g.H;
+    const int mblocks = (int)((nthreads + 127) / 128);
+    if (d == 2)
+      fh::green_table_iso<2><<<mblocks, 128, 0, s->work>>>(GP, s->G64, s->G32, s->err, mirror, geo[0], geo[1]);
+    else
+      fh::green_table_iso<3><<<mblocks, 128, 0, s->work>>>(GP, s->G64, s->G32, s->err, mirror, geo[0], geo[1]);
   } else {
     fh::green_table<<<blocks, 128, 0, s->work>>>(GP, s->G64, s->G32, s->err);
   }

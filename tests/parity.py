@@ -1,6 +1,9 @@
 """Shared set-up for the GPU parity tests: one workload built independently on the
 oracle side and on the product side, plus the permutation between their point
 orders (matched on the exact integer numerators of the pattern points)."""
+import os
+import sys
+
 import numpy as np
 
 import workloads as W
@@ -150,32 +153,10 @@ def det(M):
     return abs(OL.det_int(M))
 
 
-def read_golden_blocks(path):
-    """Parse a file of tests/golden/make_ceff_configs.py: {block name: {"iterations_to_1e-6": [...],
-    "iterations_to_1e-11": [...], "ceff_converged": array, "ceff_at_1e-6": array}}."""
-    blocks, cur, key = {}, None, None
-    for line in open(path):
-        line = line.strip()
-        if not line or line.startswith("#"):
-            continue
-        if line.startswith("["):
-            cur = blocks.setdefault(line[1:-1], {})
-            key = None
-            continue
-        head = line.split()[0]
-        if head.startswith("iterations"):
-            cur[head] = [int(v) for v in line.split()[1:]]
-        elif head.startswith("ceff"):
-            key = head
-            cur[key] = []
-        else:
-            cur[key].append([float(v) for v in line.split()])
-    for b in blocks.values():
-        for k in ("ceff_converged", "ceff_at_1e-6"):
-            b[k] = np.array(b[k])
-    return blocks
-
-
 def frob_rel(a, b):
     """Relative Frobenius distance ||a - b|| / ||b||."""
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+from golden_io import read_golden_blocks  # noqa: E402,F401

@@ -58,6 +58,22 @@ def test_brute_dft_route_equals_snf_route(M, rng):
     assert ob["imag_max"].max() < 1e-13
 
 
+def test_threaded_fft_route_equals_literal_dft(rng):
+    """The scipy.fft route (workers > 1), used to time the oracle on all host cores,
+    is the same DFT as the literal matrix of Eq. (Fouriermatrix)."""
+    M = [[6, 2], [0, 5]]
+    Tb = scheme.BruteTransform(M)
+    Ts = scheme.SNFTransform(M, workers=2)
+    idx = {tuple(p): i for i, p in enumerate(Tb.points.tolist())}
+    perm = np.array([idx[tuple(p)] for p in Ts.points.tolist()])
+    fidx = {tuple(h): i for i, h in enumerate(Tb.freqs.tolist())}
+    fperm = np.array([fidx[tuple(h)] for h in Ts.freqs.tolist()])
+    x = rng.standard_normal((Tb.m, 3))
+    assert np.abs(Tb.fwd(x)[fperm] - Ts.fwd(x[perm])).max() < 1e-12
+    X = rng.standard_normal((Tb.m, 3)) + 1j * rng.standard_normal((Tb.m, 3))
+    assert np.abs(Tb.inv(X)[perm] - Ts.inv(X[fperm])).max() < 1e-12
+
+
 def test_forms_A_and_B_agree_iff_dirichlet():
     """Remark constants: eps - Gamma^p C0 eps = eps0 holds iff Dirichlet, so the paper's
     form (A) and the strain-update form (B) give the same iterates only then."""
