@@ -136,6 +136,21 @@ typedef struct {
                       iterations of these loads and use the fastest from then
                       on (see fh_get_tuning).  The trials overwrite the
                       strain before the actual solve starts from E = 0.      */
+  int method;      /* 0: the fixed point of Sec. 4 (Basic Scheme).
+                      1: BiCGStab (van der Vorst 1992) on the same discrete
+                      equation, (I + Gamma^p (C - C0)) E = -Gamma^p (C - C0)
+                      eps0 (the Krylov solvers the paper's introduction cites),
+                      two operator applications per iteration, on the
+                      whole-GPU passes (path 0 or 1; path 2 gives
+                      FH_ERR_UNSUPPORTED), form 0, tune 0.  It stops by the
+                      same rule: the fixed point's step from E is b - A E, so
+                      a load stops after the first iteration with
+                      |b - A E| <= tol |E + eps0|; iterations count BiCGStab
+                      iterations and the residual history holds that ratio.
+                      With FH_PREC_MIXED the FP32 BiCGStab phase aims at
+                      tol / 2 (its recursively updated residual drifts from
+                      the true one) and the FP64 phase is the fixed point, as
+                      for method 0.                                           */
 } fh_solve_opts;
 
 typedef struct {

@@ -45,7 +45,7 @@ class fh_generator(C.Structure):
 class fh_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("precision", C.c_int),
                 ("init", C.c_int), ("chunk", C.c_int), ("path", C.c_int), ("cluster", C.c_int),
-                ("form", C.c_int), ("tune", C.c_int)]
+                ("form", C.c_int), ("tune", C.c_int), ("method", C.c_int)]
 
 
 class fh_result(C.Structure):
@@ -295,15 +295,16 @@ class Solver:
             _check(library().fh_set_reference(self._h, _ptr(C0)))
 
     def solve(self, eps0, tol=1e-8, max_iter=1000, precision=FH_PREC_FP64, init=0, chunk=0, path=0, cluster=0,
-              form=0, tune=0):
+              form=0, tune=0, method=0):
         """path: 0 automatic, 1 whole-GPU passes, 2 cluster-resident (2-axis grids);
         form: 0 Eq. (pde_coefficients), 1 the variational discretisation;
-        tune: 1 picks path and cluster size by timing them (see fh_get_tuning)."""
+        tune: 1 picks path and cluster size by timing them (see fh_get_tuning);
+        method: 0 the fixed point, 1 BiCGStab on the same equation."""
         eps0 = np.ascontiguousarray(np.atleast_2d(np.asarray(eps0, dtype=np.float64)))
         if eps0.ndim != 2 or eps0.shape[1] != self.nv:
             raise ValueError(f"eps0: need shape (n_L, {self.nv}), got {eps0.shape}")
         opts = fh_solve_opts(float(tol), int(max_iter), int(precision), int(init), int(chunk), int(path),
-                             int(cluster), int(form), int(tune))
+                             int(cluster), int(form), int(tune), int(method))
         res = fh_result()
         rc = library().fh_solve(self._h, eps0.shape[0], _ptr(eps0), C.byref(opts), C.byref(res))
         _check(rc, ok=(FH_OK, FH_NOT_CONVERGED, FH_DIVERGED, FH_NONFINITE))
@@ -365,7 +366,7 @@ class Solver:
 
 
 def solve_batch(solvers, eps0s, tol=1e-6, max_iter=20000, precision=FH_PREC_MIXED, init=0, chunk=0, path=0,
-                cluster=0, form=0):
+                cluster=0, form=0, method=0):
     """fh_solve_batch over Solver objects; eps0s[i] is solver i's (n_L, n_v) strains.  With path and
     cluster automatic, solvers tuned before (Solver.solve(..., tune=1)) keep their tuned choice."""
     n = len(solvers)
@@ -379,7 +380,7 @@ def solve_batch(solvers, eps0s, tol=1e-6, max_iter=20000, precision=FH_PREC_MIXE
     nl = (C.c_int * n)(*[e.shape[0] for e in e0])
     ptrs = (C.c_void_p * n)(*[e.ctypes.data for e in e0])
     opts = fh_solve_opts(float(tol), int(max_iter), int(precision), int(init), int(chunk), int(path), int(cluster),
-                         int(form), 0)
+                         int(form), 0, int(method))
     res = (fh_result * n)()
     rc = library().fh_solve_batch(hs, n, nl, ptrs, C.byref(opts), res)
     _check(rc, ok=(FH_OK, FH_NOT_CONVERGED, FH_DIVERGED, FH_NONFINITE))

@@ -102,6 +102,7 @@ template <typename T> struct ResAcc;
 template <> struct ResAcc<double> {
   double s = 0.0;
   __device__ __forceinline__ void add_sq(double a) { s = fma(a, a, s); }
+  __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
   __device__ __forceinline__ void add(double v) { s += v; }
   __device__ __forceinline__ double value() const { return s; }
 };
@@ -111,6 +112,15 @@ template <> struct ResAcc<float> {
     const float p = a * a;
     const float e = fmaf(a, a, -p);        // a*a = p + e exactly
     const float s = hi + p;                 // TwoSum(hi, p)
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (p - bp);
+    hi = s;
+    lo += err + e;
+  }
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);        // a*b = p + e exactly
+    const float s = hi + p;
     const float bp = s - hi;
     const float err = (hi - (s - bp)) + (p - bp);
     hi = s;
@@ -248,12 +258,19 @@ __device__ void advance_state(LoadState& s, Control* ctl, double* hist, int load
 // the registers and spilled, measured slower)
 template <typename T> struct PassOcc { static constexpr int value = 1; };
 
-template <typename T, int NV, bool FIRST>
+// KINV (with FIRST = false): the inverse half of an operator application for
+// the Krylov solver.  The inverse transform gives y = -Gamma^p tau of the
+// field X (= E) whose stress the previous FIRST pass transformed; the pass
+// writes W = X - y = (I + Gamma^p (C - C0)) X to Wout and the block sums of
+// W . Yaux (Yaux = X when null) and W . W to partials, and does nothing else.
+template <typename T, int NV, bool FIRST, bool KINV = false>
 __global__ void __launch_bounds__(256, PassOcc<T>::value) row_pass(GridInfo g, DevPlan plan, const cplx<T>* __restrict__ tw,
                                                 T* __restrict__ E, cplx<T>* __restrict__ S,
                                                 const uint8_t* __restrict__ phase, const T* __restrict__ dC,
                                                 Control* ctl, LoadState* st, double* __restrict__ partials,
-                                                double* __restrict__ hist, int rpb, int blocks_per_load) {
+                                                double* __restrict__ hist, int rpb, int blocks_per_load,
+                                                T* __restrict__ Wout = nullptr, const T* __restrict__ Yaux = nullptr) {
+  static_assert(!(FIRST && KINV), "the inverse-only pass follows a transform");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
   __shared__ int s_skip;
@@ -331,7 +348,23 @@ __global__ void __launch_bounds__(256, PassOcc<T>::value) row_pass(GridInfo g, D
     //    (variational form: E_new = E_old + update, tau = C:(E_new + eps0))
     const T scale = (T)g.inv_m;
     const bool incremental = ctl->form == 1;
-    for (int idx = threadIdx.x; idx < nrow * L; idx += blockDim.x) {
+    if constexpr (KINV) {
+      const size_t ob = (size_t)load * NV * g.m + row0 * L;
+      for (int idx = threadIdx.x; idx < nrow * L; idx += blockDim.x) {
+        const int r = fdiv(idx, fL), x = idx - r * L;
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+          const int f = r * NV + c;
+          const cplx<T> zz = Z[(f >> 1) * Lp + padi<PS>(x)];
+          const size_t o = ob + (size_t)c * cstrE + r * L + x;
+          const T w = E[o] - ((f & 1) ? zz.y : zz.x) * scale;
+          Wout[o] = w;
+          acc_d.add_prod(w, Yaux ? Yaux[o] : E[o]);
+          acc_n.add_sq(w);
+        }
+      }
+    }
+    for (int idx = threadIdx.x; idx < (KINV ? 0 : nrow * L); idx += blockDim.x) {
       const int r = fdiv(idx, fL), x = idx - r * L;
       T* ep = Eb + r * L + x;
       T en[NV];
@@ -362,10 +395,12 @@ __global__ void __launch_bounds__(256, PassOcc<T>::value) row_pass(GridInfo g, D
       }
     }
     // odd number of real lines: the last pair's imaginary part is zero
-    if (nreal & 1) {
+    if (!KINV && (nreal & 1)) {
       for (int x = threadIdx.x; x < L; x += blockDim.x) Z[(npair - 1) * Lp + padi<PS>(x)].y = T(0);
     }
     __syncthreads();
+    if (KINV) goto partial_sums;
+    {
     // 4. forward FFT
     cplx<T>* Zf = fft_lines_pp<-1, T, PS>(Z, Zo, npair, Lp, plan, tw);
     // 5. split into the two half spectra A = (Z_k + conj Z_{L-k})/2, B = (Z_k - conj Z_{L-k})/(2i)
@@ -386,11 +421,20 @@ __global__ void __launch_bounds__(256, PassOcc<T>::value) row_pass(GridInfo g, D
         Sw[cb * cstrS + rbb * H + k] = B;
       }
     }
+    }
   }
+partial_sums:
   if (FIRST) return;
   // 6. partial sums of this block
   const double d2 = block_sum_acc(acc_d, red);
   const double n2 = block_sum_acc(acc_n, red);
+  if (KINV) {
+    if (threadIdx.x == 0) {
+      partials[2 * (size_t)blockIdx.x] = d2;
+      partials[2 * (size_t)blockIdx.x + 1] = n2;
+    }
+    return;
+  }
   __shared__ unsigned int s_ticket;
   if (threadIdx.x == 0) {
     partials[2 * (size_t)blockIdx.x] = d2;

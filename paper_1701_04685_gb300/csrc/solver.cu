@@ -20,6 +20,7 @@
 #include "cluster.cuh"
 #include "warprow.cuh"
 #include "linewarp.cuh"
+#include "krylov.cuh"
 
 namespace fh {
 static thread_local std::string g_err;
@@ -57,7 +58,7 @@ struct Axis {
 };
 
 struct GraphEntry {
-  int prec, nload, chunk;
+  int prec, nload, chunk, method;
   cudaGraphExec_t exec;
 };
 
@@ -125,6 +126,14 @@ struct fh_solver {
   fh::ClusterTask* qtasks = nullptr;                    // cluster-kernel task list of a single solve
   unsigned int* qnext = nullptr;
   fh::ClusterTask* h_tasks = nullptr;                   // pinned staging of that list
+  // BiCGStab (fh_solve_opts.method = 1): fields r, rhat, p, v, s, t per bulk
+  // precision (allocated on first use), scalars, block sums, and a copy of
+  // the control block with a zero macroscopic strain for operator applications
+  int method = 0;
+  void* kbuf[2] = {nullptr, nullptr};
+  fh::KrylovScal* ksc = nullptr;
+  double* kpart = nullptr;
+  Control* ctl0 = nullptr;
 };
 
 namespace {
@@ -336,6 +345,8 @@ cudaError_t set_warp_attrs(fh_solver* s, int prec, size_t rs) {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(fh::row_pass_warp6<T, P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(fh::row_pass_warp6<T, P, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs);
+  if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s->warp_res[prec], fh::row_pass_warp6<T, P, false>,
                                                        fh::kWarpRowThreads, rs);
 }
@@ -359,6 +370,7 @@ fh_status set_smem_attrs_nv(fh_solver* s, int prec) {
   if (s->row_warp[prec] == 0) {
     CK(cudaFuncSetAttribute(fh::row_pass<T, NV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
     CK(cudaFuncSetAttribute(fh::row_pass<T, NV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
+    CK(cudaFuncSetAttribute(fh::row_pass<T, NV, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
   } else if constexpr (sizeof(T) == 4) {
     switch (s->row_warp[prec]) {
       case 1: CK((set_warp_attrs<T, 1>(s, prec, rs))); break;
@@ -401,7 +413,7 @@ fh_status set_smem_attrs(fh_solver* s, int prec) {
 template <typename T>
 fh_status get_graph(fh_solver* s, int prec, int nload, int chunk, cudaGraphExec_t* out) {
   for (auto& e : s->graphs)
-    if (e.prec == prec && e.nload == nload && e.chunk == chunk) {
+    if (e.prec == prec && e.nload == nload && e.chunk == chunk && e.method == 0) {
       *out = e.exec;
       return FH_OK;
     }
@@ -419,7 +431,7 @@ fh_status get_graph(fh_solver* s, int prec, int nload, int chunk, cudaGraphExec_
     fh::set_error(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
     return FH_ERR_CUDA;
   }
-  s->graphs.push_back({prec, nload, chunk, exec});
+  s->graphs.push_back({prec, nload, chunk, 0, exec});
   *out = exec;
   return FH_OK;
 }
@@ -454,6 +466,154 @@ fh_status run_solve(fh_solver* s, int prec, int nload, int chunk, int max_iter, 
   CK(cudaGetLastError());
   CK(cudaEventRecord(s->ev1, s->work));
   *launches = 2 + launched * (1 + line_launches_per_iter(s->g));
+  return FH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// BiCGStab on the pass path (see krylov.cuh)
+// ---------------------------------------------------------------------------
+constexpr int kKryBpl = 128;  // blocks per load of the vector kernels
+
+template <typename T>
+T* kry_field(fh_solver* s, int prec, int which) {
+  return reinterpret_cast<T*>(s->kbuf[prec == FH_PREC_FP64 ? 0 : 1]) + (size_t)which * s->nload_max * s->g.nv * s->g.m;
+}
+enum { KR = 0, KRH = 1, KP = 2, KV = 3, KS = 4, KT = 5 };
+
+template <typename T>
+const T* dC_form0(const fh_solver* s);
+template <>
+const double* dC_form0<double>(const fh_solver* s) { return s->dC64; }
+template <>
+const float* dC_form0<float>(const fh_solver* s) { return s->dC32; }
+
+// Row pass on an explicit field X with an explicit control block: FIRST (stress
+// of X + ctl's eps0, forward transform) or KINV (Wout = X - inverse transform,
+// block sums of Wout . Yaux and Wout . Wout).  Returns the blocks per load.
+template <typename T, bool FIRST, bool KINV>
+int enqueue_row_x(fh_solver* s, int prec, int nload, T* X, Control* ctl, T* Wout, const T* Yaux) {
+  using C = typename fh::cplx_t<T>::type;
+  const GridInfo& g = s->g;
+  C* S = reinterpret_cast<C*>(s->S);
+  const int last = g.nd - 1;
+  if constexpr (sizeof(T) == 4) {
+    const int P = s->row_warp[prec];
+    if (P > 0) {
+      const int resident = std::max(1, s->warp_res[prec]) * std::max(1, s->sms);
+      const int bpl = std::max(1, std::min(s->row_bpl[prec], resident / nload));
+      const unsigned blocks = nload * bpl;
+      const size_t sm = s->row_smem[prec];
+      const C* tw = twp<T>(s->ax[last]);
+      switch (P) {
+        case 1: fh::row_pass_warp6<T, 1, FIRST, KINV><<<blocks, fh::kWarpRowThreads, sm, s->work>>>(g, tw, X, S, s->phase, dC_form0<T>(s), ctl, s->st, s->partials, s->hist, bpl, Wout, Yaux); break;
+        case 2: fh::row_pass_warp6<T, 2, FIRST, KINV><<<blocks, fh::kWarpRowThreads, sm, s->work>>>(g, tw, X, S, s->phase, dC_form0<T>(s), ctl, s->st, s->partials, s->hist, bpl, Wout, Yaux); break;
+        case 4: fh::row_pass_warp6<T, 4, FIRST, KINV><<<blocks, fh::kWarpRowThreads, sm, s->work>>>(g, tw, X, S, s->phase, dC_form0<T>(s), ctl, s->st, s->partials, s->hist, bpl, Wout, Yaux); break;
+        default: fh::row_pass_warp6<T, 8, FIRST, KINV><<<blocks, fh::kWarpRowThreads, sm, s->work>>>(g, tw, X, S, s->phase, dC_form0<T>(s), ctl, s->st, s->partials, s->hist, bpl, Wout, Yaux); break;
+      }
+      return bpl;
+    }
+  }
+  const int blocks = nload * s->row_bpl[prec];
+  if (g.nv == 3)
+    fh::row_pass<T, 3, FIRST, KINV><<<blocks, kThreads, s->row_smem[prec], s->work>>>(
+        g, s->ax[last].plan, twp<T>(s->ax[last]), X, S, s->phase, dC_form0<T>(s), ctl, s->st, s->partials, s->hist,
+        s->rpb[prec], s->row_bpl[prec], Wout, Yaux);
+  else
+    fh::row_pass<T, 6, FIRST, KINV><<<blocks, kThreads, s->row_smem[prec], s->work>>>(
+        g, s->ax[last].plan, twp<T>(s->ax[last]), X, S, s->phase, dC_form0<T>(s), ctl, s->st, s->partials, s->hist,
+        s->rpb[prec], s->row_bpl[prec], Wout, Yaux);
+  return s->row_bpl[prec];
+}
+
+// W = A X = X + Gamma^p (C - C0) X (the stress with ctl's eps0: zero for the
+// operator, eps0 for the start), with the block sums of W . Yaux and W . W;
+// returns the blocks per load of those sums
+template <typename T>
+int enqueue_apply(fh_solver* s, int prec, int nload, T* X, Control* ctl, T* W, const T* Yaux) {
+  enqueue_row_x<T, true, false>(s, prec, nload, X, ctl, nullptr, nullptr);
+  enqueue_line_passes<T>(s, prec, nload);
+  return enqueue_row_x<T, false, true>(s, prec, nload, X, ctl, W, Yaux);
+}
+
+// one BiCGStab iteration of every load that has not stopped
+template <typename T>
+void enqueue_bicgstab_iteration(fh_solver* s, int prec, int nload) {
+  const long long n = (long long)s->g.nv * s->g.m;
+  T* x = Eptr<T>(s);
+  T *r = kry_field<T>(s, prec, KR), *rh = kry_field<T>(s, prec, KRH), *p = kry_field<T>(s, prec, KP);
+  T *v = kry_field<T>(s, prec, KV), *sv = kry_field<T>(s, prec, KS), *t = kry_field<T>(s, prec, KT);
+  const unsigned vb = nload * kKryBpl;
+  fh::kry_update_p<T><<<vb, fh::kKryThreads, 0, s->work>>>(p, r, v, s->ksc, s->st, n, kKryBpl);
+  int bpl = enqueue_apply<T>(s, prec, nload, p, s->ctl0, v, rh);                       // v = A p
+  fh::kry_scalars<1><<<1, fh::kKryThreads, 0, s->work>>>(s->ksc, s->st, s->ctl, s->hist, s->partials, 2, bpl);
+  fh::kry_update_s<T><<<vb, fh::kKryThreads, 0, s->work>>>(sv, r, v, s->ksc, s->st, n, kKryBpl);
+  bpl = enqueue_apply<T>(s, prec, nload, sv, s->ctl0, t, nullptr);                       // t = A s
+  fh::kry_scalars<2><<<1, fh::kKryThreads, 0, s->work>>>(s->ksc, s->st, s->ctl, s->hist, s->partials, 2, bpl);
+  fh::kry_update_xr<T><<<vb, fh::kKryThreads, 0, s->work>>>(x, r, p, sv, t, rh, s->ksc, s->st, s->ctl, s->g.m,
+                                                            s->g.nv, kKryBpl, s->kpart);
+  fh::kry_scalars<3><<<1, fh::kKryThreads, 0, s->work>>>(s->ksc, s->st, s->ctl, s->hist, s->kpart, 3, kKryBpl);
+}
+
+int kry_launches_per_iter(const GridInfo& g) { return 4 + 2 * (2 + line_launches_per_iter(g)) + 3; }
+
+template <typename T>
+fh_status run_bicgstab(fh_solver* s, int prec, int nload, int chunk, int max_iter, long long* launches) {
+  fh_status rc = set_smem_attrs<T>(s, prec);
+  if (rc != FH_OK) return rc;
+  const int slot = prec == FH_PREC_FP64 ? 0 : 1;
+  const size_t nfield = (size_t)s->nload_max * s->g.nv * s->g.m;
+  if (!s->kbuf[slot]) CK(cudaMalloc(&s->kbuf[slot], 6 * nfield * sizeof(T)));
+  if (!s->ksc) {
+    CK(cudaMalloc(&s->ksc, FH_MAX_LOADS * sizeof(fh::KrylovScal)));
+    CK(cudaMalloc(&s->kpart, (size_t)FH_MAX_LOADS * kKryBpl * 3 * sizeof(double)));
+    CK(cudaMalloc(&s->ctl0, sizeof(Control)));
+  }
+  // control block of the operator applications: the solve's, with eps0 = 0
+  CK(cudaMemcpyAsync(s->ctl0, s->ctl, sizeof(Control), cudaMemcpyDeviceToDevice, s->work));
+  CK(cudaMemsetAsync(s->ctl0->eps0, 0, sizeof(s->ctl0->eps0), s->work));
+  cudaGraphExec_t exec = nullptr;
+  for (auto& e : s->graphs)
+    if (e.prec == prec && e.nload == nload && e.chunk == chunk && e.method == 1) exec = e.exec;
+  if (!exec) {
+    CK(cudaStreamBeginCapture(s->work, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < chunk; ++i) enqueue_bicgstab_iteration<T>(s, prec, nload);
+    cudaGraph_t graph;
+    CK(cudaStreamEndCapture(s->work, &graph));
+    cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      fh::set_error(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+      return FH_ERR_CUDA;
+    }
+    s->graphs.push_back({prec, nload, chunk, 1, exec});
+  }
+  CK(cudaEventRecord(s->ev0, s->work));
+  // start: r = b - A E0 (the stress of E0 + eps0 through the passes), rhat = r
+  T* x = Eptr<T>(s);
+  T* r = kry_field<T>(s, prec, KR);
+  enqueue_apply<T>(s, prec, nload, x, s->ctl, r, nullptr);
+  fh::kry_init<T><<<nload * kKryBpl, fh::kKryThreads, 0, s->work>>>(r, kry_field<T>(s, prec, KRH), x, s->st, s->ctl,
+                                                                     s->g.m, s->g.nv, kKryBpl, s->kpart);
+  fh::kry_scalars<0><<<1, fh::kKryThreads, 0, s->work>>>(s->ksc, s->st, s->ctl, s->hist, s->kpart, 3, kKryBpl);
+  CK(cudaGetLastError());
+  long long launched = 0;
+  for (;;) {
+    CK(cudaGraphLaunch(exec, s->work));
+    launched += chunk;
+    CK(cudaMemcpyAsync(s->h_flag, &s->ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, s->work));
+    CK(cudaStreamSynchronize(s->work));
+    if (*s->h_flag) break;
+    if (launched > (long long)max_iter + chunk) {
+      fh::set_error("iteration state did not terminate");
+      return FH_ERR_INTERNAL;
+    }
+  }
+  const int bpl = std::max(1, (int)std::min<long long>((s->g.m + kThreads - 1) / kThreads, 64));
+  fh::mean_stress<T><<<nload * bpl, kThreads, 0, s->work>>>(s->g, x, s->phase, s->Cp64, s->ctl, s->partials2,
+                                                            s->mstress, bpl);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(s->ev1, s->work));
+  *launches = (2 + line_launches_per_iter(s->g)) + 2 + 1 + launched * kry_launches_per_iter(s->g);
   return FH_OK;
 }
 
@@ -618,7 +778,8 @@ void free_all(fh_solver* s) {
   for (auto& e : s->graphs) cudaGraphExecDestroy(e.exec);
   s->graphs.clear();
   void* ptrs[] = {s->E64, s->E32, s->S, s->phase, s->Cp64, s->dC64, s->dC32, s->Cp32, s->G64, s->G32, s->ctl, s->st,
-                  s->partials, s->partials2, s->hist, s->mstress, s->err, s->scratch64, s->qtasks, s->qnext};
+                  s->partials, s->partials2, s->hist, s->mstress, s->err, s->scratch64, s->qtasks, s->qnext,
+                  s->kbuf[0], s->kbuf[1], s->ksc, s->kpart, s->ctl0};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& a : s->ax) {
@@ -1200,6 +1361,9 @@ fh_status begin_phase(fh_solver* s, int nload, const double* eps0, double tol, i
   if (out->path == 2)
     rc = prec == FH_PREC_FP64 ? run_solve_cluster<double>(s, nload, out->cs, &out->launches)
                               : run_solve_cluster<float>(s, nload, out->cs, &out->launches);
+  else if (s->method == 1)
+    rc = prec == FH_PREC_FP64 ? run_bicgstab<double>(s, prec, nload, chunk, max_iter, &out->launches)
+                              : run_bicgstab<float>(s, prec, nload, chunk, max_iter, &out->launches);
   else
     rc = prec == FH_PREC_FP64 ? run_solve<double>(s, prec, nload, chunk, max_iter, &out->launches)
                               : run_solve<float>(s, prec, nload, chunk, max_iter, &out->launches);
@@ -1250,6 +1414,15 @@ fh_status validate_solve(fh_solver* s, int nload, const double* eps0, const fh_s
   if (opts->path < 0 || opts->path > 2 || (opts->cluster != 0 && opts->cluster != 8 && opts->cluster != 16)) {
     fh::set_error("path must be 0..2 and cluster 0, 8 or 16");
     return FH_ERR_ARG;
+  }
+  if (opts->method != 0 && opts->method != 1) { fh::set_error("method must be 0 or 1"); return FH_ERR_ARG; }
+  if (opts->method == 1 && (opts->form != 0 || opts->tune != 0)) {
+    fh::set_error("BiCGStab (method 1) solves form 0 and takes no tuning");
+    return FH_ERR_ARG;
+  }
+  if (opts->method == 1 && opts->path == 2) {
+    fh::set_error("BiCGStab (method 1) runs on the whole-GPU passes (path 1)");
+    return FH_ERR_UNSUPPORTED;
   }
   for (int i = 0; i < nload * s->g.nv; ++i)
     if (!std::isfinite(eps0[i])) { fh::set_error("non-finite eps0"); return FH_ERR_ARG; }
@@ -1531,10 +1704,19 @@ fh_status fh_solve(fh_solver* s, int nload, const double* eps0, const fh_solve_o
     cs2 = s->tuned_cs[0];
   }
   PhaseOut A, B;
-  rc = solve_phase(s, nload, eps0, opts->tol, opts->max_iter, prec1, opts->init, chunk, path1, cs1, nullptr, &A,
+  s->method = opts->method;
+  if (s->method == 1) path1 = 1;
+  // mixed BiCGStab: its FP32 phase stops on the recursively updated residual,
+  // which drifts from the true one, so it aims at half the tolerance; the FP64
+  // phase then usually needs a single fixed-point step to confirm it
+  const double tol1 = (mixed && opts->method == 1) ? 0.5 * opts->tol : opts->tol;
+  rc = solve_phase(s, nload, eps0, tol1, opts->max_iter, prec1, opts->init, chunk, path1, cs1, nullptr, &A,
                    mixed ? kStallWindow : 0);
+  s->method = 0;
   if (rc != FH_OK) return rc;
   if (mixed) {
+    // the FP64 phase is the fixed point in every method: its Cauchy residual is
+    // the residual of the FP32 result, so it also removes the FP32 rounding
     LoadState st0[FH_MAX_LOADS];
     polish_start(A, st0);
     rc = solve_phase(s, nload, eps0, opts->tol, opts->max_iter, FH_PREC_FP64, 1, chunk, path2, cs2, st0, &B);
@@ -1580,8 +1762,11 @@ fh_status fh_solve_batch(fh_solver* const* solvers, int n, const int* nload, con
       fh_status rc = batch_cluster_choice(solvers[i], prec1, &p1, &c1);
       if (rc != FH_OK) return rc;
     }
-    rc = begin_phase(solvers[i], nload[i], eps0[i], opts->tol, opts->max_iter, prec1, opts->init, chunk, p1, c1,
-                     nullptr, &A[i], mixed ? kStallWindow : 0, true);
+    solvers[i]->method = opts->method;
+    if (opts->method == 1) p1 = 1;
+    rc = begin_phase(solvers[i], nload[i], eps0[i], (mixed && opts->method == 1) ? 0.5 * opts->tol : opts->tol,
+                     opts->max_iter, prec1, opts->init, chunk, p1, c1, nullptr, &A[i], mixed ? kStallWindow : 0, true);
+    solvers[i]->method = 0;
     if (rc != FH_OK) return rc;
     if (A[i].path == 2) deferred1.push_back(i);
   }

@@ -489,13 +489,19 @@ constexpr int kWarpRowThreads = 256;
 // barrier of the residual reduction is met once per launch.  All global loads
 // of a row (half spectra, old strain, phase indices) are issued together
 // before any of them is used.
-template <typename T, int P, bool FIRST>
+// KINV (with FIRST = false): the inverse half of a Krylov operator
+// application, as in row_pass: W = X - y to Wout (X = E, y the inverse
+// transform), block sums of W . Yaux (Yaux = X when null) and W . W.
+template <typename T, int P, bool FIRST, bool KINV = false>
 __global__ void __launch_bounds__(kWarpRowThreads, (P <= 4 ? 2 : 1)) row_pass_warp6(GridInfo g, const cplx<T>* __restrict__ twg,
                                                                   T* __restrict__ E, cplx<T>* __restrict__ S,
                                                                   const uint8_t* __restrict__ phase,
                                                                   const T* __restrict__ dC, Control* ctl,
                                                                   LoadState* st, double* __restrict__ partials,
-                                                                  double* __restrict__ hist, int blocks_per_load) {
+                                                                  double* __restrict__ hist, int blocks_per_load,
+                                                                  T* __restrict__ Wout = nullptr,
+                                                                  const T* __restrict__ Yaux = nullptr) {
+  static_assert(!(FIRST && KINV), "the inverse-only pass follows a transform");
   constexpr int NV = 6, L = 32 * P, H = L / 2 + 1;
   constexpr int WS = ((6 * H > 3 * L ? 6 * H : 3 * L) * 17 + 15) / 16 + 2;
   constexpr int NW = kWarpRowThreads / 32;
@@ -546,7 +552,7 @@ __global__ void __launch_bounds__(kWarpRowThreads, (P <= 4 ? 2 : 1)) row_pass_wa
 #pragma unroll
         for (int j = 0; j < P; ++j) ev[c][j] = Eload[c * cstrE + row * L + lane + 32 * j];
 #pragma unroll
-      for (int j = 0; j < P; ++j) ph[j] = phase[row * L + lane + 32 * j];
+      for (int j = 0; j < P; ++j) ph[j] = KINV ? 0 : phase[row * L + lane + 32 * j];
       cplx<T> z[3][P];
       if (!FIRST) {
         // 2. Z = A + i B per line pair from the half spectra, inverse FFT
@@ -572,6 +578,22 @@ __global__ void __launch_bounds__(kWarpRowThreads, (P <= 4 ? 2 : 1)) row_pass_wa
           }
         __syncwarp();
         warp_fft_inv_any<P, 3, T>(z, tw, lane);
+      }
+      if constexpr (KINV) {
+        const T* Yl = Yaux ? Yaux + (size_t)load * NV * cstrE : Eload;
+        T* Wl = Wout + (size_t)load * NV * cstrE;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          const size_t x = row * L + lane + 32 * j;
+#pragma unroll
+          for (int c = 0; c < NV; ++c) {
+            const T w = ev[c][j] - ((c & 1) ? z[c >> 1][j].y : z[c >> 1][j].x) * scale;
+            Wl[c * cstrE + x] = w;
+            acc_d.add_prod(w, Yaux ? Yl[c * cstrE + x] : ev[c][j]);
+            acc_n.add_sq(w);
+          }
+        }
+        continue;
       }
       // 3. pointwise: E_new, residual sums, tau
       T rd = T(0), rn = T(0);
@@ -641,6 +663,13 @@ __global__ void __launch_bounds__(kWarpRowThreads, (P <= 4 ? 2 : 1)) row_pass_wa
   if (FIRST) return;
   const double d2 = block_sum_acc(acc_d, red);
   const double n2 = block_sum_acc(acc_n, red);
+  if (KINV) {
+    if (threadIdx.x == 0) {
+      partials[2 * (size_t)blockIdx.x] = d2;
+      partials[2 * (size_t)blockIdx.x + 1] = n2;
+    }
+    return;
+  }
   __shared__ unsigned int s_ticket;
   if (threadIdx.x == 0) {
     partials[2 * (size_t)blockIdx.x] = d2;
