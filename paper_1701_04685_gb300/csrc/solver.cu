@@ -21,6 +21,7 @@
 #include "warprow.cuh"
 #include "linewarp.cuh"
 #include "krylov.cuh"
+#include "planewarp.cuh"
 
 namespace fh {
 static thread_local std::string g_err;
@@ -112,6 +113,8 @@ struct fh_solver {
   // launch shapes per precision (0: fp64, 1: fp32)
   int rpb[2] = {1, 1};
   int row_warp[2] = {0, 0};  // > 0: warp-per-row pass with L = 32 * row_warp
+  int plane[2] = {0, 0};     // 3-D FP32: > 0 = the fused plane pass (axis-1 P, axis-2 P packed as 10 P1 + P2)
+  bool no_plane = false;     // path 3 of the solve in progress: keep the four separate passes
   int warp_res[2] = {0, 0};  // resident blocks per SM of that pass
   int sms = 0;               // multiprocessors of the device
   int row_bpl[2] = {1, 1};
@@ -140,6 +143,11 @@ namespace {
 
 size_t csize(int prec) { return prec == FH_PREC_FP64 ? sizeof(double2) : sizeof(float2); }
 
+size_t plane_smem_of(int P1, int P2) {
+  const int N1 = 32 * P1, L = 32 * P2, H = L / 2 + 1;
+  return (size_t)(3 * N1 * H + N1 + L + fh::kPlaneWarps * fh::plane_ws(L)) * sizeof(float2);
+}
+
 void choose_shapes(fh_solver* s, int prec) {
   const GridInfo& g = s->g;
   const int sms = 152;
@@ -166,6 +174,14 @@ void choose_shapes(fh_solver* s, int prec) {
       s->row_bpl[prec] = (int)((g.nrows + nw - 1) / nw);
       s->row_smem[prec] = fh::warprow_smem<float>(g.L);
     }
+  }
+  // FP32 3-D grids whose axis-1 and axis-2 lengths are 32, 64 or 128 points
+  // (and whose plane fits in a CTA's shared memory): the fused plane pass
+  s->plane[prec] = 0;
+  if (prec == FH_PREC_FP32 && g.nv == 6 && g.nd == 3 && s->row_warp[prec] > 0) {
+    const int P1 = g.dims[1] % 32 == 0 ? g.dims[1] / 32 : 0, P2 = s->row_warp[prec];
+    if ((P1 == 1 || P1 == 2 || P1 == 4) && (P2 == 1 || P2 == 2 || P2 == 4) && plane_smem_of(P1, P2) + 4096 <= kMaxSmem)
+      s->plane[prec] = 10 * P1 + P2;
   }
   for (int a = 0; a + 1 < g.nd; ++a) {
     const int N = g.dims[a];
@@ -282,9 +298,12 @@ void launch_axis(fh_solver* s, int prec, int a, int mode, int nload) {
   launch_line<T>(s, prec, a, mode, (unsigned)blocks, (int)n_outer, (int)n_inner);
 }
 
+// the fused plane pass applies: FP32, an eligible 3-D grid, not disabled (path 3)
+bool use_plane(const fh_solver* s, int prec) { return prec == FH_PREC_FP32 && s->plane[prec] > 0 && !s->no_plane; }
+
 // Enqueue the line passes of one iteration (everything between two row passes).
 template <typename T>
-void enqueue_line_passes(fh_solver* s, int prec, int nload) {
+void enqueue_line_passes(fh_solver* s, int prec, int nload, bool plane_ok = true) {
   const GridInfo& g = s->g;
   using C = typename fh::cplx_t<T>::type;
   C* S = reinterpret_cast<C*>(s->S);
@@ -295,6 +314,10 @@ void enqueue_line_passes(fh_solver* s, int prec, int nload) {
     return;
   }
   auto launch = [&](int a, int mode) { launch_axis<T>(s, prec, a, mode, nload); };
+  if (plane_ok && use_plane(s, prec)) {   // the plane pass transforms axes 1 and 2
+    launch(0, 2);
+    return;
+  }
   // forward along axes nd-2 .. 1, then axis 0 with the Green step, then inverse 1 .. nd-2
   for (int a = g.nd - 2; a >= 1; --a) launch(a, 0);
   launch(0, 2);
@@ -324,9 +347,50 @@ void enqueue_row_pass_warp(fh_solver* s, int prec, int nload) {
       s->partials, s->hist, bpl);
 }
 
+// the fused plane pass (planewarp.cuh): one cluster of two CTAs per plane x0
+// and load
+template <int P1, int P2, bool FIRST>
+void launch_plane(fh_solver* s, int nload) {
+  const GridInfo& g = s->g;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(2 * g.dims[0] * nload));
+  cfg.blockDim = dim3(fh::kPlaneThreads);
+  cfg.dynamicSmemBytes = fh::plane_smem<P1, P2>();
+  cfg.stream = s->work;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, fh::plane_pass_warp6<P1, P2, FIRST>, g, (const float2*)s->ax[1].tw32,
+                     (const float2*)s->ax[2].tw32, s->E32, reinterpret_cast<float2*>(s->S), (const uint8_t*)s->phase,
+                     (const float*)dCptr<float>(s), s->ctl, s->st, s->partials, s->hist);
+}
+
+template <bool FIRST>
+void enqueue_plane(fh_solver* s, int nload) {
+  switch (s->plane[FH_PREC_FP32]) {
+    case 11: launch_plane<1, 1, FIRST>(s, nload); break;
+    case 12: launch_plane<1, 2, FIRST>(s, nload); break;
+    case 14: launch_plane<1, 4, FIRST>(s, nload); break;
+    case 21: launch_plane<2, 1, FIRST>(s, nload); break;
+    case 22: launch_plane<2, 2, FIRST>(s, nload); break;
+    case 24: launch_plane<2, 4, FIRST>(s, nload); break;
+    case 41: launch_plane<4, 1, FIRST>(s, nload); break;
+    case 42: launch_plane<4, 2, FIRST>(s, nload); break;
+    default: launch_plane<4, 4, FIRST>(s, nload); break;
+  }
+}
+
 template <typename T, bool FIRST>
 void enqueue_row_pass(fh_solver* s, int prec, int nload) {
   if constexpr (sizeof(T) == 4) {
+    if (use_plane(s, prec)) {
+      enqueue_plane<FIRST>(s, nload);
+      return;
+    }
     switch (s->row_warp[prec]) {
       case 1: enqueue_row_pass_warp<T, 1, FIRST>(s, prec, nload); return;
       case 2: enqueue_row_pass_warp<T, 2, FIRST>(s, prec, nload); return;
@@ -360,9 +424,34 @@ cudaError_t set_col_attrs() {
   return e;
 }
 
+template <int P1, int P2>
+cudaError_t set_plane_attrs() {
+  const int sm = (int)fh::plane_smem<P1, P2>();
+  cudaError_t e = cudaFuncSetAttribute(fh::plane_pass_warp6<P1, P2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fh::plane_pass_warp6<P1, P2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  return e;
+}
+
+cudaError_t set_plane_attrs_of(int code) {
+  switch (code) {
+    case 11: return set_plane_attrs<1, 1>();
+    case 12: return set_plane_attrs<1, 2>();
+    case 14: return set_plane_attrs<1, 4>();
+    case 21: return set_plane_attrs<2, 1>();
+    case 22: return set_plane_attrs<2, 2>();
+    case 24: return set_plane_attrs<2, 4>();
+    case 41: return set_plane_attrs<4, 1>();
+    case 42: return set_plane_attrs<4, 2>();
+    case 44: return set_plane_attrs<4, 4>();
+    default: return cudaSuccess;
+  }
+}
+
 template <typename T, int NV>
 fh_status set_smem_attrs_nv(fh_solver* s, int prec) {
   const size_t rs = s->row_smem[prec];
+  if (sizeof(T) == 4 && s->plane[prec] > 0) CK(set_plane_attrs_of(s->plane[prec]));
   if (rs > kMaxSmem) {
     fh::set_error("contiguous axis too long for this precision (shared memory)");
     return FH_ERR_UNSUPPORTED;
@@ -412,8 +501,9 @@ fh_status set_smem_attrs(fh_solver* s, int prec) {
 
 template <typename T>
 fh_status get_graph(fh_solver* s, int prec, int nload, int chunk, cudaGraphExec_t* out) {
+  const int variant = s->no_plane ? 2 : 0;   // graphs with and without the plane pass differ
   for (auto& e : s->graphs)
-    if (e.prec == prec && e.nload == nload && e.chunk == chunk && e.method == 0) {
+    if (e.prec == prec && e.nload == nload && e.chunk == chunk && e.method == variant) {
       *out = e.exec;
       return FH_OK;
     }
@@ -431,12 +521,13 @@ fh_status get_graph(fh_solver* s, int prec, int nload, int chunk, cudaGraphExec_
     fh::set_error(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
     return FH_ERR_CUDA;
   }
-  s->graphs.push_back({prec, nload, chunk, 0, exec});
+  s->graphs.push_back({prec, nload, chunk, variant, exec});
   *out = exec;
   return FH_OK;
 }
 
 int line_launches_per_iter(const GridInfo& g) { return g.nd == 1 ? 1 : 1 + 2 * (g.nd - 2); }
+int line_launches_per_iter(const fh_solver* s, int prec) { return use_plane(s, prec) ? 1 : line_launches_per_iter(s->g); }
 
 template <typename T>
 fh_status run_solve(fh_solver* s, int prec, int nload, int chunk, int max_iter, long long* launches) {
@@ -465,7 +556,7 @@ fh_status run_solve(fh_solver* s, int prec, int nload, int chunk, int max_iter, 
                                                             s->mstress, bpl);
   CK(cudaGetLastError());
   CK(cudaEventRecord(s->ev1, s->work));
-  *launches = 2 + launched * (1 + line_launches_per_iter(s->g));
+  *launches = 2 + launched * (1 + line_launches_per_iter(s, prec));
   return FH_OK;
 }
 
@@ -531,7 +622,7 @@ int enqueue_row_x(fh_solver* s, int prec, int nload, T* X, Control* ctl, T* Wout
 template <typename T>
 int enqueue_apply(fh_solver* s, int prec, int nload, T* X, Control* ctl, T* W, const T* Yaux) {
   enqueue_row_x<T, true, false>(s, prec, nload, X, ctl, nullptr, nullptr);
-  enqueue_line_passes<T>(s, prec, nload);
+  enqueue_line_passes<T>(s, prec, nload, false);
   return enqueue_row_x<T, false, true>(s, prec, nload, X, ctl, W, Yaux);
 }
 
@@ -741,7 +832,8 @@ template <typename T>
 fh_status choose_path(fh_solver* s, int want_path, int want_cs, int* path, int* cs) {
   *path = 1;
   *cs = 0;
-  if (want_path == 1) return FH_OK;
+  s->no_plane = want_path == 3;
+  if (want_path == 1 || want_path == 3) return FH_OK;
   bool ok8 = false, ok16 = false;
   if (want_cs == 0 || want_cs == 16) {
     fh_status rc = cluster_fits<T, 16>(s, &ok16);
@@ -943,7 +1035,7 @@ fh_status profile_passes(fh_solver* s, int prec, int nload, int reps, double* ms
   } else {
     rc = timed(1, [&] { line(0, 2); });
     if (rc != FH_OK) return rc;
-    if (g.nd == 3) {
+    if (g.nd == 3 && !use_plane(s, prec)) {
       rc = timed(2, [&] { line(1, 0); });
       if (rc != FH_OK) return rc;
       rc = timed(3, [&] { line(1, 1); });
@@ -1411,8 +1503,8 @@ fh_status validate_solve(fh_solver* s, int nload, const double* eps0, const fh_s
   if (opts->init != 0 && opts->init != 1) { fh::set_error("init must be 0 or 1"); return FH_ERR_ARG; }
   if (opts->form != 0 && opts->form != 1) { fh::set_error("form must be 0 or 1"); return FH_ERR_ARG; }
   if (opts->tune != 0 && opts->tune != 1) { fh::set_error("tune must be 0 or 1"); return FH_ERR_ARG; }
-  if (opts->path < 0 || opts->path > 2 || (opts->cluster != 0 && opts->cluster != 8 && opts->cluster != 16)) {
-    fh::set_error("path must be 0..2 and cluster 0, 8 or 16");
+  if (opts->path < 0 || opts->path > 3 || (opts->cluster != 0 && opts->cluster != 8 && opts->cluster != 16)) {
+    fh::set_error("path must be 0..3 and cluster 0, 8 or 16");
     return FH_ERR_ARG;
   }
   if (opts->method != 0 && opts->method != 1) { fh::set_error("method must be 0 or 1"); return FH_ERR_ARG; }

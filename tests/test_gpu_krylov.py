@@ -101,22 +101,26 @@ def test_bicgstab_stop_rule_is_the_cauchy_criterion(fh):
     s.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_bicgstab_benchmark_ceff(fh, prec):
-    """The 2-D benchmark workload (dlVP, [[128,32],[0,128]], contrast 100) at r <= 1e-6:
-    C_eff within 1e-6 of the converged oracle, with fewer operator applications
-    than the fixed point needs iterations."""
+@pytest.mark.parametrize("prec,tol,bound", [("fp64", 1e-6, 2e-6), ("fp64", 2e-7, 1e-6), ("mixed", 1e-6, 1e-6)])
+def test_bicgstab_benchmark_ceff(fh, prec, tol, bound):
+    """The 2-D benchmark workload (dlVP, [[128,32],[0,128]], contrast 100): C_eff
+    against the converged oracle, with fewer operator applications than the fixed
+    point needs iterations.  At the same residual 1e-6 the FP64 BiCGStab result's
+    C_eff is 1.1e-6 off (the fixed point's 9e-8: its remaining error lies in
+    directions the mean stress hardly sees); 2e-7 brings it within 1e-6, and the
+    mixed mode (FP32 BiCGStab to tol / 2, then FP64 fixed-point steps) meets 1e-6
+    at 1e-6."""
     P = {"fp64": fh.FH_PREC_FP64, "mixed": fh.FH_PREC_MIXED}[prec]
     case = Case.from_workload(W.dlvp_sheared())
     s = case.product(fh)
     fp = s.solve(case.eps0, tol=1e-6, max_iter=20000, precision=P, path=1)
-    kr = s.solve(case.eps0, tol=1e-6, max_iter=20000, precision=P, method=1)
+    kr = s.solve(case.eps0, tol=tol, max_iter=20000, precision=P, method=1)
     assert kr["status"] == 0
     Cref = np.loadtxt(os.path.join(GOLDEN, "ceff_dlvp_sheared.txt"))
     err = frob_rel(s.get_ceff(), Cref)
-    print(f"{prec}: BiCGStab iterations {list(kr['iterations'])} (fixed point {list(fp['iterations'])}), "
-          f"C_eff error {err:.3e}")
-    assert err < 1e-6
+    print(f"{prec} tol {tol}: BiCGStab iterations {list(kr['iterations'])} (fixed point to 1e-6 "
+          f"{list(fp['iterations'])}), C_eff error {err:.3e}")
+    assert err < bound
     assert np.all(2 * kr["iterations"] < fp["iterations"])
     s.close()
 
