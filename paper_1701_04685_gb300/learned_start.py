@@ -3,9 +3,11 @@
 The Fourier neural operator of ``fh_fno_*`` is trained on strain fields that
 the solver itself produces for seeded random-sphere microstructures (3-D,
 M = diag(n, n, n), Dirichlet kernel), then used as the starting strain of the
-fixed point.  The iteration still runs to the same Cauchy tolerance, so the
-network can only save iterations; the zero start is the fallback, taken when
-the learned start's first Cauchy residual is not smaller than the zero start's.
+fixed point or of BiCGStab.  The solve still runs to the same Cauchy
+tolerance, so the network can only save iterations; the zero start is the
+fallback: for each solver method a validation split of held-out seeds decides
+whether the learned start pays (mean time to tolerance, inference included),
+and the other seeds report what that choice gives.
 
 The solution is linear in the macroscopic strain, E = sum_j eps0_j E^(j), so
 the network maps the modulus field log10 E(x) (one input channel) to the six
@@ -99,8 +101,9 @@ def train(net, X, T, epochs, lr=2e-3, batch=4, seed=0, log=None):
     return hist
 
 
-def evaluate(net, seeds, n, tol=1e-6):
-    """Iterations and time to tolerance per held-out seed: zero start vs learned start."""
+def evaluate(net, seeds, n, tol=1e-6, methods=(0,)):
+    """Iterations and time to tolerance per held-out seed, zero start vs learned start,
+    for each solver method (0: the fixed point, 1: BiCGStab), mixed precision."""
     import torch
     rows = []
     x = torch.empty((1, 1, n ** 3), dtype=torch.float32, device="cuda")
@@ -108,40 +111,50 @@ def evaluate(net, seeds, n, tol=1e-6):
     for seed in seeds:
         s, ids, logE = make_solver(W.fno3d_item(seed, n=n))
         ph = torch.from_numpy(ids).cuda()
-        z = s.solve(np.eye(6), tol=tol, max_iter=20000, precision=FH_PREC_MIXED)
-        r1_zero = [s.get_residuals(L)[0] for L in range(6)]
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        net.make_input(ph, logE, np.zeros(6), x[0])
-        net.forward(x, y)
-        for L in range(6):                       # unit load L: its block of six channels
-            set_strain_f32(s, L, y[0, 6 * L:6 * L + 6])
-        torch.cuda.synchronize()
-        t_inf = time.perf_counter() - t0
-        lrn = s.solve(np.eye(6), tol=tol, max_iter=20000, precision=FH_PREC_MIXED, init=1)
-        r1_lrn = [s.get_residuals(L)[0] for L in range(6)]
-        fallback = [r1_lrn[L] >= r1_zero[L] for L in range(6)]
-        it_best = [z["iterations"][L] if fallback[L] else lrn["iterations"][L] for L in range(6)]
-        rows.append({"seed": int(seed), "iters_zero": [int(i) for i in z["iterations"]],
-                     "iters_learned": [int(i) for i in lrn["iterations"]],
-                     "iters_with_fallback": [int(i) for i in it_best],
-                     "ms_zero": z["elapsed_ms"], "ms_learned": lrn["elapsed_ms"] + 1e3 * t_inf,
-                     "ms_inference": 1e3 * t_inf, "fallback": [bool(f) for f in fallback]})
+        row = {"seed": int(seed)}
+        for method in methods:
+            z = s.solve(np.eye(6), tol=tol, max_iter=20000, precision=FH_PREC_MIXED, method=method)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            net.make_input(ph, logE, np.zeros(6), x[0])
+            net.forward(x, y)
+            for L in range(6):                       # unit load L: its block of six channels
+                set_strain_f32(s, L, y[0, 6 * L:6 * L + 6])
+            torch.cuda.synchronize()
+            t_inf = time.perf_counter() - t0
+            lrn = s.solve(np.eye(6), tol=tol, max_iter=20000, precision=FH_PREC_MIXED, init=1, method=method)
+            row[f"m{method}"] = {"iters_zero": [int(i) for i in z["iterations"]],
+                                 "iters_learned": [int(i) for i in lrn["iterations"]],
+                                 "ms_zero": z["elapsed_ms"], "ms_learned": lrn["elapsed_ms"] + 1e3 * t_inf,
+                                 "ms_inference": 1e3 * t_inf}
+        rows.append(row)
         s.close()
     return rows
 
 
-def summary(rows):
-    iz = np.array([r["iters_zero"] for r in rows], dtype=float)
-    il = np.array([r["iters_learned"] for r in rows], dtype=float)
-    ib = np.array([r["iters_with_fallback"] for r in rows], dtype=float)
-    mz = np.array([r["ms_zero"] for r in rows])
-    ml = np.array([r["ms_learned"] for r in rows])
-    return {"seeds": len(rows), "loads": 6, "mean_iters_zero": float(iz.mean()),
-            "mean_iters_learned": float(il.mean()), "mean_iters_with_fallback": float(ib.mean()),
-            "iteration_saving": float(1 - ib.mean() / iz.mean()), "mean_ms_zero": float(mz.mean()),
-            "mean_ms_learned_incl_inference": float(ml.mean()), "time_saving": float(1 - ml.mean() / mz.mean()),
-            "fallback_fraction": float(np.mean([f for r in rows for f in r["fallback"]]))}
+def summary(rows, methods=(0,), val=0):
+    """Means over seeds and loads per method, and the start a validation split selects.
+
+    The first ``val`` seeds choose, per method, the start (learned or zero) with
+    the smaller mean time to tolerance (inference included); the remaining seeds
+    report what that choice gives: the fallback to the zero start is taken
+    whenever the network does not pay on held-out data."""
+    out = {"seeds": len(rows), "loads": 6, "validation_seeds": val}
+    for m in methods:
+        def mean(key, rs):
+            return float(np.mean([np.mean(r[f"m{m}"][key]) for r in rs]))
+        va, te = rows[:val], (rows[val:] if val < len(rows) else rows)
+        use_learned = bool(val > 0 and mean("ms_learned", va) < mean("ms_zero", va))
+        pick = "learned" if use_learned else "zero"
+        out[f"method{m}"] = {
+            "mean_iters_zero": mean("iters_zero", rows), "mean_iters_learned": mean("iters_learned", rows),
+            "iteration_saving": 1 - mean("iters_learned", rows) / mean("iters_zero", rows),
+            "mean_ms_zero": mean("ms_zero", rows), "mean_ms_learned_incl_inference": mean("ms_learned", rows),
+            "time_saving": 1 - mean("ms_learned", rows) / mean("ms_zero", rows),
+            "policy_start": pick,
+            "test_mean_iters_zero": mean("iters_zero", te), "test_mean_iters_policy": mean(f"iters_{pick}", te),
+            "test_mean_ms_zero": mean("ms_zero", te), "test_mean_ms_policy": mean(f"ms_{pick}", te)}
+    return out
 
 
 def main():
@@ -155,8 +168,11 @@ def main():
     ap.add_argument("--epochs", type=int, default=10)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--methods", default="0,1", help="solver methods to evaluate (0 fixed point, 1 BiCGStab)")
+    ap.add_argument("--val", type=int, default=32, help="held-out seeds that choose the start per method")
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
+    methods = tuple(int(v) for v in a.methods.split(","))
     import torch
     log = lambda s: print(s, flush=True)  # noqa: E731
     net = FNO(a.n, 1, 36, a.width, min(a.modes, a.n // 2), a.layers, max_batch=a.batch)
@@ -172,9 +188,9 @@ def main():
     t_train = time.perf_counter() - t0
     log(f"trained {a.epochs} epochs in {t_train:.1f} s")
     del X, T
-    rows = evaluate(net, range(100000, 100000 + a.test), a.n)
+    rows = evaluate(net, range(100000, 100000 + a.test), a.n, methods=methods)
     res = {"config": vars(a), "generate_s": t_gen, "train_s": t_train, "loss_history": hist,
-           "summary": summary(rows)}
+           "summary": summary(rows, methods, a.val)}
     log(json.dumps(res["summary"]))
     if a.out:
         with open(a.out, "w") as f:
