@@ -52,7 +52,7 @@ typedef enum {
   FH_ERR_CUDA = -5,       /* a CUDA runtime call failed                      */
   FH_ERR_TIMEOUT = -6,    /* reserved: a bounded device wait gave up         */
   FH_ERR_INTERNAL = -7,   /* internal consistency check failed               */
-  FH_ERR_UNSUPPORTED = -8,/* e.g. an FFT axis with a prime factor > 13       */
+  FH_ERR_UNSUPPORTED = -8,/* e.g. an FFT axis longer than 4096               */
   FH_ERR_STATE = -9       /* call order violated (e.g. solve before stiffness) */
 } fh_status;
 
@@ -201,8 +201,10 @@ fh_status fh_pattern_half_freqs(const fh_pattern* p, int64_t* h, int64_t* nh);
 /* Solver for one pattern and generator on one CUDA stream (cudaStream_t,
  * NULL = legacy default stream).  Allocates device work memory for up to
  * nload_max load cases (1..FH_MAX_LOADS).  The pattern may be destroyed
- * afterwards.  Errors: FH_ERR_ARG, FH_ERR_UNSUPPORTED (an SNF axis longer
- * than 4096 or with a prime factor > 13, or |det M| = 1: a single point has
+ * afterwards.  Every axis length up to 4096 is supported: radices 2, 3, 4,
+ * 5, 8 are written out, 7, 11, 13 and any larger prime factor run as direct
+ * DFT stages (slower for large primes).  Errors: FH_ERR_ARG,
+ * FH_ERR_UNSUPPORTED (an SNF axis longer than 4096, or |det M| = 1: a single point has
  * no fluctuation, E = 0 and C_eff = C there), FH_ERR_CUDA. */
 fh_status fh_solver_create(const fh_pattern* p, const fh_generator* gen,
                            int nload_max, void* cuda_stream, fh_solver** out);
@@ -218,13 +220,17 @@ fh_status fh_set_stiffness_phases(fh_solver* s, const uint8_t* phase, int nphase
 
 /* Stiffness given point by point (Sec. 3.1, C in SSym_d(L^inf), sampled at
  * the pattern points): C[m*n_v*n_v] Mandel matrices in storage order (the
- * order of fh_pattern_points), host or device memory, read once.  The
- * kernels index the stiffness through a phase id per point and a table of at
- * most 16 matrices, so the field is reduced to its distinct matrices (exact,
- * bitwise comparison) and passed on as in fh_set_stiffness_phases; the result
- * is identical to that call with the same matrices.  Errors: FH_ERR_ARG
- * (non-finite or non-symmetric matrix), FH_ERR_UNSUPPORTED when the field
- * holds more than 16 distinct matrices (nothing is changed then). */
+ * order of fh_pattern_points), host or device memory, read once.  A field of
+ * at most 16 distinct matrices (exact, bitwise comparison) is reduced to phase
+ * ids and a table and solved exactly as fh_set_stiffness_phases with those
+ * matrices.  A field with more distinct matrices (a graded or continuously
+ * varying material) is kept point by point: its upper triangles live on the
+ * device (21 doubles per point in 3-D, plus FP32 copies and C - C0 after
+ * fh_set_reference), the constitutive stage reads them per point, and such
+ * solves run on the whole-GPU passes with the block row pass (path 2 gives
+ * FH_ERR_UNSUPPORTED).  The reference-medium rule of fh_set_reference then
+ * takes its ranges over all points.  Errors: FH_ERR_ARG (non-finite or
+ * non-symmetric matrix). */
 fh_status fh_set_stiffness_field(fh_solver* s, const double* C);
 
 /* Reference medium C0 (n_v x n_v Mandel, host).  NULL selects the rule of

@@ -5,7 +5,8 @@
 // stored grid.  Every pass of the solver transforms a batch of lines that sit
 // in shared memory; this file holds that line transform: a Stockham
 // (self-sorting) radix decomposition L = r_0 r_1 ... with radices
-// 2, 3, 4, 5, 8 written out and 7, 11, 13 done as small direct DFTs.
+// 2, 3, 4, 5, 8 written out, 7, 11, 13 done as small direct DFTs, and any
+// larger prime factor by a direct-DFT stage with one thread per output.
 //
 // Forward (DIR = -1) computes X_k = sum_n x_n exp(-2 pi i k n / L); inverse
 // (DIR = +1) the same with +i and no 1/L factor.  Twiddles come from a table
@@ -213,6 +214,42 @@ __device__ __forceinline__ void stockham_stage(const cplx<T>* in, cplx<T>* out, 
   }
 }
 
+// Stage of any other prime radix R (the factors above 13 of an axis length):
+// one thread per output.  Output o = jq Ns R + t_out Ns + k of group
+// j = jq Ns + k is sum_t v_t w_L^{t k stride} w_R^{t_out t}, v_t = in[j + t nb];
+// both twiddles come from the table as one exponent t k stride +
+// ((t_out t) mod R) L / R, reduced mod L.  The work per point grows with R
+// (2 R flops of complex multiply-add) where the written-out radices need
+// O(log R); it makes every axis length up to 4096 usable.
+template <int DIR, typename T, int PADSH = 0>
+__device__ __forceinline__ void stockham_stage_prime(const cplx<T>* in, cplx<T>* out, int nlines, int ls, int L,
+                                                     int Ns, int R, const cplx<T>* __restrict__ tw, int tid,
+                                                     int nthr) {
+  const int nb = L / R;
+  const int stride = L / (Ns * R);
+  const int step = L / R;
+  const int total = nlines * L;
+  for (int idx = tid; idx < total; idx += nthr) {
+    const int line = idx / L;
+    const int o = idx - line * L;
+    const int k = o % Ns;
+    const int rest = o / Ns;
+    const int t_out = rest % R;
+    const int jq = rest / R;
+    const int j = jq * Ns + k;
+    const cplx<T>* li = in + line * ls;
+    cplx<T> acc = li[padi<PADSH>(j)];
+    for (int t = 1; t < R; ++t) {
+      int e = t * k * stride + ((t_out * t) % R) * step;
+      if (e >= L) e -= L;
+      cplx<T> w = tw[e];
+      if (DIR > 0) w.y = -w.y;
+      acc = cadd(acc, cmul(li[padi<PADSH>(j + t * nb)], w));
+    }
+    out[line * ls + padi<PADSH>(o)] = acc;
+  }
+}
+
 // Barrier of a team of threads: the whole block (nthr == blockDim.x), else the
 // first nthr threads (a multiple of 32) on named barrier 1.
 __device__ __forceinline__ void team_sync(int nthr) {
@@ -252,7 +289,8 @@ __device__ cplx<T>* fft_lines_pp(cplx<T>* buf, cplx<T>* tmp, int nlines, int ls,
         case 7: stockham_stage<7, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw, tid, nthr); break;
         case 8: stockham_stage<8, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw, tid, nthr); break;
         case 11: stockham_stage<11, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw, tid, nthr); break;
-        default: stockham_stage<13, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw, tid, nthr); break;
+        case 13: stockham_stage<13, DIR, T, PADSH>(in, out, nlines, ls, L, Ns, tw, tid, nthr); break;
+        default: stockham_stage_prime<DIR, T, PADSH>(in, out, nlines, ls, L, Ns, r, tw, tid, nthr); break;
       }
     }
     team_sync(nthr);

@@ -269,8 +269,12 @@ __global__ void __launch_bounds__(256, PassOcc<T>::value) row_pass(GridInfo g, D
                                                 const uint8_t* __restrict__ phase, const T* __restrict__ dC,
                                                 Control* ctl, LoadState* st, double* __restrict__ partials,
                                                 double* __restrict__ hist, int rpb, int blocks_per_load,
-                                                T* __restrict__ Wout = nullptr, const T* __restrict__ Yaux = nullptr) {
+                                                T* __restrict__ Wout = nullptr, const T* __restrict__ Yaux = nullptr,
+                                                const T* __restrict__ Cfld = nullptr) {
   static_assert(!(FIRST && KINV), "the inverse-only pass follows a transform");
+  // Cfld (not null): the stiffness of the constitutive stage given point by
+  // point, upper triangle of the Mandel matrix as [tri][m] (C - C0, or C for
+  // the variational form), instead of the phase table
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
   __shared__ int s_skip;
@@ -383,15 +387,34 @@ __global__ void __launch_bounds__(256, PassOcc<T>::value) row_pass(GridInfo g, D
           ep[c * cstrE] = en[c];
         }
       }
-      const T* dc = dcs + (size_t)phase[(row0 + r) * L + x] * NV * NV;
+      T tau[NV];
+      if (Cfld) {
+        const size_t pt = (size_t)(row0 + r) * L + x;
+#pragma unroll
+        for (int a = 0; a < NV; ++a) tau[a] = T(0);
+#pragma unroll
+        for (int a = 0; a < NV; ++a)
+#pragma unroll
+          for (int b = a; b < NV; ++b) {
+            const T cab = Cfld[(size_t)(a * NV - (a * (a - 1)) / 2 + (b - a)) * g.m + pt];
+            tau[a] += cab * (en[b] + e0[b]);
+            if (b != a) tau[b] += cab * (en[a] + e0[a]);
+          }
+      } else {
+        const T* dc = dcs + (size_t)phase[(row0 + r) * L + x] * NV * NV;
+#pragma unroll
+        for (int a = 0; a < NV; ++a) {
+          T t = T(0);
+#pragma unroll
+          for (int b = 0; b < NV; ++b) t += dc[a * NV + b] * (en[b] + e0[b]);
+          tau[a] = t;
+        }
+      }
 #pragma unroll
       for (int a = 0; a < NV; ++a) {
-        T t = T(0);
-#pragma unroll
-        for (int b = 0; b < NV; ++b) t += dc[a * NV + b] * (en[b] + e0[b]);
         const int f = r * NV + a;
-        if (f & 1) Z[(f >> 1) * Lp + padi<PS>(x)].y = t;
-        else Z[(f >> 1) * Lp + padi<PS>(x)].x = t;
+        if (f & 1) Z[(f >> 1) * Lp + padi<PS>(x)].y = tau[a];
+        else Z[(f >> 1) * Lp + padi<PS>(x)].x = tau[a];
       }
     }
     // odd number of real lines: the last pair's imaginary part is zero
@@ -610,7 +633,7 @@ __global__ void __launch_bounds__(256) mean_stress(GridInfo g, const T* __restri
                                                    const uint8_t* __restrict__ phase,
                                                    const double* __restrict__ Cp, Control* ctl,
                                                    double* __restrict__ partials, double* __restrict__ out,
-                                                   int blocks_per_load) {
+                                                   int blocks_per_load, const double* __restrict__ Cfld = nullptr) {
   __shared__ double red[32];
   __shared__ unsigned int s_ticket;
   const int load = blockIdx.x / blocks_per_load;
@@ -623,11 +646,21 @@ __global__ void __launch_bounds__(256) mean_stress(GridInfo g, const T* __restri
   for (long long i = (long long)q * blockDim.x + threadIdx.x; i < g.m; i += (long long)blocks_per_load * blockDim.x) {
     double e[MAXV];
     for (int c = 0; c < nv; ++c) e[c] = (double)E[Ebase + (size_t)c * g.m + i] + e0[c];
-    const double* C = Cp + (size_t)phase[i] * nv * nv;
-    for (int a = 0; a < nv; ++a) {
-      double s = 0.0;
-      for (int b = 0; b < nv; ++b) s += C[a * nv + b] * e[b];
-      acc[a] += s;
+    if (Cfld) {   // point-by-point stiffness, upper triangle [tri][m]
+      int t = 0;
+      for (int a = 0; a < nv; ++a)
+        for (int b = a; b < nv; ++b, ++t) {
+          const double cab = Cfld[(size_t)t * g.m + i];
+          acc[a] += cab * e[b];
+          if (b != a) acc[b] += cab * e[a];
+        }
+    } else {
+      const double* C = Cp + (size_t)phase[i] * nv * nv;
+      for (int a = 0; a < nv; ++a) {
+        double s = 0.0;
+        for (int b = 0; b < nv; ++b) s += C[a * nv + b] * e[b];
+        acc[a] += s;
+      }
     }
   }
   for (int a = 0; a < nv; ++a) {
@@ -1097,6 +1130,24 @@ __global__ void __launch_bounds__(128) green_table_iso(GreenParams P, double* __
       }
       ++t;
     }
+  }
+}
+
+// Point-by-point stiffness after the reference medium is known: from C(x)
+// (upper triangle [tri][m], FP64) the differences C(x) - C0 in FP64 and FP32
+// and C(x) in FP32 (variational form), same layout
+struct Tri21 {
+  double v[21];
+};
+__global__ void field_prepare(const double* __restrict__ C, Tri21 c0, int ntri, long long m,
+                              double* __restrict__ dC64, float* __restrict__ dC32, float* __restrict__ C32) {
+  const long long n = (long long)ntri * m;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int t = (int)(i / m);
+    const double d = C[i] - c0.v[t];
+    dC64[i] = d;
+    dC32[i] = (float)d;
+    C32[i] = (float)C[i];
   }
 }
 

@@ -303,7 +303,10 @@ bool make_plan(int L, FftPlan* plan) {
   while (n % 2 == 0) if (!push(2)) return false;
   for (int r : {3, 5, 7, 11, 13})
     while (n % r == 0) if (!push(r)) return false;
-  if (n != 1) return false;
+  // larger primes: the generic direct-DFT stage
+  for (int r = 17; r * r <= n; r += 2)
+    while (n % r == 0) if (!push(r)) return false;
+  if (n > 1 && !push(n)) return false;
   *plan = p;
   return true;
 }

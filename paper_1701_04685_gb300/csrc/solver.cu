@@ -8,6 +8,7 @@
 // per-load iteration counts are exact.
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -43,6 +44,16 @@ using fh::LoadState;
   } while (0)
 
 namespace {
+
+// NVTX range over a host call (header-only NVTX 3: inert unless a profiler
+// attaches), so that a timeline shows the table build, the phases of a solve
+// and the batched queue launches by name
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr int kThreads = 256;
 constexpr int kHistCap = 65536;
@@ -133,6 +144,20 @@ struct fh_solver {
   // precision (allocated on first use), scalars, block sums, and a copy of
   // the control block with a zero macroscopic strain for operator applications
   int method = 0;
+  // point-by-point stiffness (fh_set_stiffness_field with more than 16 distinct
+  // matrices): C(x), C(x) - C0 (FP64, FP32) and C(x) in FP32, upper triangle
+  // [tri][m]; such solves take the block row pass on the whole-GPU passes
+  bool field = false;
+  double* Cf64 = nullptr;
+  double* dCf64 = nullptr;
+  float* dCf32 = nullptr;
+  float* Cf32 = nullptr;
+  double field_lam[2] = {0, 0}, field_mu[2] = {0, 0};  // ranges over the points (reference-medium rule)
+  // shapes of the block row pass per precision (the warp and plane passes
+  // replace it where they apply, the point-by-point stiffness needs it)
+  int rpb_gen[2] = {1, 1};
+  int row_bpl_gen[2] = {1, 1};
+  size_t row_smem_gen[2] = {0, 0};
   void* kbuf[2] = {nullptr, nullptr};
   fh::KrylovScal* ksc = nullptr;
   double* kpart = nullptr;
@@ -162,6 +187,9 @@ void choose_shapes(fh_solver* s, int prec) {
   s->rpb[prec] = rpb;
   s->row_bpl[prec] = (int)((g.nrows + rpb - 1) / rpb);
   s->row_smem[prec] = row_smem(rpb);
+  s->rpb_gen[prec] = rpb;
+  s->row_bpl_gen[prec] = s->row_bpl[prec];
+  s->row_smem_gen[prec] = s->row_smem[prec];
   // FP32 3-D grids whose contiguous axis is 32, 64, 128 or 256 points long
   // take the warp-per-row pass (FP64 keeps the block pass: its radix-8
   // stages need fewer operations on the narrow FP64 pipe)
@@ -299,7 +327,9 @@ void launch_axis(fh_solver* s, int prec, int a, int mode, int nload) {
 }
 
 // the fused plane pass applies: FP32, an eligible 3-D grid, not disabled (path 3)
-bool use_plane(const fh_solver* s, int prec) { return prec == FH_PREC_FP32 && s->plane[prec] > 0 && !s->no_plane; }
+bool use_plane(const fh_solver* s, int prec) {
+  return prec == FH_PREC_FP32 && s->plane[prec] > 0 && !s->no_plane && !s->field;
+}
 
 // Enqueue the line passes of one iteration (everything between two row passes).
 template <typename T>
@@ -324,15 +354,23 @@ void enqueue_line_passes(fh_solver* s, int prec, int nload, bool plane_ok = true
   for (int a = 1; a <= g.nd - 2; ++a) launch(a, 1);
 }
 
+// the point-by-point stiffness of the constitutive stage (null: phase table)
+template <typename T>
+const T* field_ptr(const fh_solver* s, int form);
+template <>
+const double* field_ptr<double>(const fh_solver* s, int form) { return !s->field ? nullptr : form == 1 ? s->Cf64 : s->dCf64; }
+template <>
+const float* field_ptr<float>(const fh_solver* s, int form) { return !s->field ? nullptr : form == 1 ? s->Cf32 : s->dCf32; }
+
 template <typename T, int NV, bool FIRST>
 void enqueue_row_pass_nv(fh_solver* s, int prec, int nload) {
   const GridInfo& g = s->g;
   using C = typename fh::cplx_t<T>::type;
   const int last = g.nd - 1;
-  const int blocks = nload * s->row_bpl[prec];
-  fh::row_pass<T, NV, FIRST><<<blocks, kThreads, s->row_smem[prec], s->work>>>(
+  const int bpl = s->row_bpl_gen[prec];
+  fh::row_pass<T, NV, FIRST><<<nload * bpl, kThreads, s->row_smem_gen[prec], s->work>>>(
       g, s->ax[last].plan, twp<T>(s->ax[last]), Eptr<T>(s), reinterpret_cast<C*>(s->S), s->phase, dCptr<T>(s), s->ctl,
-      s->st, s->partials, s->hist, s->rpb[prec], s->row_bpl[prec]);
+      s->st, s->partials, s->hist, s->rpb_gen[prec], bpl, nullptr, nullptr, field_ptr<T>(s, s->form));
 }
 
 template <typename T, int P, bool FIRST>
@@ -387,6 +425,11 @@ void enqueue_plane(fh_solver* s, int nload) {
 template <typename T, bool FIRST>
 void enqueue_row_pass(fh_solver* s, int prec, int nload) {
   if constexpr (sizeof(T) == 4) {
+    if (s->field) {   // point-by-point stiffness: the block row pass
+      if (s->g.nv == 3) enqueue_row_pass_nv<T, 3, FIRST>(s, prec, nload);
+      else enqueue_row_pass_nv<T, 6, FIRST>(s, prec, nload);
+      return;
+    }
     if (use_plane(s, prec)) {
       enqueue_plane<FIRST>(s, nload);
       return;
@@ -456,17 +499,25 @@ fh_status set_smem_attrs_nv(fh_solver* s, int prec) {
     fh::set_error("contiguous axis too long for this precision (shared memory)");
     return FH_ERR_UNSUPPORTED;
   }
-  if (s->row_warp[prec] == 0) {
-    CK(cudaFuncSetAttribute(fh::row_pass<T, NV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
-    CK(cudaFuncSetAttribute(fh::row_pass<T, NV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
-    CK(cudaFuncSetAttribute(fh::row_pass<T, NV, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
-  } else if constexpr (sizeof(T) == 4) {
+  if (s->field && s->row_smem_gen[prec] > kMaxSmem) {
+    fh::set_error("contiguous axis too long for the point-by-point stiffness in this precision (shared memory)");
+    return FH_ERR_UNSUPPORTED;
+  }
+  if (s->row_smem_gen[prec] <= kMaxSmem) {   // the block row pass (also taken by point-by-point stiffness)
+    const int rg = (int)s->row_smem_gen[prec];
+    CK(cudaFuncSetAttribute(fh::row_pass<T, NV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, rg));
+    CK(cudaFuncSetAttribute(fh::row_pass<T, NV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, rg));
+    CK(cudaFuncSetAttribute(fh::row_pass<T, NV, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, rg));
+  }
+  if (s->row_warp[prec] != 0) {
+    if constexpr (sizeof(T) == 4) {
     switch (s->row_warp[prec]) {
       case 1: CK((set_warp_attrs<T, 1>(s, prec, rs))); break;
       case 2: CK((set_warp_attrs<T, 2>(s, prec, rs))); break;
       case 4: CK((set_warp_attrs<T, 4>(s, prec, rs))); break;
       case 8: CK((set_warp_attrs<T, 8>(s, prec, rs))); break;
       default: break;
+    }
     }
   }
   size_t lm = 0;
@@ -553,7 +604,7 @@ fh_status run_solve(fh_solver* s, int prec, int nload, int chunk, int max_iter, 
   }
   const int bpl = std::max(1, (int)std::min<long long>((s->g.m + kThreads - 1) / kThreads, 64));
   fh::mean_stress<T><<<nload * bpl, kThreads, 0, s->work>>>(s->g, Eptr<T>(s), s->phase, s->Cp64, s->ctl, s->partials2,
-                                                            s->mstress, bpl);
+                                                            s->mstress, bpl, s->field ? s->Cf64 : nullptr);
   CK(cudaGetLastError());
   CK(cudaEventRecord(s->ev1, s->work));
   *launches = 2 + launched * (1 + line_launches_per_iter(s, prec));
@@ -588,7 +639,7 @@ int enqueue_row_x(fh_solver* s, int prec, int nload, T* X, Control* ctl, T* Wout
   C* S = reinterpret_cast<C*>(s->S);
   const int last = g.nd - 1;
   if constexpr (sizeof(T) == 4) {
-    const int P = s->row_warp[prec];
+    const int P = s->field ? 0 : s->row_warp[prec];
     if (P > 0) {
       const int resident = std::max(1, s->warp_res[prec]) * std::max(1, s->sms);
       const int bpl = std::max(1, std::min(s->row_bpl[prec], resident / nload));
@@ -604,16 +655,17 @@ int enqueue_row_x(fh_solver* s, int prec, int nload, T* X, Control* ctl, T* Wout
       return bpl;
     }
   }
-  const int blocks = nload * s->row_bpl[prec];
+  const int bpl = s->row_bpl_gen[prec];
+  const int blocks = nload * bpl;
   if (g.nv == 3)
-    fh::row_pass<T, 3, FIRST, KINV><<<blocks, kThreads, s->row_smem[prec], s->work>>>(
+    fh::row_pass<T, 3, FIRST, KINV><<<blocks, kThreads, s->row_smem_gen[prec], s->work>>>(
         g, s->ax[last].plan, twp<T>(s->ax[last]), X, S, s->phase, dC_form0<T>(s), ctl, s->st, s->partials, s->hist,
-        s->rpb[prec], s->row_bpl[prec], Wout, Yaux);
+        s->rpb_gen[prec], bpl, Wout, Yaux, field_ptr<T>(s, 0));
   else
-    fh::row_pass<T, 6, FIRST, KINV><<<blocks, kThreads, s->row_smem[prec], s->work>>>(
+    fh::row_pass<T, 6, FIRST, KINV><<<blocks, kThreads, s->row_smem_gen[prec], s->work>>>(
         g, s->ax[last].plan, twp<T>(s->ax[last]), X, S, s->phase, dC_form0<T>(s), ctl, s->st, s->partials, s->hist,
-        s->rpb[prec], s->row_bpl[prec], Wout, Yaux);
-  return s->row_bpl[prec];
+        s->rpb_gen[prec], bpl, Wout, Yaux, field_ptr<T>(s, 0));
+  return bpl;
 }
 
 // W = A X = X + Gamma^p (C - C0) X (the stress with ctl's eps0: zero for the
@@ -701,7 +753,7 @@ fh_status run_bicgstab(fh_solver* s, int prec, int nload, int chunk, int max_ite
   }
   const int bpl = std::max(1, (int)std::min<long long>((s->g.m + kThreads - 1) / kThreads, 64));
   fh::mean_stress<T><<<nload * bpl, kThreads, 0, s->work>>>(s->g, x, s->phase, s->Cp64, s->ctl, s->partials2,
-                                                            s->mstress, bpl);
+                                                            s->mstress, bpl, s->field ? s->Cf64 : nullptr);
   CK(cudaGetLastError());
   CK(cudaEventRecord(s->ev1, s->work));
   *launches = (2 + line_launches_per_iter(s->g)) + 2 + 1 + launched * kry_launches_per_iter(s->g);
@@ -833,7 +885,11 @@ fh_status choose_path(fh_solver* s, int want_path, int want_cs, int* path, int* 
   *path = 1;
   *cs = 0;
   s->no_plane = want_path == 3;
-  if (want_path == 1 || want_path == 3) return FH_OK;
+  if (s->field && want_path == 2) {
+    fh::set_error("the cluster-resident path takes phase ids; a point-by-point stiffness runs on the passes");
+    return FH_ERR_UNSUPPORTED;
+  }
+  if (want_path == 1 || want_path == 3 || s->field) return FH_OK;
   bool ok8 = false, ok16 = false;
   if (want_cs == 0 || want_cs == 16) {
     fh_status rc = cluster_fits<T, 16>(s, &ok16);
@@ -859,7 +915,7 @@ fh_status run_solve_cluster(fh_solver* s, int nload, int cs, long long* launches
   if (rc != FH_OK) return rc;
   const int bpl = std::max(1, (int)std::min<long long>((s->g.m + kThreads - 1) / kThreads, 64));
   fh::mean_stress<T><<<nload * bpl, kThreads, 0, s->work>>>(s->g, Eptr<T>(s), s->phase, s->Cp64, s->ctl, s->partials2,
-                                                            s->mstress, bpl);
+                                                            s->mstress, bpl, s->field ? s->Cf64 : nullptr);
   CK(cudaGetLastError());
   CK(cudaEventRecord(s->ev1, s->work));
   *launches = 2;
@@ -871,7 +927,7 @@ void free_all(fh_solver* s) {
   s->graphs.clear();
   void* ptrs[] = {s->E64, s->E32, s->S, s->phase, s->Cp64, s->dC64, s->dC32, s->Cp32, s->G64, s->G32, s->ctl, s->st,
                   s->partials, s->partials2, s->hist, s->mstress, s->err, s->scratch64, s->qtasks, s->qnext,
-                  s->kbuf[0], s->kbuf[1], s->ksc, s->kpart, s->ctl0};
+                  s->kbuf[0], s->kbuf[1], s->ksc, s->kpart, s->ctl0, s->Cf64, s->dCf64, s->dCf32, s->Cf32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& a : s->ax) {
@@ -1154,7 +1210,7 @@ fh_status fh_solver_create(const fh_pattern* p, const fh_generator* gen, int nlo
   for (int k = 0; k < g.nd; ++k) {
     if (g.dims[k] > 4096) { delete s; fh::set_error("SNF axis longer than 4096"); return FH_ERR_UNSUPPORTED; }
     fh::FftPlan fp;
-    if (!fh::make_plan(g.dims[k], &fp)) { delete s; fh::set_error("SNF axis length has a prime factor > 13"); return FH_ERR_UNSUPPORTED; }
+    if (!fh::make_plan(g.dims[k], &fp)) { delete s; fh::set_error("SNF axis length needs more than 24 radix stages"); return FH_ERR_UNSUPPORTED; }
     s->ax[k].L = fp.L;
     s->ax[k].plan.L = fp.L;
     s->ax[k].plan.np = fp.np;
@@ -1194,7 +1250,8 @@ fh_status fh_solver_create(const fh_pattern* p, const fh_generator* gen, int nlo
   CKS(cudaMalloc(&s->G32, (size_t)g.ntri * g.nhalf * sizeof(float)));
   CKS(cudaMalloc(&s->ctl, sizeof(Control)));
   CKS(cudaMalloc(&s->st, FH_MAX_LOADS * sizeof(LoadState)));
-  const size_t nblk = (size_t)nload_max * std::max(s->row_bpl[0], s->row_bpl[1]);
+  const size_t nblk = (size_t)nload_max * std::max({s->row_bpl[0], s->row_bpl[1], s->row_bpl_gen[0], s->row_bpl_gen[1],
+                                                    2 * g.dims[0]});
   CKS(cudaMalloc(&s->partials, 2 * nblk * sizeof(double)));
   CKS(cudaMalloc(&s->partials2, (size_t)nload_max * 64 * fh::MAXV * sizeof(double)));
   CKS(cudaMalloc(&s->hist, (size_t)nload_max * kHistCap * sizeof(double)));
@@ -1263,6 +1320,7 @@ fh_status fh_set_stiffness_phases(fh_solver* s, const uint8_t* phase, int nphase
   CK(cudaMemcpyAsync(&herr, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->work));
   CK(cudaStreamSynchronize(s->work));
   if (herr != 0) { fh::set_error("phase id >= nphase"); return FH_ERR_ARG; }
+  s->field = false;
   s->nphase = nphase;
   std::memcpy(s->Cp, Cp, sizeof(double) * nphase * nv * nv);
   CK(cudaMemcpy(s->Cp64, s->Cp, sizeof(double) * nphase * nv * nv, cudaMemcpyHostToDevice));
@@ -1273,6 +1331,65 @@ fh_status fh_set_stiffness_phases(fh_solver* s, const uint8_t* phase, int nphase
   s->have_table = false;
   return FH_OK;
 }
+
+}  // extern "C"
+
+namespace {
+
+// More than 16 distinct matrices: keep C(x) itself, upper triangle [tri][m] in
+// FP64 on the device (the differences C(x) - C0 follow in fh_set_reference),
+// after checking every matrix on the host.  Also records the ranges of lambda
+// = C_1122 and mu = C_shear,shear / 2 over the points for the reference-medium
+// rule.
+fh_status set_field_pointwise(fh_solver* s, const double* Ch) {
+  const int nv = s->g.nv, ntri = s->g.ntri;
+  const size_t m = (size_t)s->g.m, per = (size_t)nv * nv;
+  std::vector<double> tri((size_t)ntri * m);
+  double lmin = 1e300, lmax = -1e300, mmin = 1e300, mmax = -1e300;
+  for (size_t i = 0; i < m; ++i) {
+    const double* c = Ch + i * per;
+    int t = 0;
+    for (int a = 0; a < nv; ++a)
+      for (int b = a; b < nv; ++b, ++t) {
+        const double v = c[a * nv + b];
+        if (!std::isfinite(v)) { fh::set_error("non-finite stiffness"); return FH_ERR_ARG; }
+        if (std::fabs(v - c[b * nv + a]) > 1e-12 * (1.0 + std::fabs(v))) {
+          fh::set_error("stiffness is not symmetric (major symmetry)");
+          return FH_ERR_ARG;
+        }
+        tri[(size_t)t * m + i] = v;
+      }
+    const double lam = c[1], mu = 0.5 * c[(nv - 1) * nv + nv - 1];
+    lmin = std::min(lmin, lam); lmax = std::max(lmax, lam);
+    mmin = std::min(mmin, mu); mmax = std::max(mmax, mu);
+  }
+  fh_status rc = join_user(s);
+  if (rc != FH_OK) return rc;
+  const size_t n = (size_t)ntri * m;
+  if (!s->Cf64) {
+    CK(cudaMalloc(&s->Cf64, n * sizeof(double)));
+    CK(cudaMalloc(&s->dCf64, n * sizeof(double)));
+    CK(cudaMalloc(&s->dCf32, n * sizeof(float)));
+    CK(cudaMalloc(&s->Cf32, n * sizeof(float)));
+  }
+  CK(cudaMemcpyAsync(s->Cf64, tri.data(), n * sizeof(double), cudaMemcpyHostToDevice, s->work));
+  CK(cudaMemsetAsync(s->phase, 0, m, s->work));
+  CK(cudaStreamSynchronize(s->work));
+  // the phase table holds the first point's matrix (read by nothing on this path)
+  s->nphase = 1;
+  std::memcpy(s->Cp, Ch, sizeof(double) * per);
+  CK(cudaMemcpy(s->Cp64, s->Cp, sizeof(double) * per, cudaMemcpyHostToDevice));
+  s->field_lam[0] = lmin; s->field_lam[1] = lmax;
+  s->field_mu[0] = mmin; s->field_mu[1] = mmax;
+  s->field = true;
+  s->have_phases = true;
+  s->have_table = false;
+  return FH_OK;
+}
+
+}  // namespace
+
+extern "C" {
 
 fh_status fh_set_stiffness_field(fh_solver* s, const double* C) {
   if (!s || !C) { fh::set_error("null argument"); return FH_ERR_ARG; }
@@ -1297,10 +1414,7 @@ fh_status fh_set_stiffness_field(fh_solver* s, const double* C) {
     int q = 0;
     while (q < nphase && std::memcmp(table + q * per, c, per * sizeof(double)) != 0) ++q;
     if (q == nphase) {
-      if (nphase == kMaxPhases) {
-        fh::set_error("stiffness field holds more than 16 distinct matrices");
-        return FH_ERR_UNSUPPORTED;
-      }
+      if (nphase == kMaxPhases) return set_field_pointwise(s, Ch);
       std::memcpy(table + q * per, c, per * sizeof(double));
       ++nphase;
     }
@@ -1310,6 +1424,7 @@ fh_status fh_set_stiffness_field(fh_solver* s, const double* C) {
 }
 
 fh_status fh_set_reference(fh_solver* s, const double* C0) {
+  NvtxRange range("fh_set_reference (Gamma^p table)");
   if (!s) { fh::set_error("null solver"); return FH_ERR_ARG; }
   if (!s->have_phases) { fh::set_error("set the stiffness before the reference medium"); return FH_ERR_STATE; }
   const int nv = s->g.nv, d = s->g.d;
@@ -1325,6 +1440,10 @@ fh_status fh_set_reference(fh_solver* s, const double* C0) {
       const double mu = 0.5 * C[(nv - 1) * nv + (nv - 1)];
       lmin = std::min(lmin, lam); lmax = std::max(lmax, lam);
       mmin = std::min(mmin, mu); mmax = std::max(mmax, mu);
+    }
+    if (s->field) {
+      lmin = s->field_lam[0]; lmax = s->field_lam[1];
+      mmin = s->field_mu[0]; mmax = s->field_mu[1];
     }
     const double lam0 = 0.5 * (lmin + lmax), mu0 = 0.5 * (mmin + mmax);
     for (int a = 0; a < d; ++a)
@@ -1381,6 +1500,14 @@ fh_status fh_set_reference(fh_solver* s, const double* C0) {
       dc[q * nv * nv + e] = s->Cp[q * nv * nv + e] - c0[e];
       dcf[q * nv * nv + e] = (float)dc[q * nv * nv + e];
     }
+  if (s->field) {   // point-by-point stiffness: C(x) - C0 and the FP32 copies
+    fh::Tri21 c0t{};
+    int t = 0;
+    for (int a = 0; a < nv; ++a)
+      for (int b = a; b < nv; ++b) c0t.v[t++] = c0[a * nv + b];
+    fh::field_prepare<<<1024, kThreads, 0, s->work>>>(s->Cf64, c0t, s->g.ntri, s->g.m, s->dCf64, s->dCf32, s->Cf32);
+    CK(cudaGetLastError());
+  }
   CK(cudaMemcpyAsync(s->dC64, dc, sizeof(double) * s->nphase * nv * nv, cudaMemcpyHostToDevice, s->work));
   CK(cudaMemcpyAsync(s->dC32, dcf, sizeof(float) * s->nphase * nv * nv, cudaMemcpyHostToDevice, s->work));
   int herr = 0;
@@ -1477,6 +1604,8 @@ fh_status end_phase(fh_solver* s, PhaseOut* out) {
 fh_status solve_phase(fh_solver* s, int nload, const double* eps0, double tol, int max_iter, int prec, int init,
                       int chunk, int want_path, int want_cs, const LoadState* start, PhaseOut* out,
                       int stall_window = 0) {
+  NvtxRange range(s->method == 1 ? (prec == FH_PREC_FP64 ? "BiCGStab FP64" : "BiCGStab FP32")
+                                 : (prec == FH_PREC_FP64 ? "fixed point FP64" : "fixed point FP32"));
   fh_status rc = begin_phase(s, nload, eps0, tol, max_iter, prec, init, chunk, want_path, want_cs, start, out,
                              stall_window);
   if (rc != FH_OK) return rc;
@@ -1625,7 +1754,7 @@ template <typename T>
 fh_status finish_deferred(fh_solver* s, int nload, PhaseOut* out) {
   const int bpl = std::max(1, (int)std::min<long long>((s->g.m + kThreads - 1) / kThreads, 64));
   fh::mean_stress<T><<<nload * bpl, kThreads, 0, s->work>>>(s->g, Eptr<T>(s), s->phase, s->Cp64, s->ctl, s->partials2,
-                                                            s->mstress, bpl);
+                                                            s->mstress, bpl, s->field ? s->Cf64 : nullptr);
   CK(cudaGetLastError());
   CK(cudaEventRecord(s->ev1, s->work));
   CK(cudaMemcpyAsync(s->h_states, s->st, sizeof(LoadState) * nload, cudaMemcpyDeviceToHost, s->work));
@@ -1771,6 +1900,7 @@ fh_status batch_cluster_choice(fh_solver* s, int prec, int* path, int* cs) {
 extern "C" {
 
 fh_status fh_solve(fh_solver* s, int nload, const double* eps0, const fh_solve_opts* opts, fh_result* res) {
+  NvtxRange range("fh_solve");
   fh_status rc = validate_solve(s, nload, eps0, opts);
   if (rc != FH_OK) return rc;
   rc = join_user(s);
@@ -1819,6 +1949,7 @@ fh_status fh_solve(fh_solver* s, int nload, const double* eps0, const fh_solve_o
 
 fh_status fh_solve_batch(fh_solver* const* solvers, int n, const int* nload, const double* const* eps0,
                          const fh_solve_opts* opts, fh_result* res) {
+  NvtxRange range("fh_solve_batch");
   if (!solvers || !nload || !eps0 || !opts || n < 1) { fh::set_error("null argument or empty batch"); return FH_ERR_ARG; }
   for (int i = 0; i < n; ++i) {
     fh_status rc = validate_solve(solvers[i], nload[i], eps0[i], opts);

@@ -164,10 +164,6 @@ def test_error_codes_without_gpu(fh):
     with pytest.raises(fh.FhError) as e:
         fh.Pattern([[1 << 21, 0], [0, 3]])
     assert e.value.status == -3          # FH_ERR_OVERFLOW
-    p = fh.Pattern([[17, 0], [0, 17]])   # axis of prime length 17
-    with pytest.raises(fh.FhError) as e:
-        fh.Solver(p, fh.generator("dirichlet"), 3)
-    assert e.value.status == -8          # FH_ERR_UNSUPPORTED
     with pytest.raises(fh.FhError) as e:
         fh.Pattern([[1 << 16, 0], [0, 1 << 16]])          # |det M| = 2^32
     assert e.value.status == -3

@@ -42,6 +42,13 @@ CASES = [
      [(1.0, 0.3), (50.0, 0.3)], _disk(3, 0.25)),
     ("sheared3d_dlvp", [[6, 2, 0], [0, 6, 2], [0, 0, 10]], {"kind": "dlvp", "alpha": [0.2, 0.3, 0.1]},
      [(1.0, 0.3), (15.0, 0.3)], _disk(3, 0.3)),
+    # axis lengths with prime factors above 13 (direct-DFT stages): 255 = 3 5 17
+    # on one axis (the odd-determinant pattern of the oracle's projection pins),
+    # and 19 x 38 on two axes
+    ("prime17_one_axis", [[15, 4], [0, 17]], {"kind": "dlvp", "alpha": [0.25, 0.25]},
+     [(1.0, 0.3), (8.0, 0.3)], _disk(2, 0.3)),
+    ("prime19_two_axes", [[19, 0], [0, 38]], {"kind": "boxspline", "order": 2, "radius": 2},
+     [(1.0, 0.3), (12.0, 0.3)], _disk(2, 0.25)),
 ]
 
 
