@@ -170,7 +170,7 @@ size_t csize(int prec) { return prec == FH_PREC_FP64 ? sizeof(double2) : sizeof(
 
 size_t plane_smem_of(int P1, int P2) {
   const int N1 = 32 * P1, L = 32 * P2, H = L / 2 + 1;
-  return (size_t)(3 * N1 * H + N1 + L + fh::kPlaneWarps * fh::plane_ws(L)) * sizeof(float2);
+  return (size_t)(3 * N1 * H + N1 + L) * sizeof(float2);
 }
 
 void choose_shapes(fh_solver* s, int prec) {

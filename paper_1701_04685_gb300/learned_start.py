@@ -60,9 +60,10 @@ def make_solver(item, stream=0):
     return s, ids, logE
 
 
-def generate(net, seeds, n, tol=1e-6):
+def generate(net, seeds, n, tol=1e-6, method=0):
     """Inputs (S, 1, n^3) and targets (S, 36, n^3) on the device, one sample per seed
-    holding the six unit-load solutions."""
+    holding the six unit-load solutions (solved with the given method: the fixed
+    point or BiCGStab give the same solution to the tolerance)."""
     import torch
     S = len(seeds)
     X = torch.empty((S, 1, n ** 3), dtype=torch.float32, device="cuda")
@@ -70,7 +71,7 @@ def generate(net, seeds, n, tol=1e-6):
     iters = []
     for j, seed in enumerate(seeds):
         s, ids, logE = make_solver(W.fno3d_item(seed, n=n))
-        out = s.solve(np.eye(6), tol=tol, max_iter=20000, precision=FH_PREC_MIXED)
+        out = s.solve(np.eye(6), tol=tol, max_iter=20000, precision=FH_PREC_MIXED, method=method)
         iters.append([int(i) for i in out["iterations"]])
         net.make_input(torch.from_numpy(ids).cuda(), logE, np.zeros(6), X[j])
         for L in range(6):
@@ -170,6 +171,7 @@ def main():
     ap.add_argument("--batch", type=int, default=4)
     ap.add_argument("--methods", default="0,1", help="solver methods to evaluate (0 fixed point, 1 BiCGStab)")
     ap.add_argument("--val", type=int, default=32, help="held-out seeds that choose the start per method")
+    ap.add_argument("--gen-method", type=int, default=1, help="solver method producing the training solutions")
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
     methods = tuple(int(v) for v in a.methods.split(","))
@@ -178,7 +180,7 @@ def main():
     net = FNO(a.n, 1, 36, a.width, min(a.modes, a.n // 2), a.layers, max_batch=a.batch)
     init_params(net, np.random.default_rng(1234))
     t0 = time.perf_counter()
-    X, T, it_train = generate(net, range(a.train), a.n)
+    X, T, it_train = generate(net, range(a.train), a.n, method=a.gen_method)
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t0
     log(f"generated {6 * X.shape[0]} solutions in {t_gen:.1f} s (mean iterations {it_train.mean():.1f})")
