@@ -108,11 +108,12 @@ typedef struct {
                       the previous solve or set by fh_set_strain (resume)    */
   int chunk;       /* iterations per captured CUDA-graph replay; 0 = 32      */
   int path;        /* 0 = automatic; 1 = whole-GPU passes (one kernel per axis
-                      per iteration, CUDA-graph replays; FP32 3-D grids with
-                      axis-1 and axis-2 lengths in {32, 64, 128} fuse both
-                      inner axes and the constitutive stage into one plane
-                      pass, so an iteration is two kernels); 3 = the same
-                      passes without that fusion; 2 = cluster-resident
+                      per iteration, CUDA-graph replays); 3 = the same, but
+                      FP32 3-D grids with axis-1 and axis-2 lengths in {32, 64,
+                      128} fuse both inner axes and the constitutive stage into
+                      one plane pass per 2-CTA cluster (an iteration is two
+                      kernels; measured slower than path 1 at 128^3, kept for
+                      comparison); 2 = cluster-resident
                       (2-axis grids only: one thread-block cluster per load
                       case holds the fields in distributed shared memory and
                       runs every iteration in one launch).  Automatic picks 2

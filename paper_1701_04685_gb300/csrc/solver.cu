@@ -124,8 +124,8 @@ struct fh_solver {
   // launch shapes per precision (0: fp64, 1: fp32)
   int rpb[2] = {1, 1};
   int row_warp[2] = {0, 0};  // > 0: warp-per-row pass with L = 32 * row_warp
-  int plane[2] = {0, 0};     // 3-D FP32: > 0 = the fused plane pass (axis-1 P, axis-2 P packed as 10 P1 + P2)
-  bool no_plane = false;     // path 3 of the solve in progress: keep the four separate passes
+  int plane[2] = {0, 0};     // 3-D FP32: > 0 = the fused plane pass applies (axis-1 P, axis-2 P packed as 10 P1 + P2)
+  bool plane_on = false;     // path 3 of the solve in progress: take the fused plane pass where it applies
   int warp_res[2] = {0, 0};  // resident blocks per SM of that pass
   int sms = 0;               // multiprocessors of the device
   int row_bpl[2] = {1, 1};
@@ -170,7 +170,7 @@ size_t csize(int prec) { return prec == FH_PREC_FP64 ? sizeof(double2) : sizeof(
 
 size_t plane_smem_of(int P1, int P2) {
   const int N1 = 32 * P1, L = 32 * P2, H = L / 2 + 1;
-  return (size_t)(3 * N1 * H + N1 + L) * sizeof(float2);
+  return (size_t)(3 * N1 * H + N1 + L + fh::kPlaneWarps * fh::plane_ws(L)) * sizeof(float2);
 }
 
 void choose_shapes(fh_solver* s, int prec) {
@@ -326,9 +326,9 @@ void launch_axis(fh_solver* s, int prec, int a, int mode, int nload) {
   launch_line<T>(s, prec, a, mode, (unsigned)blocks, (int)n_outer, (int)n_inner);
 }
 
-// the fused plane pass applies: FP32, an eligible 3-D grid, not disabled (path 3)
+// the fused plane pass applies: FP32, an eligible 3-D grid, asked for (path 3)
 bool use_plane(const fh_solver* s, int prec) {
-  return prec == FH_PREC_FP32 && s->plane[prec] > 0 && !s->no_plane && !s->field;
+  return prec == FH_PREC_FP32 && s->plane[prec] > 0 && s->plane_on && !s->field;
 }
 
 // Enqueue the line passes of one iteration (everything between two row passes).
@@ -552,7 +552,7 @@ fh_status set_smem_attrs(fh_solver* s, int prec) {
 
 template <typename T>
 fh_status get_graph(fh_solver* s, int prec, int nload, int chunk, cudaGraphExec_t* out) {
-  const int variant = s->no_plane ? 2 : 0;   // graphs with and without the plane pass differ
+  const int variant = s->plane_on ? 2 : 0;   // graphs with and without the plane pass differ
   for (auto& e : s->graphs)
     if (e.prec == prec && e.nload == nload && e.chunk == chunk && e.method == variant) {
       *out = e.exec;
@@ -884,7 +884,7 @@ template <typename T>
 fh_status choose_path(fh_solver* s, int want_path, int want_cs, int* path, int* cs) {
   *path = 1;
   *cs = 0;
-  s->no_plane = want_path == 3;
+  s->plane_on = want_path == 3;
   if (s->field && want_path == 2) {
     fh::set_error("the cluster-resident path takes phase ids; a point-by-point stiffness runs on the passes");
     return FH_ERR_UNSUPPORTED;

@@ -155,9 +155,9 @@ def test_full_size_fno3d_fp32_iteration_sampled(fh):
 
 
 # ---------------------------------------------------------------------------
-# the fused plane pass (FP32 3-D grids with axis-1 and axis-2 lengths in
-# {32, 64, 128}): axes 1 and 2 and the constitutive stage in one kernel per
-# plane, an iteration = plane pass + axis-0 pass; path 3 keeps the four passes
+# the fused plane pass (path 3; FP32 3-D grids with axis-1 and axis-2 lengths
+# in {32, 64, 128}): axes 1 and 2 and the constitutive stage in one kernel per
+# plane, an iteration = plane pass + axis-0 pass; path 1 runs the four passes
 # ---------------------------------------------------------------------------
 PLANE_CASES = [WARP_CASES[6], WARP_CASES[7], WARP_CASES[8], WARP_CASES[9]]
 PLANE_IDS = [c[0] for c in PLANE_CASES]
@@ -171,10 +171,10 @@ def test_plane_pass_is_taken_and_agrees_with_four_passes(fh, spec):
     case = _case(spec)
     s = case.product(fh)
     n = 20
-    a = s.solve(case.eps0, tol=0.0, max_iter=n, precision=FP32, path=1)
+    a = s.solve(case.eps0, tol=0.0, max_iter=n, precision=FP32, path=3)
     Ea = [s.get_strain(L).copy() for L in range(case.nload)]
     ha = [s.get_residuals(L) for L in range(case.nload)]
-    b = s.solve(case.eps0, tol=0.0, max_iter=n, precision=FP32, path=3)
+    b = s.solve(case.eps0, tol=0.0, max_iter=n, precision=FP32, path=1)
     # launches: 2 + (iterations of the replayed graph chunks) x (kernels per iteration)
     assert 2 * (a["kernel_launches"] - 2) == b["kernel_launches"] - 2
     for L in range(case.nload):
@@ -184,7 +184,7 @@ def test_plane_pass_is_taken_and_agrees_with_four_passes(fh, spec):
         big = hb > 1e-5
         assert rel(ha[L][big], hb[big]) < 1e-3
     ref = case.oracle_solve(tol=0.0, max_iter=n)
-    s.solve(case.eps0, tol=0.0, max_iter=n, precision=FP32, path=1)
+    s.solve(case.eps0, tol=0.0, max_iter=n, precision=FP32, path=3)
     assert case.strain_error(s, ref["E"]) < TOL32
     assert rel(a["mean_stress"], ref["mean_stress"]) < TOL32
 
@@ -193,7 +193,7 @@ def test_plane_pass_variational_form(fh):
     case = _case(WARP_CASES[7])
     s = case.product(fh)
     n = 25
-    out = s.solve(case.eps0, tol=0.0, max_iter=n, precision=FP32, form=1, path=1)
+    out = s.solve(case.eps0, tol=0.0, max_iter=n, precision=FP32, form=1, path=3)
     ref = OS.solve(case.T, case.Gp, case.Cp_o[case.ids], case.C0_o, case.eps0, tol=0.0, max_iter=n, form="B")
     assert case.strain_error(s, ref["E"]) < TOL32
     assert rel(out["mean_stress"], ref["mean_stress"]) < TOL32
@@ -204,13 +204,13 @@ def test_plane_pass_resume_and_per_load_stop(fh):
     iteration of the four-pass path (the residuals differ by FP32 rounding)."""
     case = _case(WARP_CASES[9])
     s = case.product(fh)
-    s.solve(case.eps0, tol=0.0, max_iter=16, precision=FP32)
+    s.solve(case.eps0, tol=0.0, max_iter=16, precision=FP32, path=3)
     E16 = [s.get_strain(L).copy() for L in range(case.nload)]
-    s.solve(case.eps0, tol=0.0, max_iter=9, precision=FP32)
-    s.solve(case.eps0, tol=0.0, max_iter=7, init=1, precision=FP32)
+    s.solve(case.eps0, tol=0.0, max_iter=9, precision=FP32, path=3)
+    s.solve(case.eps0, tol=0.0, max_iter=7, init=1, precision=FP32, path=3)
     for L in range(case.nload):
         assert np.array_equal(s.get_strain(L), E16[L])
-    a = s.solve(case.eps0, tol=1e-5, max_iter=5000, precision=FP32, path=1)
-    b = s.solve(case.eps0, tol=1e-5, max_iter=5000, precision=FP32, path=3)
+    a = s.solve(case.eps0, tol=1e-5, max_iter=5000, precision=FP32, path=3)
+    b = s.solve(case.eps0, tol=1e-5, max_iter=5000, precision=FP32, path=1)
     assert a["status"] == 0 and b["status"] == 0
     assert np.all(np.abs(a["iterations"] - b["iterations"]) <= 1), (a["iterations"], b["iterations"])
