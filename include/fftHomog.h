@@ -73,6 +73,7 @@ typedef enum {
 
 #define FH_MAX_XI 16
 #define FH_MAX_LOADS 16
+#define FH_TUNE_CANDIDATES 8   /* launch configurations the autotuner times */
 
 typedef struct {
   int kind;                 /* fh_gen_kind                                   */
@@ -137,10 +138,19 @@ typedef struct {
                       of V^f_M that the theorem assumes.                     */
   int tune;        /* 1 with path = cluster = 0 and init = 0: on the first such
                       solve of each bulk precision, time every eligible launch
-                      configuration (passes; clusters of 8 and 16) for 24
-                      iterations of these loads and use the fastest from then
-                      on (see fh_get_tuning).  The trials overwrite the
-                      strain before the actual solve starts from E = 0.      */
+                      configuration for 24 iterations of these loads and use
+                      the fastest from then on (see fh_get_tuning): the
+                      whole-GPU passes with the default shapes and radix
+                      schedules, clusters of 8 and 16 CTAs, the fused plane
+                      pass, and the passes with twice the rows per block of
+                      the block row pass, twice the line tile width, every
+                      axis's radix schedule reversed, or radix-4 stages in
+                      place of radix-8 / radix-2.  The trials overwrite the
+                      strain before the actual solve starts from E = 0.
+                      2 + c (c < FH_TUNE_CANDIDATES): run candidate c of the
+                      list of fh_get_tuning without timing (FH_ERR_UNSUPPORTED
+                      where it does not apply); its shapes stay with the
+                      solver.                                                 */
   int method;      /* 0: the fixed point of Sec. 4 (Basic Scheme).
                       1: BiCGStab (van der Vorst 1992) on the same discrete
                       equation, (I + Gamma^p (C - C0)) E = -Gamma^p (C - C0)
@@ -297,10 +307,15 @@ fh_status fh_get_ceff(const fh_solver* s, double* Ceff, int voigt);
 fh_status fh_get_green(const fh_solver* s, double* G);
 
 /* Autotuner result for a bulk precision (FH_PREC_FP64 or FH_PREC_FP32): the
- * chosen path (0 = not tuned yet) and cluster size, and the measured
- * microseconds per iteration of [passes, cluster 8, cluster 16] (-1 where a
- * configuration does not fit); us_per_iter may be NULL. */
-fh_status fh_get_tuning(const fh_solver* s, int precision, int* path, int* cluster, float* us_per_iter);
+ * chosen path (0 = not tuned yet; 1 passes, 2 cluster-resident, 3 passes with
+ * the fused plane pass), cluster size and candidate index, and the measured
+ * microseconds per iteration of every candidate (-1 where it does not apply):
+ * [0] passes, [1] cluster 8, [2] cluster 16, [3] passes with the plane pass,
+ * [4] twice the rows per block of the block row pass, [5] twice the line tile
+ * width, [6] reversed radix schedules, [7] radix-4 schedules.  candidate and
+ * us_per_iter[FH_TUNE_CANDIDATES] may be NULL. */
+fh_status fh_get_tuning(const fh_solver* s, int precision, int* path, int* cluster, int* candidate,
+                        float* us_per_iter);
 
 /* Residual history r_1..r_n of one load from the last solve: hist[n] host;
  * *n receives the count (hist may be NULL to query it). */

@@ -24,6 +24,7 @@ FH_OK, FH_NOT_CONVERGED, FH_DIVERGED, FH_NONFINITE = 0, 1, 2, 3
 FH_GEN_DIRICHLET, FH_GEN_DLVP, FH_GEN_BOXSPLINE = 0, 1, 2
 FH_PREC_FP64, FH_PREC_FP32, FH_PREC_MIXED = 0, 1, 2
 FH_MAX_LOADS = 16
+FH_TUNE_CANDIDATES = 8
 FH_MAX_XI = 16
 
 _STATUS = {0: "ok", 1: "not converged", 2: "diverged", 3: "non-finite", -1: "invalid argument",
@@ -86,7 +87,7 @@ def library():
             "fh_get_residuals": (I, [P, I, P, P]),
             "fh_profile_passes": (I, [P, I, I, I, P]),
             "fh_solve_batch": (I, [P, I, P, P, C.POINTER(fh_solve_opts), P]),
-            "fh_get_tuning": (I, [P, I, P, P, P]),
+            "fh_get_tuning": (I, [P, I, P, P, P, P]),
             "fh_status_string": (C.c_char_p, [I]),
             "fh_last_error": (C.c_char_p, []),
         }
@@ -345,10 +346,10 @@ class Solver:
         return out
 
     def get_tuning(self, precision):
-        path, cl = C.c_int(), C.c_int()
-        us = (C.c_float * 3)()
-        _check(library().fh_get_tuning(self._h, int(precision), C.byref(path), C.byref(cl), us))
-        return {"path": path.value, "cluster": cl.value, "us_per_iter": list(us)}
+        path, cl, cand = C.c_int(), C.c_int(), C.c_int()
+        us = (C.c_float * FH_TUNE_CANDIDATES)()
+        _check(library().fh_get_tuning(self._h, int(precision), C.byref(path), C.byref(cl), C.byref(cand), us))
+        return {"path": path.value, "cluster": cl.value, "candidate": cand.value, "us_per_iter": list(us)}
 
     def get_residuals(self, load):
         n = C.c_int()

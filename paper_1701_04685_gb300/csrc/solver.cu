@@ -64,7 +64,8 @@ int mandel_nv(int d) { return d == 2 ? 3 : 6; }
 
 struct Axis {
   int L = 1;
-  DevPlan plan{};
+  DevPlan plan{};        // radix schedule of the cluster kernel (and the default)
+  DevPlan planp[2]{};    // radix schedule of the passes per bulk precision (autotuned)
   double2* tw64 = nullptr;
   float2* tw32 = nullptr;
 };
@@ -97,7 +98,8 @@ struct fh_solver {
   // autotuned (path, cluster size) per bulk precision [fp64, fp32]; path 0 = not tuned yet
   int tuned_path[2] = {0, 0};
   int tuned_cs[2] = {0, 0};
-  float tuned_us[2][3] = {};  // per-iteration time of the candidates: passes, cluster 8, cluster 16
+  float tuned_us[2][FH_TUNE_CANDIDATES] = {};  // per-iteration time of each autotuner candidate (-1: not eligible)
+  int tuned_cand[2] = {0, 0};                   // the candidate chosen
   double* G64 = nullptr;
   float* G32 = nullptr;
   Control* ctl = nullptr;
@@ -158,6 +160,15 @@ struct fh_solver {
   int rpb_gen[2] = {1, 1};
   int row_bpl_gen[2] = {1, 1};
   size_t row_smem_gen[2] = {0, 0};
+  // the shapes and radix schedules choose_shapes and make_plan gave, per bulk
+  // precision: the autotuner's candidates start from these
+  struct PassShapes {
+    int rpb_gen, row_bpl_gen;
+    size_t row_smem_gen;
+    int lineW[3], ntiles[3];
+    size_t line_smem[3];
+    fh::DevPlan plans[3];
+  } shape_def[2];
   void* kbuf[2] = {nullptr, nullptr};
   fh::KrylovScal* ksc = nullptr;
   double* kpart = nullptr;
@@ -229,6 +240,26 @@ void choose_shapes(fh_solver* s, int prec) {
   }
 }
 
+void save_default_shapes(fh_solver* s) {
+  for (int prec = 0; prec < 2; ++prec) {
+    fh_solver::PassShapes& d = s->shape_def[prec];
+    d.rpb_gen = s->rpb_gen[prec];
+    d.row_bpl_gen = s->row_bpl_gen[prec];
+    d.row_smem_gen = s->row_smem_gen[prec];
+    for (int a = 0; a < 3; ++a) {
+      d.lineW[a] = s->lineW[prec][a];
+      d.ntiles[a] = s->ntiles[prec][a];
+      d.line_smem[a] = s->line_smem[prec][a];
+      d.plans[a] = s->ax[a].planp[prec];
+    }
+  }
+}
+
+void clear_graphs(fh_solver* s) {
+  for (auto& e : s->graphs) cudaGraphExecDestroy(e.exec);
+  s->graphs.clear();
+}
+
 template <typename T>
 const typename fh::cplx_t<T>::type* twp(const Axis& a);
 template <>
@@ -266,11 +297,11 @@ void launch_line_nv(fh_solver* s, int prec, int a, int mode, unsigned blocks, in
   const size_t sm = s->line_smem[prec][a];
   const int W = s->lineW[prec][a], nt = s->ntiles[prec][a];
   if (mode == 0)
-    fh::line_pass<T, NV, 0><<<blocks, kThreads, sm, s->work>>>(s->g, s->ax[a].plan, twp<T>(s->ax[a]), S, Gptr<T>(s), s->st, a, W, nt, n_outer, n_inner);
+    fh::line_pass<T, NV, 0><<<blocks, kThreads, sm, s->work>>>(s->g, s->ax[a].planp[prec], twp<T>(s->ax[a]), S, Gptr<T>(s), s->st, a, W, nt, n_outer, n_inner);
   else if (mode == 1)
-    fh::line_pass<T, NV, 1><<<blocks, kThreads, sm, s->work>>>(s->g, s->ax[a].plan, twp<T>(s->ax[a]), S, Gptr<T>(s), s->st, a, W, nt, n_outer, n_inner);
+    fh::line_pass<T, NV, 1><<<blocks, kThreads, sm, s->work>>>(s->g, s->ax[a].planp[prec], twp<T>(s->ax[a]), S, Gptr<T>(s), s->st, a, W, nt, n_outer, n_inner);
   else
-    fh::line_pass<T, NV, 2><<<blocks, kThreads, sm, s->work>>>(s->g, s->ax[a].plan, twp<T>(s->ax[a]), S, Gptr<T>(s), s->st, a, W, nt, n_outer, n_inner);
+    fh::line_pass<T, NV, 2><<<blocks, kThreads, sm, s->work>>>(s->g, s->ax[a].planp[prec], twp<T>(s->ax[a]), S, Gptr<T>(s), s->st, a, W, nt, n_outer, n_inner);
 }
 
 template <typename T>
@@ -369,7 +400,7 @@ void enqueue_row_pass_nv(fh_solver* s, int prec, int nload) {
   const int last = g.nd - 1;
   const int bpl = s->row_bpl_gen[prec];
   fh::row_pass<T, NV, FIRST><<<nload * bpl, kThreads, s->row_smem_gen[prec], s->work>>>(
-      g, s->ax[last].plan, twp<T>(s->ax[last]), Eptr<T>(s), reinterpret_cast<C*>(s->S), s->phase, dCptr<T>(s), s->ctl,
+      g, s->ax[last].planp[prec], twp<T>(s->ax[last]), Eptr<T>(s), reinterpret_cast<C*>(s->S), s->phase, dCptr<T>(s), s->ctl,
       s->st, s->partials, s->hist, s->rpb_gen[prec], bpl, nullptr, nullptr, field_ptr<T>(s, s->form));
 }
 
@@ -659,11 +690,11 @@ int enqueue_row_x(fh_solver* s, int prec, int nload, T* X, Control* ctl, T* Wout
   const int blocks = nload * bpl;
   if (g.nv == 3)
     fh::row_pass<T, 3, FIRST, KINV><<<blocks, kThreads, s->row_smem_gen[prec], s->work>>>(
-        g, s->ax[last].plan, twp<T>(s->ax[last]), X, S, s->phase, dC_form0<T>(s), ctl, s->st, s->partials, s->hist,
+        g, s->ax[last].planp[prec], twp<T>(s->ax[last]), X, S, s->phase, dC_form0<T>(s), ctl, s->st, s->partials, s->hist,
         s->rpb_gen[prec], bpl, Wout, Yaux, field_ptr<T>(s, 0));
   else
     fh::row_pass<T, 6, FIRST, KINV><<<blocks, kThreads, s->row_smem_gen[prec], s->work>>>(
-        g, s->ax[last].plan, twp<T>(s->ax[last]), X, S, s->phase, dC_form0<T>(s), ctl, s->st, s->partials, s->hist,
+        g, s->ax[last].planp[prec], twp<T>(s->ax[last]), X, S, s->phase, dC_form0<T>(s), ctl, s->st, s->partials, s->hist,
         s->rpb_gen[prec], bpl, Wout, Yaux, field_ptr<T>(s, 0));
   return bpl;
 }
@@ -1215,9 +1246,11 @@ fh_status fh_solver_create(const fh_pattern* p, const fh_generator* gen, int nlo
     s->ax[k].plan.L = fp.L;
     s->ax[k].plan.np = fp.np;
     for (int q = 0; q < 24; ++q) s->ax[k].plan.r[q] = fp.r[q];
+    s->ax[k].planp[0] = s->ax[k].planp[1] = s->ax[k].plan;
   }
   choose_shapes(s, FH_PREC_FP64);
   choose_shapes(s, FH_PREC_FP32);
+  save_default_shapes(s);
   auto fail = [&](fh_status rc) { free_all(s); delete s; return rc; };
 #define CKS(call)                                                             \
   do {                                                                        \
@@ -1631,7 +1664,10 @@ fh_status validate_solve(fh_solver* s, int nload, const double* eps0, const fh_s
   }
   if (opts->init != 0 && opts->init != 1) { fh::set_error("init must be 0 or 1"); return FH_ERR_ARG; }
   if (opts->form != 0 && opts->form != 1) { fh::set_error("form must be 0 or 1"); return FH_ERR_ARG; }
-  if (opts->tune != 0 && opts->tune != 1) { fh::set_error("tune must be 0 or 1"); return FH_ERR_ARG; }
+  if (opts->tune < 0 || opts->tune >= 2 + FH_TUNE_CANDIDATES) {
+    fh::set_error("tune must be 0, 1, or 2 + a candidate index");
+    return FH_ERR_ARG;
+  }
   if (opts->path < 0 || opts->path > 3 || (opts->cluster != 0 && opts->cluster != 8 && opts->cluster != 16)) {
     fh::set_error("path must be 0..3 and cluster 0, 8 or 16");
     return FH_ERR_ARG;
@@ -1716,13 +1752,104 @@ int status_rank(fh_status st) {
 // in the given bulk precision and keep the fastest per iteration.  The trials
 // overwrite the solver's strain, so they run only for solves that start from
 // E = 0.
+// Autotuner variants of the whole-GPU passes for one bulk precision; each
+// starts from the shapes and radix schedules choose_shapes and make_plan gave.
+// Returns false where the variant does not apply (or changes nothing).
+//   0 the defaults
+//   4 the block row pass with twice the rows per block
+//   5 the block line passes with twice the tile width (columns per block)
+//   6 every axis's radix schedule in reverse order
+//   7 radix-4 stages in place of radix-8 and radix-2 pairs
+bool apply_variant(fh_solver* s, int prec, int var) {
+  const fh_solver::PassShapes& d = s->shape_def[prec];
+  const GridInfo& g = s->g;
+  s->rpb_gen[prec] = d.rpb_gen;
+  s->row_bpl_gen[prec] = d.row_bpl_gen;
+  s->row_smem_gen[prec] = d.row_smem_gen;
+  for (int a = 0; a < 3; ++a) {
+    s->lineW[prec][a] = d.lineW[a];
+    s->ntiles[prec][a] = d.ntiles[a];
+    s->line_smem[prec][a] = d.line_smem[a];
+    s->ax[a].planp[prec] = d.plans[a];
+  }
+  if (var == 0) return true;
+  if (var == 4) {
+    if (s->row_warp[prec] > 0 && !s->field) return false;   // the warp row pass runs instead
+    const int rpb = 2 * d.rpb_gen;
+    if (rpb > g.nrows) return false;
+    const int Lp = prec == FH_PREC_FP64 ? fh::padded_len<3>(g.L) : fh::padded_len<4>(g.L);
+    const size_t sm = (size_t)2 * ((rpb * g.nv + 1) / 2) * Lp * csize(prec);
+    if (sm > kMaxSmem) return false;
+    s->rpb_gen[prec] = rpb;
+    s->row_bpl_gen[prec] = (int)((g.nrows + rpb - 1) / rpb);
+    s->row_smem_gen[prec] = sm;
+    return true;
+  }
+  if (var == 5) {
+    bool any = false;
+    for (int a = 0; a + 1 < g.nd; ++a) {
+      if (col_warp_p(s, prec, a) > 0) continue;
+      const int W = 2 * d.lineW[a];
+      const size_t sm = (size_t)2 * g.nv * W * (g.dims[a] + 1) * csize(prec);
+      if (W > g.H || sm > kMaxSmem) continue;
+      s->lineW[prec][a] = W;
+      s->ntiles[prec][a] = (g.H + W - 1) / W;
+      s->line_smem[prec][a] = sm;
+      any = true;
+    }
+    return any;
+  }
+  bool any = false;
+  for (int a = 0; a < g.nd; ++a) {
+    fh::DevPlan p = d.plans[a];
+    if (var == 6) {
+      std::reverse(p.r, p.r + p.np);
+    } else {   // var 7: the power of two as radix-4 stages (and one radix 2), the odd radices as before
+      int e = 0, odd[24], no = 0;
+      for (int q = 0; q < p.np; ++q) {
+        const int r = p.r[q];
+        if (r == 2) e += 1;
+        else if (r == 4) e += 2;
+        else if (r == 8) e += 3;
+        else odd[no++] = r;
+      }
+      int np = 0;
+      for (int k = 0; k < e / 2 && np < 24; ++k) p.r[np++] = 4;
+      if ((e & 1) && np < 24) p.r[np++] = 2;
+      for (int k = 0; k < no && np < 24; ++k) p.r[np++] = odd[k];
+      if (np != (e / 2) + (e & 1) + no) continue;
+      p.np = np;
+    }
+    bool same = p.np == d.plans[a].np;
+    for (int q = 0; same && q < p.np; ++q) same = p.r[q] == d.plans[a].r[q];
+    if (same) continue;
+    s->ax[a].planp[prec] = p;
+    any = true;
+  }
+  return any;
+}
+
+// Autotuner: time every candidate -- whole-GPU passes (with the default
+// shapes, the fused plane pass, and variants 4-7 of apply_variant) and
+// cluster-resident solves of 8 and 16 CTAs -- for 24 iterations of the actual
+// loads, keep the fastest (its shapes stay with the solver).
+constexpr int kCandPath[FH_TUNE_CANDIDATES] = {1, 2, 2, 3, 1, 1, 1, 1};
+constexpr int kCandCs[FH_TUNE_CANDIDATES] = {0, 8, 16, 0, 0, 0, 0, 0};
+constexpr int kCandVar[FH_TUNE_CANDIDATES] = {0, 0, 0, 0, 4, 5, 6, 7};
+
 fh_status autotune(fh_solver* s, int nload, const double* eps0, int prec, int chunk) {
   const int slot = prec == FH_PREC_FP64 ? 0 : 1;
-  const int cand_path[3] = {1, 2, 2}, cand_cs[3] = {0, 8, 16};
+  const int* cand_path = kCandPath;
+  const int* cand_cs = kCandCs;
+  const int* cand_var = kCandVar;
   const int iters = 24;
   float best = 1e30f;
-  for (int c = 0; c < 3; ++c) {
+  int best_c = 0;
+  for (int c = 0; c < FH_TUNE_CANDIDATES; ++c) {
     s->tuned_us[slot][c] = -1.f;
+    if (!apply_variant(s, prec, cand_var[c])) continue;
+    if (c == 3 && !(prec == FH_PREC_FP32 && s->plane[1] > 0 && !s->field)) continue;
+    clear_graphs(s);
     int path = 1, cs = 0;
     fh_status rc = prec == FH_PREC_FP64 ? choose_path<double>(s, cand_path[c], cand_cs[c], &path, &cs)
                                         : choose_path<float>(s, cand_path[c], cand_cs[c], &path, &cs);
@@ -1737,10 +1864,14 @@ fh_status autotune(fh_solver* s, int nload, const double* eps0, int prec, int ch
     s->tuned_us[slot][c] = us;
     if (us < best) {
       best = us;
-      s->tuned_path[slot] = P.path;
+      best_c = c;
+      s->tuned_path[slot] = cand_path[c] == 3 ? 3 : P.path;
       s->tuned_cs[slot] = P.cs;
     }
   }
+  apply_variant(s, prec, cand_var[best_c]);
+  clear_graphs(s);
+  s->tuned_cand[slot] = best_c;
   return FH_OK;
 }
 
@@ -1910,7 +2041,16 @@ fh_status fh_solve(fh_solver* s, int nload, const double* eps0, const fh_solve_o
   const bool mixed = opts->precision == FH_PREC_MIXED;
   const int prec1 = opts->precision == FH_PREC_FP64 ? FH_PREC_FP64 : FH_PREC_FP32;
   int path1 = opts->path, cs1 = opts->cluster, path2 = opts->path, cs2 = opts->cluster;
-  if (opts->tune && opts->path == 0 && opts->cluster == 0 && opts->init == 0) {
+  if (opts->tune >= 2) {   // a given autotuner candidate, without timing
+    const int c = opts->tune - 2;
+    if (!apply_variant(s, prec1, kCandVar[c])) {
+      fh::set_error("this autotuner candidate does not apply to the grid");
+      return FH_ERR_UNSUPPORTED;
+    }
+    clear_graphs(s);
+    path1 = kCandPath[c];
+    cs1 = kCandCs[c];
+  } else if (opts->tune && opts->path == 0 && opts->cluster == 0 && opts->init == 0) {
     for (int pr : {prec1, mixed ? (int)FH_PREC_FP64 : -1}) {
       if (pr < 0) continue;
       const int slot = pr == FH_PREC_FP64 ? 0 : 1;
@@ -2178,14 +2318,16 @@ fh_status fh_profile_passes(fh_solver* s, int nload, int precision, int reps, do
                                    : profile_passes<float>(s, precision, nload, reps, ms);
 }
 
-fh_status fh_get_tuning(const fh_solver* s, int precision, int* path, int* cluster, float* us_per_iter) {
+fh_status fh_get_tuning(const fh_solver* s, int precision, int* path, int* cluster, int* candidate,
+                        float* us_per_iter) {
   if (!s || !path || !cluster) { fh::set_error("null argument"); return FH_ERR_ARG; }
   if (precision != FH_PREC_FP64 && precision != FH_PREC_FP32) { fh::set_error("precision must be FP64 or FP32"); return FH_ERR_ARG; }
   const int slot = precision == FH_PREC_FP64 ? 0 : 1;
   *path = s->tuned_path[slot];
   *cluster = s->tuned_cs[slot];
+  if (candidate) *candidate = s->tuned_cand[slot];
   if (us_per_iter)
-    for (int c = 0; c < 3; ++c) us_per_iter[c] = s->tuned_us[slot][c];
+    for (int c = 0; c < FH_TUNE_CANDIDATES; ++c) us_per_iter[c] = s->tuned_us[slot][c];
   return FH_OK;
 }
 

@@ -380,17 +380,38 @@ def test_variational_form_matches_oracle(fh, spec, path):
 
 
 def test_autotuner_picks_a_measured_configuration(fh):
-    """tune=1 times passes and clusters of 8 and 16, keeps the fastest, and the tuned
-    solve agrees with the oracle."""
+    """tune=1 times every eligible candidate (passes with their shape and radix
+    variants, clusters of 8 and 16), keeps the fastest, and the tuned solve agrees
+    with the oracle."""
     case = Case.from_workload(W.dlvp_sheared())
     s = case.product(fh)
     out = s.solve(case.eps0, tol=0.0, max_iter=30, precision=fh.FH_PREC_FP64, tune=1)
     t = s.get_tuning(fh.FH_PREC_FP64)
     assert t["path"] in (1, 2)
     us = [u for u in t["us_per_iter"] if u > 0]
-    assert len(us) >= 2
-    chosen = {1: 0, 2: 1 if t["cluster"] == 8 else 2}[t["path"]]
-    assert t["us_per_iter"][chosen] == min(us)
-    assert out["path"] == t["path"]
+    assert len(us) >= 4
+    assert t["us_per_iter"][t["candidate"]] == min(us)
+    assert out["path"] == (2 if t["path"] == 2 else 1)
     ref = case.oracle_solve(tol=0.0, max_iter=30)
     assert case.strain_error(s, ref["E"]) < TOL64
+
+
+@pytest.mark.parametrize("spec", [CASES[1], CASES[5], CASES[7], CASES[8]], ids=[CASES[i][0] for i in (1, 5, 7, 8)])
+def test_every_autotuner_candidate_matches_oracle(fh, spec):
+    """Each candidate the autotuner may choose (tune = 2 + c) gives the oracle's
+    iterates in FP64 (shapes and radix schedules only change the launch)."""
+    case = _case(spec)
+    ref = case.oracle_solve(tol=0.0, max_iter=12)
+    ran = 0
+    for c in range(fh.FH_TUNE_CANDIDATES):
+        s = case.product(fh)
+        try:
+            s.solve(case.eps0, tol=0.0, max_iter=12, precision=fh.FH_PREC_FP64, tune=2 + c)
+        except fh.FhError as e:
+            assert e.status == -8      # the candidate does not apply to this grid
+            s.close()
+            continue
+        assert case.strain_error(s, ref["E"]) < TOL64, c
+        ran += 1
+        s.close()
+    assert ran >= 2
