@@ -17,6 +17,10 @@ stages, and mixed (FP32 iterations, then FP64 iterations to the same tolerance: 
 The line also carries the 2-D anisotropic workload (M = [[128,32],[0,128]], dlVP, 3 loads) and
 the batched 2-D workload (512 microstructures), each with its own modes.
 
+BiCGStab on the same equation (fh_solve_opts.method = 1, the Krylov solver the paper's introduction
+cites) is timed beside the fixed point as the modes bicgstab_mixed and bicgstab_fp64: same stopping
+rule, its iterations are two operator applications each.
+
 Prints one JSON line (rank 0).  --impl reference runs the FP64 CPU oracle on a bounded sample of
 the headline workload instead.
 """
@@ -67,7 +71,8 @@ def parse():
     ap.add_argument("--no-2d", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-cluster", type=int, default=0)
-    ap.add_argument("--modes", default="mixed,fp32,fp64", help="precision modes of the headline workload")
+    ap.add_argument("--modes", default="mixed,fp32,fp64,bicgstab_mixed,bicgstab_fp64",
+                    help="modes of the headline workload: precision (fixed point), or bicgstab_<precision>")
     ap.add_argument("--only-headline", action="store_true", help="skip every extra section")
     ap.add_argument("--ncu-iteration", action="store_true",
                     help="profiling aid: set up the headline workload, run 3 FP32 iterations, then launch each "
@@ -321,9 +326,12 @@ def run_headline(fh, args, dist, local_rank):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
 
     def step_fn(mode):
+        method = 1 if mode.startswith("bicgstab_") else 0
+        pm = prec[mode.split("_")[-1]]
+
         def step():
             s.set_reference(None)                 # Gamma^p table (FP64, on the device)
-            return s.solve(eps0, tol=args.tol, max_iter=20000, precision=prec[mode])
+            return s.solve(eps0, tol=args.tol, max_iter=20000, precision=pm, method=method)
         return step
 
     modes = [m for m in args.modes.split(",") if m]
@@ -332,7 +340,7 @@ def run_headline(fh, args, dist, local_rank):
     results, clocks = {}, None
     for mode in [args.mode] + [m for m in modes if m != args.mode]:
         head = mode == args.mode
-        steps = args.steps if head else (1 if mode == "fp64" else min(args.steps, 3))
+        steps = args.steps if head else (1 if mode.endswith("fp64") else min(args.steps, 3))
         warm = args.warmup if head else 1
         if dist:
             dist.barrier()
@@ -347,6 +355,8 @@ def run_headline(fh, args, dist, local_rank):
         ce = s.get_ceff()
         last = outs[-1]
         results[mode] = {"value": vox / (total_ms * 1e-3), "ms_per_step": total_ms / steps, "steps": steps,
+                         "method": "BiCGStab (iterations = 2 operator applications each)" if mode.startswith("bicgstab")
+                         else "fixed point",
                          "iterations": [int(x) for x in last["iterations"]], "status": int(last["status"]),
                          "gpu_launches_per_step": int(last["kernel_launches"]) + 1,
                          "ceff_rel_err_vs_converged_oracle": None if ref is None else frob_rel(ce, ref["ceff_converged"]),
@@ -453,10 +463,11 @@ def run_2d(fh, args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     steps = min(args.steps, 10)
     out = {"workload": WORKLOAD_2D, "modes": {}}
-    for mode in ("fp64", "fp32", "mixed"):
+    for mode in ("fp64", "fp32", "mixed", "bicgstab_mixed"):
         def step():
             s.set_reference(None)
-            return s.solve(np.eye(3), tol=args.tol, max_iter=20000, precision=prec[mode])
+            return s.solve(np.eye(3), tol=args.tol, max_iter=20000, precision=prec[mode.split("_")[-1]],
+                           method=1 if mode.startswith("bicgstab") else 0)
         times, outs, _ = timed_steps(step, steps, min(args.warmup, 2), flush)
         tot = float(np.sum(times))
         vox = sum(int(np.sum(o["iterations"])) * p.m for o in outs)

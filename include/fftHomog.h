@@ -386,8 +386,15 @@ fh_status fh_fno_set_params(fh_fno* f, const float* params);
 fh_status fh_fno_get_params(const fh_fno* f, float* params);
 fh_status fh_fno_get_grads(const fh_fno* f, float* grads);
 fh_status fh_fno_zero_grad(fh_fno* f);
-/* y = network(x) for `batch` samples (x, y device). */
+/* y = network(x) for `batch` samples (x, y device).  FH_ERR_TIMEOUT when a
+ * tensor-core layer's bounded wait for its MMAs gave up (y not valid). */
 fh_status fh_fno_forward(fh_fno* f, int batch, const float* x, float* y);
+/* The hidden 1 x 1 layers W_l v + w_l run on the tensor cores (tcgen05, BF16
+ * weights as above, each FP32 activation split into three BF16 terms, FP32
+ * accumulation in tensor memory) when width is 16, 32 or 64 and n^3 is a
+ * multiple of 128; enable = 0 selects the SIMT layers (default 1).  Not in
+ * the paper: the network is this library's own. */
+fh_status fh_fno_set_tensor_cores(fh_fno* f, int enable);
 /* Forward and backward of the mean squared error against `target`
  * (mean over samples, channels and voxels); the loss goes to *loss (host,
  * may be NULL) and the gradient is ADDED to the accumulated gradient. */

@@ -412,6 +412,7 @@ def _sig_fno():
         "fh_fno_get_grads": (I, [P, P]),
         "fh_fno_zero_grad": (I, [P]),
         "fh_fno_forward": (I, [P, I, P, P]),
+        "fh_fno_set_tensor_cores": (I, [P, I]),
         "fh_fno_loss_grad": (I, [P, I, P, P, P]),
         "fh_fno_adam_step": (I, [P, C.c_float, C.c_float, C.c_float, C.c_float, I]),
         "fh_fno_make_input": (I, [P, P, I, P, P, P]),
@@ -427,7 +428,7 @@ def _sig_fno():
 
 FNO_SYMBOLS = ["fh_fno_create", "fh_fno_destroy", "fh_fno_param_count", "fh_fno_set_params", "fh_fno_get_params",
                "fh_fno_get_grads", "fh_fno_zero_grad", "fh_fno_forward", "fh_fno_loss_grad", "fh_fno_adam_step",
-               "fh_fno_make_input", "fh_get_strain_f32", "fh_set_strain_f32"]
+               "fh_fno_make_input", "fh_fno_set_tensor_cores", "fh_get_strain_f32", "fh_set_strain_f32"]
 
 
 class FNO:
@@ -463,6 +464,10 @@ class FNO:
         out = np.empty(self.nparam, dtype=np.float32)
         _check(library().fh_fno_get_grads(self._h, _ptr(out)))
         return out
+
+    def set_tensor_cores(self, enable):
+        """Hidden 1 x 1 layers on the tensor cores (tcgen05) or as SIMT loops."""
+        _check(library().fh_fno_set_tensor_cores(self._h, int(bool(enable))))
 
     def zero_grad(self):
         _check(library().fh_fno_zero_grad(self._h))

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "internal.hpp"
+#include "fno_tc.cuh"
 
 namespace {
 
@@ -474,6 +475,11 @@ struct fh_fno {
   float* gb = nullptr;      // [B][W][N3]
   double* part = nullptr;
   int nparts = 0;
+  // hidden 1 x 1 layers on the tensor cores (fno_tc.cuh) where the width is
+  // 16, 32 or 64 and N^3 is a multiple of 128; tc_err is set by a kernel whose
+  // bounded wait gave up
+  bool tensor_cores = true;
+  int* tc_err = nullptr;
 };
 
 namespace {
@@ -508,6 +514,23 @@ fh_status spectral_forward(fh_fno* f, int B, int l, const float* a, float2* coef
   return FH_OK;
 }
 
+// a tensor-core layer whose bounded wait gave up leaves an error word
+fh_status tc_status(fh_fno* f) {
+  int h = 0;
+  FCK(cudaMemcpy(&h, f->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h != 0) {
+    FCK(cudaMemset(f->tc_err, 0, sizeof(int)));
+    fh::set_error("a tensor-core layer's wait for its MMAs gave up");
+    return FH_ERR_TIMEOUT;
+  }
+  return FH_OK;
+}
+
+bool use_tc(const fh_fno* f) {
+  const FnoDims& d = f->d;
+  return f->tensor_cores && (d.W == 16 || d.W == 32 || d.W == 64) && d.N3 % fhtc::kTcTile == 0;
+}
+
 fh_status forward_all(fh_fno* f, int B, const float* x) {
   const FnoDims& d = f->d;
   const size_t act = (size_t)B * d.W * d.N3;
@@ -518,9 +541,24 @@ fh_status forward_all(fh_fno* f, int B, const float* x) {
     const float* vl = f->v + (size_t)l * act;
     fh_status rc = spectral_forward(f, B, l, vl, f->vh + (size_t)l * B * d.W * d.NM, f->spec);
     if (rc != FH_OK) return rc;
-    k_pointwise<true><<<grid_for(tot), kT, (size_t)d.W * d.W * 4, f->stream>>>(
-        B, d.N3, d.W, d.W, f->Wbf + (size_t)l * d.W * d.W, f->prm + f->off_w + (size_t)l * d.W, vl, f->spec,
-        f->u + (size_t)l * act, f->v + (size_t)(l + 1) * act, 1);
+    if (use_tc(f)) {
+      const int ntiles = B * (d.N3 / fhtc::kTcTile);
+      const int grid = std::min(ntiles, 152 * 4);
+      const __nv_bfloat16* Wl = f->Wbf + (size_t)l * d.W * d.W;
+      const float* wl = f->prm + f->off_w + (size_t)l * d.W;
+      float* ul = f->u + (size_t)l * act;
+      float* vn = f->v + (size_t)(l + 1) * act;
+      if (d.W == 16)
+        fhtc::k_pointwise_tc<16><<<grid, fhtc::kTcThreads, 0, f->stream>>>(B, d.N3, Wl, wl, vl, f->spec, ul, vn, 1, f->tc_err);
+      else if (d.W == 32)
+        fhtc::k_pointwise_tc<32><<<grid, fhtc::kTcThreads, 0, f->stream>>>(B, d.N3, Wl, wl, vl, f->spec, ul, vn, 1, f->tc_err);
+      else
+        fhtc::k_pointwise_tc<64><<<grid, fhtc::kTcThreads, 0, f->stream>>>(B, d.N3, Wl, wl, vl, f->spec, ul, vn, 1, f->tc_err);
+    } else {
+      k_pointwise<true><<<grid_for(tot), kT, (size_t)d.W * d.W * 4, f->stream>>>(
+          B, d.N3, d.W, d.W, f->Wbf + (size_t)l * d.W * d.W, f->prm + f->off_w + (size_t)l * d.W, vl, f->spec,
+          f->u + (size_t)l * act, f->v + (size_t)(l + 1) * act, 1);
+    }
   }
   k_pointwise<false><<<grid_for(tot), kT, (size_t)d.cout * d.W * 4, f->stream>>>(
       B, d.N3, d.W, d.cout, f->prm + f->off_Q, f->prm + f->off_q, f->v + (size_t)d.L * act, nullptr, nullptr, f->y, 0);
@@ -592,6 +630,8 @@ fh_status fh_fno_create(int n, int cin, int cout, int width, int modes, int laye
   if ((e = cudaMalloc(&f->gb, act * 4)) != cudaSuccess) return fail(e);
   f->nparts = 152 * 16;
   if ((e = cudaMalloc(&f->part, f->nparts * sizeof(double))) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&f->tc_err, sizeof(int))) != cudaSuccess) return fail(e);
+  if ((e = cudaMemset(f->tc_err, 0, sizeof(int))) != cudaSuccess) return fail(e);
   cudaMemset(f->prm, 0, o * 4);
   cudaMemset(f->grd, 0, o * 4);
   cudaMemset(f->m1, 0, o * 4);
@@ -621,7 +661,7 @@ fh_status fh_fno_create(int n, int cin, int cout, int width, int modes, int laye
 void fh_fno_destroy(fh_fno* f) {
   if (!f) return;
   void* ptrs[] = {f->prm, f->grd, f->m1, f->m2, f->Wbf, f->Rbf, f->tw, f->v, f->u, f->vh, f->spec,
-                  f->Yy, f->cf, f->gin, f->y, f->gy, f->ga, f->gb, f->part};
+                  f->Yy, f->cf, f->gin, f->y, f->gy, f->ga, f->gb, f->part, f->tc_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete f;
@@ -717,6 +757,12 @@ fh_status fh_fno_forward(fh_fno* f, int batch, const float* x, float* y) {
   if (rc != FH_OK) return rc;
   FCK(cudaMemcpyAsync(y, f->y, (size_t)batch * f->d.cout * f->d.N3 * 4, cudaMemcpyDefault, f->stream));
   FCK(cudaStreamSynchronize(f->stream));
+  return tc_status(f);
+}
+
+fh_status fh_fno_set_tensor_cores(fh_fno* f, int enable) {
+  if (!f || (enable != 0 && enable != 1)) { fh::set_error("null network or enable not 0/1"); return FH_ERR_ARG; }
+  f->tensor_cores = enable != 0;
   return FH_OK;
 }
 
@@ -773,7 +819,7 @@ fh_status fh_fno_loss_grad(fh_fno* f, int batch, const float* x, const float* ta
     for (double p : parts) s += p;
     *loss = s / (double)ny;
   }
-  return FH_OK;
+  return tc_status(f);
 }
 
 fh_status fh_fno_adam_step(fh_fno* f, float lr, float beta1, float beta2, float eps, int step) {

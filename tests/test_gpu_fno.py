@@ -125,3 +125,47 @@ def test_make_input_channels(fh):
     assert np.allclose(xc[0], np.where(np.arange(512) % 2 == 1, 1.0, 0.0))
     for c in range(6):
         assert np.allclose(xc[c + 1], e0[c])
+
+
+def _params(rng, cin, cout, width, modes, layers):
+    p = OF.Params(cin, cout, width, modes, layers)
+    p.P = rng.standard_normal(p.P.shape) / np.sqrt(cin)
+    p.p = 0.1 * rng.standard_normal(p.p.shape)
+    p.W = bf16(rng.standard_normal(p.W.shape) / np.sqrt(width))
+    p.w = 0.1 * rng.standard_normal(p.w.shape)
+    s = 1.0 / width
+    p.R = bf16(s * rng.standard_normal(p.R.shape)) + 1j * bf16(s * rng.standard_normal(p.R.shape))
+    p.Q = rng.standard_normal(p.Q.shape) / np.sqrt(width)
+    p.q = 0.1 * rng.standard_normal(p.q.shape)
+    p.set_flat(p.flat().astype(np.float32).astype(np.float64))
+    return p
+
+
+@pytest.mark.parametrize("n,width", [(16, 16), (16, 32), (32, 32)])
+def test_tensor_core_layers_match_simt_layers_and_oracle(fh, n, width):
+    """The hidden 1 x 1 layers on tcgen05 (split-BF16 activations, FP32
+    accumulation in tensor memory) against the SIMT layers and the FP64 network
+    oracle, forward and loss."""
+    import torch
+    rng = np.random.default_rng(21 + n + width)
+    p = _params(rng, 1, 6, width, 4, 2)
+    net = fh.FNO(n, 1, 6, width, 4, 2, max_batch=2)
+    net.set_params(p.flat().astype(np.float32))
+    xs = rng.standard_normal((2, 1, n, n, n)).astype(np.float32)
+    x = torch.from_numpy(xs.reshape(2, 1, -1)).cuda()
+    y_tc = torch.empty((2, 6, n ** 3), dtype=torch.float32, device="cuda")
+    y_simt = torch.empty_like(y_tc)
+    net.set_tensor_cores(True)
+    net.forward(x, y_tc)
+    t = torch.zeros_like(y_tc)
+    l_tc = net.loss_grad(x, t)
+    net.set_tensor_cores(False)
+    net.forward(x, y_simt)
+    l_simt = net.loss_grad(x, t)
+    a, b = y_tc.cpu().numpy(), y_simt.cpu().numpy()
+    assert np.abs(a - b).max() / np.abs(b).max() < 2e-6
+    assert abs(l_tc - l_simt) / l_simt < 1e-5
+    for k in range(2):
+        ref = OF.forward(p, xs[k].astype(np.float64)).reshape(6, -1)
+        assert np.abs(a[k] - ref).max() / np.abs(ref).max() < 2e-5
+    net.close()
