@@ -56,6 +56,7 @@ struct NvtxRange {
 };
 
 constexpr int kThreads = 256;
+constexpr int kMeanBlocks = 512;   // blocks per load of the mean-stress reduction
 constexpr int kHistCap = 65536;
 constexpr size_t kMaxSmem = 227 * 1024;
 constexpr int kMaxPhases = 16;
@@ -633,7 +634,7 @@ fh_status run_solve(fh_solver* s, int prec, int nload, int chunk, int max_iter, 
       return FH_ERR_INTERNAL;
     }
   }
-  const int bpl = std::max(1, (int)std::min<long long>((s->g.m + kThreads - 1) / kThreads, 64));
+  const int bpl = std::max(1, (int)std::min<long long>((s->g.m + kThreads - 1) / kThreads, kMeanBlocks));
   fh::mean_stress<T><<<nload * bpl, kThreads, 0, s->work>>>(s->g, Eptr<T>(s), s->phase, s->Cp64, s->ctl, s->partials2,
                                                             s->mstress, bpl, s->field ? s->Cf64 : nullptr);
   CK(cudaGetLastError());
@@ -782,7 +783,7 @@ fh_status run_bicgstab(fh_solver* s, int prec, int nload, int chunk, int max_ite
       return FH_ERR_INTERNAL;
     }
   }
-  const int bpl = std::max(1, (int)std::min<long long>((s->g.m + kThreads - 1) / kThreads, 64));
+  const int bpl = std::max(1, (int)std::min<long long>((s->g.m + kThreads - 1) / kThreads, kMeanBlocks));
   fh::mean_stress<T><<<nload * bpl, kThreads, 0, s->work>>>(s->g, x, s->phase, s->Cp64, s->ctl, s->partials2,
                                                             s->mstress, bpl, s->field ? s->Cf64 : nullptr);
   CK(cudaGetLastError());
@@ -944,7 +945,7 @@ fh_status run_solve_cluster(fh_solver* s, int nload, int cs, long long* launches
   CK(cudaEventRecord(s->ev0, s->work));
   fh_status rc = cs == 16 ? launch_cluster<T, 16>(s, nload) : launch_cluster<T, 8>(s, nload);
   if (rc != FH_OK) return rc;
-  const int bpl = std::max(1, (int)std::min<long long>((s->g.m + kThreads - 1) / kThreads, 64));
+  const int bpl = std::max(1, (int)std::min<long long>((s->g.m + kThreads - 1) / kThreads, kMeanBlocks));
   fh::mean_stress<T><<<nload * bpl, kThreads, 0, s->work>>>(s->g, Eptr<T>(s), s->phase, s->Cp64, s->ctl, s->partials2,
                                                             s->mstress, bpl, s->field ? s->Cf64 : nullptr);
   CK(cudaGetLastError());
@@ -1286,7 +1287,7 @@ fh_status fh_solver_create(const fh_pattern* p, const fh_generator* gen, int nlo
   const size_t nblk = (size_t)nload_max * std::max({s->row_bpl[0], s->row_bpl[1], s->row_bpl_gen[0], s->row_bpl_gen[1],
                                                     2 * g.dims[0]});
   CKS(cudaMalloc(&s->partials, 2 * nblk * sizeof(double)));
-  CKS(cudaMalloc(&s->partials2, (size_t)nload_max * 64 * fh::MAXV * sizeof(double)));
+  CKS(cudaMalloc(&s->partials2, (size_t)nload_max * kMeanBlocks * fh::MAXV * sizeof(double)));
   CKS(cudaMalloc(&s->hist, (size_t)nload_max * kHistCap * sizeof(double)));
   CKS(cudaMalloc(&s->mstress, FH_MAX_LOADS * fh::MAXV * sizeof(double)));
   CKS(cudaMalloc(&s->err, sizeof(int)));
@@ -1688,6 +1689,12 @@ fh_status validate_solve(fh_solver* s, int nload, const double* eps0, const fh_s
 
 int chunk_of(const fh_solve_opts* opts) { return opts->chunk > 0 ? std::min(opts->chunk, 1024) : 32; }
 
+// The FP64 phase of the mixed mode usually needs one or two iterations: its
+// graph replays two at a time, so that the loads that have stopped do not run
+// through a long chunk of early-exit passes (each FP64 row pass still
+// launches its blocks and reduces their partial sums)
+int polish_chunk(int chunk) { return std::min(chunk, 2); }
+
 // start states of the FP64 step of the mixed mode: continue every load's count
 void polish_start(const PhaseOut& A, LoadState* st0) {
   for (int l = 0; l < A.nload; ++l) {
@@ -1883,7 +1890,7 @@ namespace {
 // begin_phase does for a solve it runs itself.
 template <typename T>
 fh_status finish_deferred(fh_solver* s, int nload, PhaseOut* out) {
-  const int bpl = std::max(1, (int)std::min<long long>((s->g.m + kThreads - 1) / kThreads, 64));
+  const int bpl = std::max(1, (int)std::min<long long>((s->g.m + kThreads - 1) / kThreads, kMeanBlocks));
   fh::mean_stress<T><<<nload * bpl, kThreads, 0, s->work>>>(s->g, Eptr<T>(s), s->phase, s->Cp64, s->ctl, s->partials2,
                                                             s->mstress, bpl, s->field ? s->Cf64 : nullptr);
   CK(cudaGetLastError());
@@ -2081,7 +2088,8 @@ fh_status fh_solve(fh_solver* s, int nload, const double* eps0, const fh_solve_o
     // the residual of the FP32 result, so it also removes the FP32 rounding
     LoadState st0[FH_MAX_LOADS];
     polish_start(A, st0);
-    rc = solve_phase(s, nload, eps0, opts->tol, opts->max_iter, FH_PREC_FP64, 1, chunk, path2, cs2, st0, &B);
+    rc = solve_phase(s, nload, eps0, opts->tol, opts->max_iter, FH_PREC_FP64, 1, polish_chunk(chunk), path2, cs2,
+                     st0, &B);
     if (rc != FH_OK) return rc;
   }
   return finish_solve(s, nload, eps0, A, &B, mixed, res);
@@ -2153,7 +2161,8 @@ fh_status fh_solve_batch(fh_solver* const* solvers, int n, const int* nload, con
         fh_status rc = batch_cluster_choice(solvers[i], FH_PREC_FP64, &p2, &c2);
         if (rc != FH_OK) return rc;
       }
-      fh_status rc = begin_phase(solvers[i], nload[i], eps0[i], opts->tol, opts->max_iter, FH_PREC_FP64, 1, chunk, p2,
+      fh_status rc = begin_phase(solvers[i], nload[i], eps0[i], opts->tol, opts->max_iter, FH_PREC_FP64, 1,
+                                 polish_chunk(chunk), p2,
                                  c2, st0, &B[i], 0, true);
       if (rc != FH_OK) return rc;
       if (B[i].path == 2) deferred2.push_back(i);
