@@ -18,7 +18,7 @@ LIB = os.path.join(OUT_DIR, "libffthomog.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["solver.cu", "lattice.cpp", "noalloc.cu", "fno.cu"]
-HEADERS = ["internal.hpp", "kernels.cuh", "fft.cuh", "cluster.cuh", "warprow.cuh", "linewarp.cuh"]
+HEADERS = ["internal.hpp", "kernels.cuh", "fft.cuh", "cluster.cuh", "warprow.cuh", "linewarp.cuh", "colpass2.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,201 @@
+// Two-step column pass for 3-D grids (n_v = 6) in FP32, for axes of
+// N = R1 R2 points (32 = 4 x 8, 64 = 8 x 8, 128 = 8 x 16).
+//
+// Same job as line_pass_warp6 (forward, inverse, or forward + Green step +
+// inverse along one strided axis of the half spectra, kColTile adjacent
+// columns of one load and all six components per block), with the length-N
+// DFT of each column split as N = R1 R2 (the four-step factorisation):
+// with j = j2 + R2 j1 and k = k1 + R1 k2,
+//   X[k1 + R1 k2] = sum_j2 w_R2^{j2 k2} w_N^{j2 k1} sum_j1 w_R1^{j1 k1} x[j2 + R2 j1].
+//   stage A - one thread per (column, j2): the R1 points x[j2 + R2 j1] come
+//             straight from global memory (the eight columns of a tile are
+//             adjacent, so eight lanes read 64 contiguous bytes), an R1-point
+//             DFT in registers, the twiddles w_N^{j2 k1}, one store to shared
+//             memory;
+//   stage B - one thread per (column, k1): the R2 values of row k1 from
+//             shared memory, an R2-point DFT in registers, and the
+//             frequencies k1 + R1 k2 straight to global memory.
+// Each value passes through shared memory once (one store, one load) and no
+// lane exchange is needed.  MODE 2 (axis 0) keeps the spectrum in shared
+// memory, runs the Green step E^ = -Gamma^p tau^ (E^_0 = 0) with one thread
+// per (frequency, column), and takes the inverse in the mirror order (stage B
+// inverse with the twiddles after it, then stage A inverse, writing the
+// points in natural order).  Inverse transforms are unnormalised.
+//
+// Shared memory: line (component c, column w) = c kColTile + w holds the
+// R1 rows of R2 values at padded offsets j2 + (R2 + 1) k1, LS entries per line
+// with LS = 4 mod 16 (in float2): the stage A stores (8 columns x 4 values of
+// j2 per warp), the stage B loads (8 columns x 4 rows) and the Green step's
+// loads each touch every bank pair exactly twice per warp.
+#pragma once
+
+#include "linewarp.cuh"
+
+namespace fh {
+
+template <int R1, int R2>
+struct Col2 {
+  static constexpr int N = R1 * R2;
+  static constexpr int RMIN = R1 < R2 ? R1 : R2;
+  static constexpr int LINES = 6 * kColTile;                 // 48 lines per block
+  static constexpr int THREADS = LINES * RMIN;
+  static constexpr int A_PER = LINES * R2 / THREADS;         // stage A tasks per thread
+  static constexpr int B_PER = LINES * R1 / THREADS;         // stage B tasks per thread
+  static constexpr int LS = ((N + R1 + 11) / 16) * 16 + 4;   // >= N + R1, = 4 mod 16
+  static_assert(A_PER * THREADS == LINES * R2 && B_PER * THREADS == LINES * R1, "uneven task split");
+  static_assert(LS >= N + R1 && LS % 16 == 4, "line stride");
+};
+
+template <int R1, int R2>
+__host__ inline size_t col2_smem() {
+  return (size_t)(R1 * R2 + 6 * kColTile * Col2<R1, R2>::LS) * sizeof(float2);
+}
+
+// padded offset of (row k1, entry j2) inside a line
+template <int R2>
+__device__ __forceinline__ int c2off(int k1, int j2) { return j2 + (R2 + 1) * k1; }
+
+template <int R1, int R2, int MODE>
+__global__ void __launch_bounds__(Col2<R1, R2>::THREADS, 3)
+    line_pass_2s(GridInfo g, const float2* __restrict__ twg, float2* __restrict__ S, const float* __restrict__ Gt,
+                 const LoadState* st, long long stride, long long ncols, int nload) {
+  using K = Col2<R1, R2>;
+  constexpr int NV = 6, NTRI = 21, N = K::N, LS = K::LS, CT = kColTile;
+  // forward transforms take w = exp(-2 pi i / N); MODE 1 is an inverse
+  constexpr int DIR = MODE == 1 ? 1 : -1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* tw = reinterpret_cast<float2*>(smem_raw);   // tw[t] = exp(-2 pi i t / N)
+  float2* tile = tw + N;                               // [NV * CT][LS]
+  __shared__ long long colbase[CT];
+  const int load = blockIdx.x % nload;
+  const long long q0 = (long long)(blockIdx.x / nload) * CT;
+  if (st[load].done) return;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  if (threadIdx.x < CT) {
+    const long long q = q0 + threadIdx.x;
+    const long long outer = q / stride;
+    colbase[threadIdx.x] = outer * N * stride + (q - outer * stride);
+  }
+  __syncthreads();
+  float2* Sl = S + (size_t)load * NV * g.nhalf;
+  auto gidx = [&](int c, int w, int n) -> size_t { return (size_t)c * g.nhalf + colbase[w] + (long long)n * stride; };
+
+  // stage A (first step in natural order): task a -> column w, entry j2, component c
+  {
+    float2 v[K::A_PER][R1];
+#pragma unroll
+    for (int i = 0; i < K::A_PER; ++i) {
+      const int a = threadIdx.x + K::THREADS * i;
+      const int w = a % CT, j2 = (a / CT) % R2, c = a / (CT * R2);
+      const bool ok = q0 + w < ncols;
+#pragma unroll
+      for (int j1 = 0; j1 < R1; ++j1) v[i][j1] = ok ? Sl[gidx(c, w, j2 + R2 * j1)] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int i = 0; i < K::A_PER; ++i) {
+      const int a = threadIdx.x + K::THREADS * i;
+      const int w = a % CT, j2 = (a / CT) % R2, c = a / (CT * R2);
+      small_dft<R1, DIR, float>(v[i]);
+      float2* line = tile + (c * CT + w) * LS;
+      line[c2off<R2>(0, j2)] = v[i][0];
+#pragma unroll
+      for (int k1 = 1; k1 < R1; ++k1) line[c2off<R2>(k1, j2)] = cmul(v[i][k1], twl<DIR, float>(tw, j2 * k1));
+    }
+  }
+  __syncthreads();
+
+  if constexpr (MODE != 2) {
+    // stage B, results to global memory in natural frequency order
+#pragma unroll
+    for (int i = 0; i < K::B_PER; ++i) {
+      const int b = threadIdx.x + K::THREADS * i;
+      const int w = b % CT, k1 = (b / CT) % R1, c = b / (CT * R1);
+      const float2* line = tile + (c * CT + w) * LS;
+      float2 v[R2];
+#pragma unroll
+      for (int j2 = 0; j2 < R2; ++j2) v[j2] = line[c2off<R2>(k1, j2)];
+      small_dft<R2, DIR, float>(v);
+      if (q0 + w < ncols) {
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) Sl[gidx(c, w, k1 + R1 * k2)] = v[k2];
+      }
+    }
+  } else {
+  // MODE 2: stage B forward in place (row k1 now holds X[k1 + R1 k2] at entry k2)
+#pragma unroll
+  for (int i = 0; i < K::B_PER; ++i) {
+    const int b = threadIdx.x + K::THREADS * i;
+    const int w = b % CT, k1 = (b / CT) % R1, c = b / (CT * R1);
+    float2* line = tile + (c * CT + w) * LS;
+    float2 v[R2];
+#pragma unroll
+    for (int j2 = 0; j2 < R2; ++j2) v[j2] = line[c2off<R2>(k1, j2)];
+    small_dft<R2, -1, float>(v);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) line[c2off<R2>(k1, k2)] = v[k2];
+  }
+  __syncthreads();
+
+  // Green step at frequency (n along this axis, column q): f = n * stride + q
+  for (int idx = threadIdx.x; idx < N * CT; idx += K::THREADS) {
+    const int w = idx % CT, n = idx / CT;
+    const long long q = q0 + w;
+    if (q >= ncols) continue;
+    const long long f = (long long)n * stride + q;
+    const int off = c2off<R2>(n % R1, n / R1);
+    float2 tv[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) tv[c] = tile[(c * CT + w) * LS + off];
+    float gm[NTRI];
+#pragma unroll
+    for (int t = 0; t < NTRI; ++t) gm[t] = Gt[(size_t)t * g.nhalf + f];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      float re = 0.f, im = 0.f;
+#pragma unroll
+      for (int b = 0; b < NV; ++b) {
+        const int lo = a < b ? a : b, hi = a < b ? b : a;
+        const float gv = gm[lo * NV - (lo * (lo - 1)) / 2 + (hi - lo)];
+        re = fmaf(-gv, tv[b].x, re);
+        im = fmaf(-gv, tv[b].y, im);
+      }
+      tile[(a * CT + w) * LS + off] = (f == 0) ? make_float2(0.f, 0.f) : make_float2(re, im);
+    }
+  }
+  __syncthreads();
+
+  // inverse, stage B: row k1, sum over k2, then the twiddles w_N^{+j2 k1}
+#pragma unroll
+  for (int i = 0; i < K::B_PER; ++i) {
+    const int b = threadIdx.x + K::THREADS * i;
+    const int w = b % CT, k1 = (b / CT) % R1, c = b / (CT * R1);
+    float2* line = tile + (c * CT + w) * LS;
+    float2 v[R2];
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) v[k2] = line[c2off<R2>(k1, k2)];
+    small_dft<R2, 1, float>(v);
+    line[c2off<R2>(k1, 0)] = v[0];
+#pragma unroll
+    for (int j2 = 1; j2 < R2; ++j2) line[c2off<R2>(k1, j2)] = cmul(v[j2], twl<1, float>(tw, j2 * k1));
+  }
+  __syncthreads();
+
+  // inverse, stage A: entry j2, sum over k1, points j2 + R2 j1 to global memory
+#pragma unroll
+  for (int i = 0; i < K::A_PER; ++i) {
+    const int a = threadIdx.x + K::THREADS * i;
+    const int w = a % CT, j2 = (a / CT) % R2, c = a / (CT * R2);
+    const float2* line = tile + (c * CT + w) * LS;
+    float2 v[R1];
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) v[k1] = line[c2off<R2>(k1, j2)];
+    small_dft<R1, 1, float>(v);
+    if (q0 + w < ncols) {
+#pragma unroll
+      for (int j1 = 0; j1 < R1; ++j1) Sl[gidx(c, w, j2 + R2 * j1)] = v[j1];
+    }
+  }
+  }
+}
+
+}  // namespace fh

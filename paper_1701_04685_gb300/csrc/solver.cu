@@ -21,6 +21,7 @@
 #include "cluster.cuh"
 #include "warprow.cuh"
 #include "linewarp.cuh"
+#include "colpass2.cuh"
 #include "krylov.cuh"
 #include "planewarp.cuh"
 
@@ -129,6 +130,7 @@ struct fh_solver {
   int row_warp[2] = {0, 0};  // > 0: warp-per-row pass with L = 32 * row_warp
   int plane[2] = {0, 0};     // 3-D FP32: > 0 = the fused plane pass applies (axis-1 P, axis-2 P packed as 10 P1 + P2)
   bool plane_on = false;     // path 3 of the solve in progress: take the fused plane pass where it applies
+  bool col2s = true;         // 3-D FP32 columns of 32, 64 or 128 points: the two-step pass (else the warp-exchange pass)
   int warp_res[2] = {0, 0};  // resident blocks per SM of that pass
   int sms = 0;               // multiprocessors of the device
   int row_bpl[2] = {1, 1};
@@ -337,12 +339,45 @@ void launch_col_pass_mode(fh_solver* s, int a, int mode, int nload) {
   else launch_col_pass<P, 2>(s, a, nload);
 }
 
+// The two-step column pass (colpass2.cuh) applies to the warp-pass axes of 32,
+// 64 or 128 points: returns N there, else 0.
+int col2_len(const fh_solver* s, int prec, int a) {
+  if (!s->col2s || col_warp_p(s, prec, a) == 0) return 0;
+  const int N = s->g.dims[a];
+  return (N == 32 || N == 64 || N == 128) ? N : 0;
+}
+
+template <int R1, int R2, int MODE>
+void launch_col2(fh_solver* s, int a, int nload) {
+  const GridInfo& g = s->g;
+  long long stride = g.H;
+  for (int k = a + 1; k + 1 < g.nd; ++k) stride *= g.dims[k];
+  const long long ncols = g.nhalf / g.dims[a];
+  const long long tiles = (ncols + fh::kColTile - 1) / fh::kColTile;
+  fh::line_pass_2s<R1, R2, MODE><<<(unsigned)(tiles * nload), fh::Col2<R1, R2>::THREADS, fh::col2_smem<R1, R2>(),
+                                   s->work>>>(g, s->ax[a].tw32, reinterpret_cast<float2*>(s->S), s->G32, s->st,
+                                              stride, ncols, nload);
+}
+
+template <int R1, int R2>
+void launch_col2_mode(fh_solver* s, int a, int mode, int nload) {
+  if (mode == 0) launch_col2<R1, R2, 0>(s, a, nload);
+  else if (mode == 1) launch_col2<R1, R2, 1>(s, a, nload);
+  else launch_col2<R1, R2, 2>(s, a, nload);
+}
+
 // line pass along axis a in the given mode (0 forward, 1 inverse, 2 forward +
 // Green + inverse), by the warp-per-column kernel where it applies
 template <typename T>
 void launch_axis(fh_solver* s, int prec, int a, int mode, int nload) {
   const GridInfo& g = s->g;
   if constexpr (sizeof(T) == 4) {
+    switch (col2_len(s, prec, a)) {
+      case 32: launch_col2_mode<4, 8>(s, a, mode, nload); return;
+      case 64: launch_col2_mode<8, 8>(s, a, mode, nload); return;
+      case 128: launch_col2_mode<8, 16>(s, a, mode, nload); return;
+      default: break;
+    }
     switch (col_warp_p(s, prec, a)) {
       case 1: launch_col_pass_mode<1>(s, a, mode, nload); return;
       case 2: launch_col_pass_mode<2>(s, a, mode, nload); return;
@@ -499,6 +534,15 @@ cudaError_t set_col_attrs() {
   return e;
 }
 
+template <int R1, int R2>
+cudaError_t set_col2_attrs() {
+  const int sm = (int)fh::col2_smem<R1, R2>();
+  cudaError_t e = cudaFuncSetAttribute(fh::line_pass_2s<R1, R2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(fh::line_pass_2s<R1, R2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(fh::line_pass_2s<R1, R2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  return e;
+}
+
 template <int P1, int P2>
 cudaError_t set_plane_attrs() {
   const int sm = (int)fh::plane_smem<P1, P2>();
@@ -555,6 +599,12 @@ fh_status set_smem_attrs_nv(fh_solver* s, int prec) {
   size_t lm = 0;
   for (int a = 0; a + 1 < s->g.nd; ++a) {
     if constexpr (sizeof(T) == 4) {
+      switch (col2_len(s, prec, a)) {
+        case 32: CK((set_col2_attrs<4, 8>())); continue;
+        case 64: CK((set_col2_attrs<8, 8>())); continue;
+        case 128: CK((set_col2_attrs<8, 16>())); continue;
+        default: break;
+      }
       switch (col_warp_p(s, prec, a)) {
         case 1: CK((set_col_attrs<1>())); continue;
         case 2: CK((set_col_attrs<2>())); continue;
@@ -1764,7 +1814,9 @@ int status_rank(fh_status st) {
 // Returns false where the variant does not apply (or changes nothing).
 //   0 the defaults
 //   4 the block row pass with twice the rows per block
-//   5 the block line passes with twice the tile width (columns per block)
+//   5 the block line passes with twice the tile width (columns per block);
+//     the 3-D FP32 columns of 32-128 points by the warp-exchange pass in
+//     place of the two-step pass
 //   6 every axis's radix schedule in reverse order
 //   7 radix-4 stages in place of radix-8 and radix-2 pairs
 bool apply_variant(fh_solver* s, int prec, int var) {
@@ -1779,6 +1831,7 @@ bool apply_variant(fh_solver* s, int prec, int var) {
     s->line_smem[prec][a] = d.line_smem[a];
     s->ax[a].planp[prec] = d.plans[a];
   }
+  s->col2s = true;
   if (var == 0) return true;
   if (var == 4) {
     if (s->row_warp[prec] > 0 && !s->field) return false;   // the warp row pass runs instead
@@ -1795,6 +1848,10 @@ bool apply_variant(fh_solver* s, int prec, int var) {
   if (var == 5) {
     bool any = false;
     for (int a = 0; a + 1 < g.nd; ++a) {
+      if (col2_len(s, prec, a) > 0) {
+        s->col2s = false;
+        any = true;
+      }
       if (col_warp_p(s, prec, a) > 0) continue;
       const int W = 2 * d.lineW[a];
       const size_t sm = (size_t)2 * g.nv * W * (g.dims[a] + 1) * csize(prec);

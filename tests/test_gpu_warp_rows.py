@@ -56,6 +56,9 @@ WARP_CASES = [
      [(1.0, 0.3), (40.0, 0.3)], _ball(0.25), [8, 32, 128]),
     ("cols64", [[32, 0, 0], [0, 64, 0], [0, 0, 64]], {"kind": "dirichlet"},
      [(1.0, 0.3), (50.0, 0.3)], _ball(0.15), [32, 64, 64]),
+    # every column pass of 64 points, the Green step's included
+    ("cols64_cube", [[64, 0, 0], [0, 64, 0], [0, 0, 64]], {"kind": "dlvp", "alpha": [0.2, 0.25, 0.3]},
+     [(1.0, 0.3), (20.0, 0.25)], _ball(0.27), [64, 64, 64]),
 ]
 IDS = [c[0] for c in WARP_CASES]
 
@@ -129,6 +132,41 @@ def test_fp32_warp_rows_subset_of_loads(fh):
         Eg = s.get_strain(L)
         Eo = ref["E"][L][case.perm].T
         assert np.abs(Eg - Eo).max() / np.abs(Eo + eps0[L][:, None]).max() < TOL32
+
+
+def test_fp32_columns_of_128_track_oracle(fh):
+    """M = diag(128,128,128), Dirichlet kernel, two loads: every column pass
+    and the Green step on columns of 128 points, element by element after 5
+    FP32 iterations."""
+    case = Case([[128, 0, 0], [0, 128, 0], [0, 0, 128]], {"kind": "dirichlet"}, [(1.0, 0.3), (30.0, 0.3)],
+                *_ball(0.3), nload=2)
+    case.eps0 = np.stack([np.eye(6)[1], np.eye(6)[4]])
+    s = case.product(fh)
+    n = 5
+    out = s.solve(case.eps0, tol=0.0, max_iter=n, precision=FP32)
+    ref = case.oracle_solve(tol=0.0, max_iter=n)
+    assert list(out["iterations"]) == [n, n]
+    assert case.strain_error(s, ref["E"]) < 2e-5
+    assert rel(out["mean_stress"], ref["mean_stress"]) < 2e-5
+    for L in range(2):
+        assert rel(s.get_residuals(L)[:n], np.asarray(ref["resid"][L][:n])) < 1e-4
+    s.close()
+
+
+def test_two_step_and_warp_exchange_column_passes_agree(fh):
+    """The column passes of 64 points in the two-step form (the default) and in
+    the warp-exchange form (autotuner candidate 5, tune = 7) give the same
+    iterates to FP32 rounding."""
+    case = _case(WARP_CASES[-1])
+    s = case.product(fh)
+    n = 20
+    s.solve(case.eps0, tol=0.0, max_iter=n, precision=FP32, tune=2)
+    Ea = [s.get_strain(L).copy() for L in range(case.nload)]
+    s.solve(case.eps0, tol=0.0, max_iter=n, precision=FP32, tune=7)
+    for L in range(case.nload):
+        Eb = s.get_strain(L)
+        assert np.abs(Ea[L] - Eb).max() / np.abs(Eb + case.eps0[L][:, None]).max() < 3e-6
+    s.close()
 
 
 def test_full_size_box3d_fp32_iteration_sampled(fh):
