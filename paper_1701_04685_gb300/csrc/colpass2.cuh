@@ -2,7 +2,7 @@
 // N = R1 R2 points (32 = 4 x 8, 64 = 8 x 8, 128 = 8 x 16).
 //
 // Same job as line_pass_warp6 (forward, inverse, or forward + Green step +
-// inverse along one strided axis of the half spectra, kColTile adjacent
+// inverse along one strided axis of the half spectra, CT = 8 or 4 adjacent
 // columns of one load and all six components per block), with the length-N
 // DFT of each column split as N = R1 R2 (the four-step factorisation):
 // with j = j2 + R2 j1 and k = k1 + R1 k2,
@@ -22,45 +22,71 @@
 // inverse with the twiddles after it, then stage A inverse, writing the
 // points in natural order).  Inverse transforms are unnormalised.
 //
-// Shared memory: line (component c, column w) = c kColTile + w holds the
-// R1 rows of R2 values at padded offsets j2 + (R2 + 1) k1, LS entries per line
-// with LS = 4 mod 16 (in float2): the stage A stores (8 columns x 4 values of
-// j2 per warp), the stage B loads (8 columns x 4 rows) and the Green step's
-// loads each touch every bank pair exactly twice per warp.
+// Shared memory: line (component c, column w) = c CT + w holds the R1 rows
+// of R2 values at padded offsets j2 + (R2 + 1) k1, LS entries per line with
+// LS = 16 / CT mod 16 (in float2).  Eight-byte accesses are served per
+// half-warp (CT columns x 16 / CT values of j2, or x 16 / CT rows k1): the
+// columns land 32 / CT banks apart and the values or rows 2 banks apart, so
+// the stage A stores, the stage B loads and the Green step's accesses are
+// free of bank conflicts.
 #pragma once
 
 #include "linewarp.cuh"
 
 namespace fh {
 
-template <int R1, int R2>
+template <int R1, int R2, int CT = kColTile>
 struct Col2 {
   static constexpr int N = R1 * R2;
   static constexpr int RMIN = R1 < R2 ? R1 : R2;
-  static constexpr int LINES = 6 * kColTile;                 // 48 lines per block
+  static constexpr int LINES = 6 * CT;                       // lines per block (48 for 8 columns)
   static constexpr int THREADS = LINES * RMIN;
   static constexpr int A_PER = LINES * R2 / THREADS;         // stage A tasks per thread
   static constexpr int B_PER = LINES * R1 / THREADS;         // stage B tasks per thread
-  static constexpr int LS = ((N + R1 + 11) / 16) * 16 + 4;   // >= N + R1, = 4 mod 16
+  static constexpr int OFF = 16 / CT;                        // line stride mod 16
+  static constexpr int LS = ((N + R1 - OFF + 15) / 16) * 16 + OFF;
+  static_assert(CT == 4 || CT == 8, "4 or 8 columns per block");
   static_assert(A_PER * THREADS == LINES * R2 && B_PER * THREADS == LINES * R1, "uneven task split");
-  static_assert(LS >= N + R1 && LS % 16 == 4, "line stride");
+  static_assert(LS >= N + R1 && LS % 16 == OFF, "line stride");
 };
 
-template <int R1, int R2>
+template <int R1, int R2, int CT = kColTile>
 __host__ inline size_t col2_smem() {
-  return (size_t)(R1 * R2 + 6 * kColTile * Col2<R1, R2>::LS) * sizeof(float2);
+  return (size_t)(R1 * R2 + 6 * CT * Col2<R1, R2, CT>::LS) * sizeof(float2);
 }
 
 // padded offset of (row k1, entry j2) inside a line
 template <int R2>
 __device__ __forceinline__ int c2off(int k1, int j2) { return j2 + (R2 + 1) * k1; }
 
-template <int R1, int R2, int MODE>
-__global__ void __launch_bounds__(Col2<R1, R2>::THREADS, 3)
+// w[t] = w_N^{DIR base t} for t < R (R = 4, 8 or 16): the powers t = 1, 2, 4, 8
+// come from the table tw[t] = exp(-2 pi i t / N), every other one is the
+// product of two earlier ones (at most three roundings deep)
+template <int R, int DIR>
+__device__ __forceinline__ void twiddle_powers(const float2* tw, int base, float2* w) {
+  w[0] = make_float2(1.f, 0.f);
+#pragma unroll
+  for (int p = 1; p < R; p <<= 1) w[p] = twl<DIR, float>(tw, base * p);
+#pragma unroll
+  for (int t = 3; t < R; ++t) {
+    if ((t & (t - 1)) == 0) continue;
+    const int hi = t >= 8 ? 8 : (t >= 4 ? 4 : 2);
+    w[t] = cmul(w[hi], w[t - hi]);
+  }
+}
+
+// resident blocks per SM the register budget is set for: three for the
+// single transforms, two for MODE 2 (whose Green step wants more registers;
+// measured faster at two)
+template <int MODE>
+constexpr int col2_minb() { return MODE == 2 ? 2 : 3; }
+
+template <int R1, int R2, int MODE, int CT = kColTile, int MINB = col2_minb<MODE>()>
+__global__ void __launch_bounds__(Col2<R1, R2, CT>::THREADS, MINB)
     line_pass_2s(GridInfo g, const float2* __restrict__ twg, float2* __restrict__ S, const float* __restrict__ Gt,
                  const LoadState* st, long long stride, long long ncols, int nload) {
-  using K = Col2<R1, R2>;
-  constexpr int NV = 6, NTRI = 21, N = K::N, LS = K::LS, CT = kColTile;
+  using K = Col2<R1, R2, CT>;
+  constexpr int NV = 6, NTRI = 21, N = K::N, LS = K::LS;
   // forward transforms take w = exp(-2 pi i / N); MODE 1 is an inverse
   constexpr int DIR = MODE == 1 ? 1 : -1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -96,10 +122,12 @@ __global__ void __launch_bounds__(Col2<R1, R2>::THREADS, 3)
       const int a = threadIdx.x + K::THREADS * i;
       const int w = a % CT, j2 = (a / CT) % R2, c = a / (CT * R2);
       small_dft<R1, DIR, float>(v[i]);
+      float2 twv[R1];
+      twiddle_powers<R1, DIR>(tw, j2, twv);
       float2* line = tile + (c * CT + w) * LS;
       line[c2off<R2>(0, j2)] = v[i][0];
 #pragma unroll
-      for (int k1 = 1; k1 < R1; ++k1) line[c2off<R2>(k1, j2)] = cmul(v[i][k1], twl<DIR, float>(tw, j2 * k1));
+      for (int k1 = 1; k1 < R1; ++k1) line[c2off<R2>(k1, j2)] = cmul(v[i][k1], twv[k1]);
     }
   }
   __syncthreads();
@@ -174,9 +202,11 @@ __global__ void __launch_bounds__(Col2<R1, R2>::THREADS, 3)
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) v[k2] = line[c2off<R2>(k1, k2)];
     small_dft<R2, 1, float>(v);
+    float2 twv[R2];
+    twiddle_powers<R2, 1>(tw, k1, twv);
     line[c2off<R2>(k1, 0)] = v[0];
 #pragma unroll
-    for (int j2 = 1; j2 < R2; ++j2) line[c2off<R2>(k1, j2)] = cmul(v[j2], twl<1, float>(tw, j2 * k1));
+    for (int j2 = 1; j2 < R2; ++j2) line[c2off<R2>(k1, j2)] = cmul(v[j2], twv[j2]);
   }
   __syncthreads();
 
@@ -199,3 +229,4 @@ __global__ void __launch_bounds__(Col2<R1, R2>::THREADS, 3)
 }
 
 }  // namespace fh
+
