@@ -412,6 +412,23 @@ fh_status fh_fno_make_input(const fh_fno* f, const uint8_t* phase, int nphase, c
 const char* fh_status_string(fh_status st);
 const char* fh_last_error(void);
 
+/* ---- checked build --------------------------------------------------------
+ * The library compiled with -DFH_CHECKED (build(checked=True) of the Python
+ * package, libffthomog_checked.so) tests the global-memory and tile indices
+ * of its solver kernels against the extents of the arrays they address.  A
+ * violating access is skipped and recorded; fh_solve, fh_solve_batch,
+ * fh_set_reference and fh_profile_passes then return FH_ERR_INTERNAL and
+ * fh_last_error() names the kernel and array, the index and the extent.  The
+ * checks stand in for a memory checker; they cost time and are off in the
+ * normal build. */
+/* 1 in the checked build, else 0. */
+int fh_checked_build(void);
+/* Checked build: launches a one-thread kernel that tests one index inside and
+ * one outside a declared extent (inside its buffer either way) and returns
+ * FH_ERR_INTERNAL naming the self test when the check caught the second.
+ * Normal build: FH_ERR_UNSUPPORTED, nothing launched. */
+fh_status fh_check_selftest(void);
+
 #ifdef __cplusplus
 }
 #endif

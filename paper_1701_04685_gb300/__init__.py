@@ -18,9 +18,10 @@ import os
 
 import numpy as np
 
-from .build import LIB
+from .build import LIB, LIB_CHECKED
 
 FH_OK, FH_NOT_CONVERGED, FH_DIVERGED, FH_NONFINITE = 0, 1, 2, 3
+FH_ERR_ARG, FH_ERR_INTERNAL, FH_ERR_UNSUPPORTED = -1, -7, -8
 FH_GEN_DIRICHLET, FH_GEN_DLVP, FH_GEN_BOXSPLINE = 0, 1, 2
 FH_PREC_FP64, FH_PREC_FP32, FH_PREC_MIXED = 0, 1, 2
 FH_MAX_LOADS = 16
@@ -60,12 +61,16 @@ _lib = None
 
 
 def library():
-    """The loaded CUDA library; raises if it has not been built."""
+    """The loaded CUDA library; raises if it has not been built.  With the
+    environment variable FH_CHECKED=1 at the first call, the checked build
+    (``build(checked=True)``: index checks in the solver kernels) is loaded
+    instead of the normal one."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB):
-            raise RuntimeError(f"CUDA library {LIB} is missing: run paper_1701_04685_gb300.build.build()")
-        lib = C.CDLL(LIB)
+        path = LIB_CHECKED if os.environ.get("FH_CHECKED") == "1" else LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing: run paper_1701_04685_gb300.build.build()")
+        lib = C.CDLL(path)
         P, I, D, V = C.c_void_p, C.c_int, C.c_double, None
         sig = {
             "fh_pattern_create": (I, [I, P, C.POINTER(P)]),
@@ -90,6 +95,8 @@ def library():
             "fh_get_tuning": (I, [P, I, P, P, P, P]),
             "fh_status_string": (C.c_char_p, [I]),
             "fh_last_error": (C.c_char_p, []),
+            "fh_checked_build": (I, []),
+            "fh_check_selftest": (I, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -106,7 +113,20 @@ def exported_symbols():
             "fh_set_stiffness_phases", "fh_set_stiffness_field", "fh_set_reference", "fh_solve", "fh_get_strain", "fh_set_strain",
             "fh_get_ceff", "fh_get_green", "fh_get_residuals", "fh_profile_passes", "fh_status_string",
             "fh_last_error", "fh_mean_stress_noalloc", "fh_solve_batch",
-            "fh_get_tuning"]
+            "fh_get_tuning", "fh_checked_build", "fh_check_selftest"]
+
+
+def checked_build():
+    """True when the loaded library is the checked build (FH_CHECKED=1)."""
+    return bool(library().fh_checked_build())
+
+
+def check_selftest():
+    """Checked build: the status of the index checks' self test (FH_ERR_INTERNAL
+    with the self test named when the checks work); normal build:
+    FH_ERR_UNSUPPORTED.  Returns (status, message)."""
+    rc = library().fh_check_selftest()
+    return rc, library().fh_last_error().decode()
 
 
 def _check(rc, ok=(FH_OK,)):

@@ -138,7 +138,9 @@ __device__ __forceinline__ void cluster_solve_body(const GridInfo& g, const DevP
   for (int i = threadIdx.x; i < nrow * L; i += blockDim.x) {
     const int r = fdiv(i, fL), x = i - r * L;
     const int gi = (r0 + r) * L + x;
+    if (!FH_IN(CK_CLUSTER, gi, m)) continue;
     phl[i] = phase[gi];
+    if (!FH_IN(CK_CLUSTER, phl[i], nphase)) phl[i] = 0;
 #pragma unroll
     for (int c = 0; c < NV; ++c) El[(r * NV + c) * L + x] = Eg[Ebase + (size_t)c * m + gi];
   }
@@ -147,6 +149,7 @@ __device__ __forceinline__ void cluster_solve_body(const GridInfo& g, const DevP
     const int j = i - t2 * ncol;
     const int t = fdiv(t2, fN0);
     const int n = t2 - t * N0;
+    if (!FH_IN(CK_CLUSTER, (long long)t * g.nhalf + (long long)n * H + c0 + j, (long long)NTRI * g.nhalf)) continue;
     Gl[i] = Gt[(size_t)t * g.nhalf + (size_t)n * H + c0 + j];
   }
   T e0[NV];
@@ -378,6 +381,7 @@ __device__ __forceinline__ void cluster_solve_body(const GridInfo& g, const DevP
   // ---- results
   for (int i = threadIdx.x; i < nrow * L; i += blockDim.x) {
     const int r = fdiv(i, fL), x = i - r * L;
+    if (!FH_IN(CK_CLUSTER, (r0 + r) * L + x, m)) continue;
 #pragma unroll
     for (int c = 0; c < NV; ++c) Eg[Ebase + (size_t)c * m + (r0 + r) * L + x] = El[(r * NV + c) * L + x];
   }

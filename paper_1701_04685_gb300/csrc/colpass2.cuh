@@ -105,6 +105,10 @@ __global__ void __launch_bounds__(Col2<R1, R2, CT>::THREADS, MINB)
   __syncthreads();
   float2* Sl = S + (size_t)load * NV * g.nhalf;
   auto gidx = [&](int c, int w, int n) -> size_t { return (size_t)c * g.nhalf + colbase[w] + (long long)n * stride; };
+  // extents for the checked build: the launch's loads, the tile
+  const long long sl0 = (long long)load * NV * g.nhalf, nS = (long long)nload * NV * g.nhalf;
+  constexpr long long nT = (long long)NV * CT * LS;
+  (void)sl0; (void)nS; (void)nT;
 
   // stage A (first step in natural order): task a -> column w, entry j2, component c
   {
@@ -115,7 +119,9 @@ __global__ void __launch_bounds__(Col2<R1, R2, CT>::THREADS, MINB)
       const int w = a % CT, j2 = (a / CT) % R2, c = a / (CT * R2);
       const bool ok = q0 + w < ncols;
 #pragma unroll
-      for (int j1 = 0; j1 < R1; ++j1) v[i][j1] = ok ? Sl[gidx(c, w, j2 + R2 * j1)] : make_float2(0.f, 0.f);
+      for (int j1 = 0; j1 < R1; ++j1)
+        v[i][j1] = ok && FH_IN(CK_C2_S, sl0 + (long long)gidx(c, w, j2 + R2 * j1), nS) ? Sl[gidx(c, w, j2 + R2 * j1)]
+                                                                                    : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int i = 0; i < K::A_PER; ++i) {
@@ -124,6 +130,7 @@ __global__ void __launch_bounds__(Col2<R1, R2, CT>::THREADS, MINB)
       small_dft<R1, DIR, float>(v[i]);
       float2 twv[R1];
       twiddle_powers<R1, DIR>(tw, j2, twv);
+      if (!FH_IN(CK_C2_TILE, (c * CT + w) * LS + c2off<R2>(R1 - 1, j2), nT)) continue;
       float2* line = tile + (c * CT + w) * LS;
       line[c2off<R2>(0, j2)] = v[i][0];
 #pragma unroll
@@ -138,6 +145,7 @@ __global__ void __launch_bounds__(Col2<R1, R2, CT>::THREADS, MINB)
     for (int i = 0; i < K::B_PER; ++i) {
       const int b = threadIdx.x + K::THREADS * i;
       const int w = b % CT, k1 = (b / CT) % R1, c = b / (CT * R1);
+      if (!FH_IN(CK_C2_TILE, (c * CT + w) * LS + c2off<R2>(k1, R2 - 1), nT)) continue;
       const float2* line = tile + (c * CT + w) * LS;
       float2 v[R2];
 #pragma unroll
@@ -145,7 +153,8 @@ __global__ void __launch_bounds__(Col2<R1, R2, CT>::THREADS, MINB)
       small_dft<R2, DIR, float>(v);
       if (q0 + w < ncols) {
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) Sl[gidx(c, w, k1 + R1 * k2)] = v[k2];
+        for (int k2 = 0; k2 < R2; ++k2)
+          if (FH_IN(CK_C2_S, sl0 + (long long)gidx(c, w, k1 + R1 * k2), nS)) Sl[gidx(c, w, k1 + R1 * k2)] = v[k2];
       }
     }
   } else {
@@ -154,6 +163,7 @@ __global__ void __launch_bounds__(Col2<R1, R2, CT>::THREADS, MINB)
   for (int i = 0; i < K::B_PER; ++i) {
     const int b = threadIdx.x + K::THREADS * i;
     const int w = b % CT, k1 = (b / CT) % R1, c = b / (CT * R1);
+    if (!FH_IN(CK_C2_TILE, (c * CT + w) * LS + c2off<R2>(k1, R2 - 1), nT)) continue;
     float2* line = tile + (c * CT + w) * LS;
     float2 v[R2];
 #pragma unroll
@@ -171,6 +181,7 @@ __global__ void __launch_bounds__(Col2<R1, R2, CT>::THREADS, MINB)
     if (q >= ncols) continue;
     const long long f = (long long)n * stride + q;
     const int off = c2off<R2>(n % R1, n / R1);
+    if (!FH_IN(CK_C2_G, f, g.nhalf) || !FH_IN(CK_C2_TILE, ((NV - 1) * CT + w) * LS + off, nT)) continue;
     float2 tv[NV];
 #pragma unroll
     for (int c = 0; c < NV; ++c) tv[c] = tile[(c * CT + w) * LS + off];
@@ -197,6 +208,7 @@ __global__ void __launch_bounds__(Col2<R1, R2, CT>::THREADS, MINB)
   for (int i = 0; i < K::B_PER; ++i) {
     const int b = threadIdx.x + K::THREADS * i;
     const int w = b % CT, k1 = (b / CT) % R1, c = b / (CT * R1);
+    if (!FH_IN(CK_C2_TILE, (c * CT + w) * LS + c2off<R2>(k1, R2 - 1), nT)) continue;
     float2* line = tile + (c * CT + w) * LS;
     float2 v[R2];
 #pragma unroll
@@ -215,6 +227,7 @@ __global__ void __launch_bounds__(Col2<R1, R2, CT>::THREADS, MINB)
   for (int i = 0; i < K::A_PER; ++i) {
     const int a = threadIdx.x + K::THREADS * i;
     const int w = a % CT, j2 = (a / CT) % R2, c = a / (CT * R2);
+    if (!FH_IN(CK_C2_TILE, (c * CT + w) * LS + c2off<R2>(R1 - 1, j2), nT)) continue;
     const float2* line = tile + (c * CT + w) * LS;
     float2 v[R1];
 #pragma unroll
@@ -222,7 +235,8 @@ __global__ void __launch_bounds__(Col2<R1, R2, CT>::THREADS, MINB)
     small_dft<R1, 1, float>(v);
     if (q0 + w < ncols) {
 #pragma unroll
-      for (int j1 = 0; j1 < R1; ++j1) Sl[gidx(c, w, j2 + R2 * j1)] = v[j1];
+      for (int j1 = 0; j1 < R1; ++j1)
+        if (FH_IN(CK_C2_S, sl0 + (long long)gidx(c, w, j2 + R2 * j1), nS)) Sl[gidx(c, w, j2 + R2 * j1)] = v[j1];
     }
   }
   }

@@ -26,6 +26,48 @@ namespace fh {
 
 constexpr int MAXV = 6;  // n_v <= 6
 
+// ---------------------------------------------------------------------------
+// Checked build (compiled with -DFH_CHECKED): the global-memory and tile
+// accesses of the solver's kernels test their index against the extent of
+// the array they address (for the fields: the loads of the launch).  The
+// first violation is recorded (site, index, extent, and a count of all of
+// them) and the access is skipped, so that a wrong index becomes an error
+// status instead of a fault; the host reads the record after each solve.
+// Without FH_CHECKED the tests compile away.
+// ---------------------------------------------------------------------------
+enum CheckSite {
+  CK_ROW_S = 1, CK_ROW_E, CK_ROW_PHASE, CK_ROW_SMEM, CK_FIELD, CK_PARTIALS,
+  CK_LINE_S, CK_LINE_G, CK_LINE_SMEM,
+  CK_WROW_S, CK_WROW_E, CK_WROW_PHASE, CK_WROW_SCRATCH,
+  CK_COL_S, CK_COL_G, CK_COL_TILE,
+  CK_C2_S, CK_C2_G, CK_C2_TILE,
+  CK_GREEN1D, CK_MEAN, CK_KRY, CK_CLUSTER, CK_TABLE, CK_SELFTEST,
+  CK_NSITES
+};
+
+struct CheckRecord {
+  unsigned long long count;
+  long long index, extent;
+  int site, pad;
+};
+
+#ifdef FH_CHECKED
+static __device__ CheckRecord g_check;
+__device__ __noinline__ bool check_fail(int site, long long i, long long n) {
+  if (atomicAdd(&g_check.count, 1ull) == 0ull) {
+    g_check.site = site;
+    g_check.index = i;
+    g_check.extent = n;
+  }
+  return false;
+}
+#define FH_IN(site, i, n) \
+  (((unsigned long long)(long long)(i) < (unsigned long long)(long long)(n)) || \
+   ::fh::check_fail((site), (long long)(i), (long long)(n)))
+#else
+#define FH_IN(site, i, n) true
+#endif
+
 struct GridInfo {
   int d, nv, ntri, nd;
   int dims[3];
@@ -304,6 +346,13 @@ __global__ void __launch_bounds__(256, PassOcc<T>::value) row_pass(GridInfo g, D
     const cplx<T>* Sr = S + ((size_t)load * NV * g.nrows + row0) * H;  // row0 of component 0
     cplx<T>* Sw = S + ((size_t)load * NV * g.nrows + row0) * H;
     const size_t cstrE = (size_t)g.m, cstrS = (size_t)g.nrows * H;
+    // extents for the checked build: offsets of Sr / Eb inside S / E, the
+    // fields of the launch's loads, one work buffer
+    const long long sbase = ((long long)load * NV * g.nrows + row0) * H;
+    const long long ebase = (long long)load * NV * g.m + row0 * L;
+    const long long nS = (long long)ctl->nload * NV * g.nhalf, nE = (long long)ctl->nload * NV * g.m;
+    const long long nW = (long long)((rpb * NV + 1) >> 1) * Lp;
+    (void)sbase; (void)ebase; (void)nS; (void)nE; (void)nW;
     cplx<T>* Z = W0;
     cplx<T>* Zo = W1;
     if (!FIRST) {
@@ -323,10 +372,12 @@ __global__ void __launch_bounds__(256, PassOcc<T>::value) row_pass(GridInfo g, D
             const int fa = 2 * p, fb = 2 * p + 1;
             const int kk = k <= (L >> 1) ? k : L - k;
             const int ra = fa / NV, ca = fa - ra * NV;
-            A[u] = Sr[ca * cstrS + ra * H + kk];
+            const long long oa = (long long)ca * cstrS + ra * H + kk;
+            if (FH_IN(CK_ROW_S, sbase + oa, nS)) A[u] = Sr[oa];
             if (fb < nreal) {
               const int rbb = fb / NV, cb = fb - rbb * NV;
-              B[u] = Sr[cb * cstrS + rbb * H + kk];
+              const long long ob = (long long)cb * cstrS + rbb * H + kk;
+              if (FH_IN(CK_ROW_S, sbase + ob, nS)) B[u] = Sr[ob];
             }
           }
         }
@@ -339,7 +390,7 @@ __global__ void __launch_bounds__(256, PassOcc<T>::value) row_pass(GridInfo g, D
             cplx<T> z;
             z.x = A[u].x - B[u].y;
             z.y = A[u].y + B[u].x;
-            W0[p * Lp + padi<PS>(k)] = z;
+            if (FH_IN(CK_ROW_SMEM, p * Lp + padi<PS>(k), nW)) W0[p * Lp + padi<PS>(k)] = z;
           }
         }
       }
@@ -356,11 +407,13 @@ __global__ void __launch_bounds__(256, PassOcc<T>::value) row_pass(GridInfo g, D
       const size_t ob = (size_t)load * NV * g.m + row0 * L;
       for (int idx = threadIdx.x; idx < nrow * L; idx += blockDim.x) {
         const int r = fdiv(idx, fL), x = idx - r * L;
+        if (!FH_IN(CK_ROW_SMEM, ((r * NV + NV - 1) >> 1) * Lp + padi<PS>(x), nW)) continue;
 #pragma unroll
         for (int c = 0; c < NV; ++c) {
           const int f = r * NV + c;
           const cplx<T> zz = Z[(f >> 1) * Lp + padi<PS>(x)];
           const size_t o = ob + (size_t)c * cstrE + r * L + x;
+          if (!FH_IN(CK_ROW_E, (long long)o, nE)) continue;
           const T w = E[o] - ((f & 1) ? zz.y : zz.x) * scale;
           Wout[o] = w;
           acc_d.add_prod(w, Yaux ? Yaux[o] : E[o]);
@@ -370,6 +423,10 @@ __global__ void __launch_bounds__(256, PassOcc<T>::value) row_pass(GridInfo g, D
     }
     for (int idx = threadIdx.x; idx < (KINV ? 0 : nrow * L); idx += blockDim.x) {
       const int r = fdiv(idx, fL), x = idx - r * L;
+      if (!(FH_IN(CK_ROW_E, ebase + r * L + x, nE) && FH_IN(CK_ROW_E, ebase + r * L + x + (NV - 1) * (long long)cstrE, nE) &&
+            FH_IN(CK_ROW_SMEM, ((r * NV + NV - 1) >> 1) * Lp + padi<PS>(x), nW) &&
+            FH_IN(Cfld ? CK_FIELD : CK_ROW_PHASE, (row0 + r) * L + x, g.m)))
+        continue;
       T* ep = Eb + r * L + x;
       T en[NV];
 #pragma unroll
@@ -429,6 +486,8 @@ __global__ void __launch_bounds__(256, PassOcc<T>::value) row_pass(GridInfo g, D
     // 5. split into the two half spectra A = (Z_k + conj Z_{L-k})/2, B = (Z_k - conj Z_{L-k})/(2i)
     for (int idx = threadIdx.x; idx < npair * H; idx += blockDim.x) {
       const int p = fdiv(idx, fH), k = idx - p * H;
+      if (!FH_IN(CK_ROW_SMEM, p * Lp + padi<PS>(k == 0 ? 0 : L - k), nW) || !FH_IN(CK_ROW_SMEM, p * Lp + padi<PS>(k), nW))
+        continue;
       const cplx<T> zk = Zf[p * Lp + padi<PS>(k)];
       const cplx<T> zm = Zf[p * Lp + padi<PS>(k == 0 ? 0 : L - k)];
       cplx<T> A, B;
@@ -438,10 +497,12 @@ __global__ void __launch_bounds__(256, PassOcc<T>::value) row_pass(GridInfo g, D
       B.y = T(-0.5) * (zk.x - zm.x);
       const int fa = 2 * p, fb = 2 * p + 1;
       const int ra = fa / NV, ca = fa - ra * NV;
-      Sw[ca * cstrS + ra * H + k] = A;
+      const long long oa = (long long)ca * cstrS + ra * H + k;
+      if (FH_IN(CK_ROW_S, sbase + oa, nS)) Sw[oa] = A;
       if (fb < nreal) {
         const int rbb = fb / NV, cb = fb - rbb * NV;
-        Sw[cb * cstrS + rbb * H + k] = B;
+        const long long ob = (long long)cb * cstrS + rbb * H + k;
+        if (FH_IN(CK_ROW_S, sbase + ob, nS)) Sw[ob] = B;
       }
     }
     }
@@ -523,6 +584,11 @@ __global__ void __launch_bounds__(256, PassOcc<T>::value) line_pass(GridInfo g, 
   cplx<T>* Sb = S + (size_t)load * NV * comp_stride + base + w0;
   const FDiv fW = make_fdiv(W), fN = make_fdiv(N);
   const int wlim = min(W, H - w0);
+  // extents for the checked build: the launch's loads, one line buffer
+  const long long sb0 = (long long)load * NV * comp_stride + base + w0;
+  const long long nS = (long long)(gridDim.x / ((unsigned)ntiles * n_inner * n_outer)) * NV * g.nhalf;
+  const long long nX = (long long)nl * ls;
+  (void)sb0; (void)nS; (void)nX;
 
   {
     constexpr int U = 4;   // loads in flight per thread
@@ -538,7 +604,8 @@ __global__ void __launch_bounds__(256, PassOcc<T>::value) line_pass(GridInfo g, 
           const int w = idx - t * W;
           const int c = fdiv(t, fN);
           const int n = t - c * N;
-          if (w < wlim) v[u] = Sb[c * comp_stride + n * stride + w];
+          if (w < wlim && FH_IN(CK_LINE_S, sb0 + c * comp_stride + n * stride + w, nS))
+            v[u] = Sb[c * comp_stride + n * stride + w];
         }
       }
 #pragma unroll
@@ -549,7 +616,7 @@ __global__ void __launch_bounds__(256, PassOcc<T>::value) line_pass(GridInfo g, 
           const int w = idx - t * W;
           const int c = fdiv(t, fN);
           const int n = t - c * N;
-          X0[(c * W + w) * ls + n] = v[u];
+          if (FH_IN(CK_LINE_SMEM, (c * W + w) * ls + n, nX)) X0[(c * W + w) * ls + n] = v[u];
         }
       }
     }
@@ -564,6 +631,9 @@ __global__ void __launch_bounds__(256, PassOcc<T>::value) line_pass(GridInfo g, 
       const int w = idx - n * W;
       if (w >= wlim) continue;
       const long long f = (long long)n * stride + (long long)inner * H + w0 + w;
+      if (!FH_IN(CK_LINE_G, f + (long long)(NTRI - 1) * g.nhalf, (long long)NTRI * g.nhalf) ||
+          !FH_IN(CK_LINE_SMEM, ((NV - 1) * W + w) * ls + n, nX))
+        continue;
       cplx<T> tv[NV];
 #pragma unroll
       for (int c = 0; c < NV; ++c) tv[c] = X[(c * W + w) * ls + n];
@@ -594,7 +664,9 @@ __global__ void __launch_bounds__(256, PassOcc<T>::value) line_pass(GridInfo g, 
     const int w = idx - t * W;
     const int c = fdiv(t, fN);
     const int n = t - c * N;
-    if (w < wlim) Sb[c * comp_stride + n * stride + w] = X[(c * W + w) * ls + n];
+    if (w < wlim && FH_IN(CK_LINE_S, sb0 + c * comp_stride + n * stride + w, nS) &&
+        FH_IN(CK_LINE_SMEM, (c * W + w) * ls + n, nX))
+      Sb[c * comp_stride + n * stride + w] = X[(c * W + w) * ls + n];
   }
 }
 
@@ -609,6 +681,7 @@ __global__ void green_1d(GridInfo g, cplx<T>* __restrict__ S, const T* __restric
     if (st[load].done) continue;
     const int nv = g.nv;
     const size_t base = (size_t)load * nv * g.nhalf + f;
+    if (!FH_IN(CK_GREEN1D, (long long)base + (long long)(nv - 1) * g.nhalf, (long long)nload * nv * g.nhalf)) continue;
     cplx<T> tv[MAXV];
     for (int c = 0; c < nv; ++c) tv[c] = S[base + c * g.nhalf];
     int t = 0;
@@ -645,6 +718,8 @@ __global__ void __launch_bounds__(256) mean_stress(GridInfo g, const T* __restri
   const size_t Ebase = (size_t)load * nv * g.m;
   for (long long i = (long long)q * blockDim.x + threadIdx.x; i < g.m; i += (long long)blocks_per_load * blockDim.x) {
     double e[MAXV];
+    if (!FH_IN(CK_MEAN, (long long)Ebase + (long long)(nv - 1) * g.m + i, (long long)ctl->nload * nv * g.m)) continue;
+    if (!Cfld && !FH_IN(CK_MEAN, phase[i], 16)) continue;
     for (int c = 0; c < nv; ++c) e[c] = (double)E[Ebase + (size_t)c * g.m + i] + e0[c];
     if (Cfld) {   // point-by-point stiffness, upper triangle [tri][m]
       int t = 0;
@@ -894,6 +969,7 @@ __global__ void green_table(GreenParams P, double* __restrict__ G64, float* __re
   }
   for (int t = 0; t < P.ntri; ++t) {
     const double v = acc[t] / wsum;
+    if (!FH_IN(CK_TABLE, (long long)t * P.nhalf + f, (long long)P.ntri * P.nhalf)) continue;
     G64[(size_t)t * P.nhalf + f] = v;
     G32[(size_t)t * P.nhalf + f] = (float)v;
   }
@@ -1125,6 +1201,7 @@ __global__ void __launch_bounds__(128) green_table_iso(GreenParams P, double* __
         if (fm[r] < 0) continue;
         const int flips = ((r & 1) ? c0 : 0) + ((r & 2) ? c1 : 0);
         const double vr = (flips & 1) ? -v : v;
+        if (!FH_IN(CK_TABLE, (long long)t * P.nhalf + fm[r], (long long)P.ntri * P.nhalf)) continue;
         G64[(size_t)t * P.nhalf + fm[r]] = vr;
         G32[(size_t)t * P.nhalf + fm[r]] = (float)vr;
       }

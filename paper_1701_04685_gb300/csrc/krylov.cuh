@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(kKryThreads) kry_update_xr(T* __restrict__ x, 
                                                              double* __restrict__ part) {
   const int load = blockIdx.x / bpl, q = blockIdx.x - load * bpl;
   ResAcc<T> arr, arh, axx;
-  if (!st[load].done) {
+  if (FH_IN(CK_KRY, load, ctl->nload) && !st[load].done) {
     const T alpha = (T)sc[load].alpha, omega = (T)sc[load].omega;
     const size_t base = (size_t)load * nv * m;
     for (int c = 0; c < nv; ++c) {
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kKryThreads) kry_init(T* __restrict__ r, T* __
                                                         double* __restrict__ part) {
   const int load = blockIdx.x / bpl, q = blockIdx.x - load * bpl;
   ResAcc<T> arr, axx, unused;
-  if (!st[load].done) {
+  if (FH_IN(CK_KRY, load, ctl->nload) && !st[load].done) {
     const size_t base = (size_t)load * nv * m;
     for (int c = 0; c < nv; ++c) {
       const T e0 = (T)ctl->eps0[load][c];

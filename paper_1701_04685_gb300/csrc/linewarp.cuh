@@ -65,6 +65,10 @@ __global__ void __launch_bounds__(kColThreads) line_pass_warp6(GridInfo g, const
   __syncthreads();
   float2* Sl = S + (size_t)load * NV * g.nhalf;
   auto goff = [&](int w, int n) -> long long { return colbase[w] + (long long)n * stride; };
+  // extents for the checked build: the launch's loads, the tile
+  const long long sl0 = (long long)load * NV * g.nhalf, nS = (long long)nload * NV * g.nhalf;
+  constexpr long long nT = (long long)NV * kColTile * LS;
+  (void)sl0; (void)nS;
 
   // 1. tile in: thread t takes entries t + kColThreads * i, column fastest
   {
@@ -75,14 +79,15 @@ __global__ void __launch_bounds__(kColThreads) line_pass_warp6(GridInfo g, const
       const int w = idx % kColTile, t = idx / kColTile;
       const int n = t % N, c = t / N;
       v[i] = make_float2(0.f, 0.f);
-      if (q0 + w < ncols) v[i] = Sl[(size_t)c * g.nhalf + goff(w, n)];
+      if (q0 + w < ncols && FH_IN(CK_COL_S, sl0 + (long long)c * g.nhalf + goff(w, n), nS))
+        v[i] = Sl[(size_t)c * g.nhalf + goff(w, n)];
     }
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
       const int idx = threadIdx.x + kColThreads * i;
       const int w = idx % kColTile, t = idx / kColTile;
       const int n = t % N, c = t / N;
-      tile[(c * kColTile + w) * LS + wpad(n)] = v[i];
+      if (FH_IN(CK_COL_TILE, (c * kColTile + w) * LS + wpad(n), nT)) tile[(c * kColTile + w) * LS + wpad(n)] = v[i];
     }
   }
   __syncthreads();
@@ -142,6 +147,7 @@ __global__ void __launch_bounds__(kColThreads) line_pass_warp6(GridInfo g, const
       const long long q = q0 + w;
       if (q >= ncols) continue;
       const long long f = (long long)n * stride + q;
+      if (!FH_IN(CK_COL_G, f, g.nhalf) || !FH_IN(CK_COL_TILE, ((NV - 1) * kColTile + w) * LS + wpad(n), nT)) continue;
       float2 tv[NV];
 #pragma unroll
       for (int c = 0; c < NV; ++c) tv[c] = tile[(c * kColTile + w) * LS + wpad(n)];
@@ -174,14 +180,16 @@ __global__ void __launch_bounds__(kColThreads) line_pass_warp6(GridInfo g, const
       const int idx = threadIdx.x + kColThreads * i;
       const int w = idx % kColTile, t = idx / kColTile;
       const int n = t % N, c = t / N;
-      v[i] = tile[(c * kColTile + w) * LS + wpad(n)];
+      v[i] = FH_IN(CK_COL_TILE, (c * kColTile + w) * LS + wpad(n), nT) ? tile[(c * kColTile + w) * LS + wpad(n)]
+                                                                        : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
       const int idx = threadIdx.x + kColThreads * i;
       const int w = idx % kColTile, t = idx / kColTile;
       const int n = t % N, c = t / N;
-      if (q0 + w < ncols) Sl[(size_t)c * g.nhalf + goff(w, n)] = v[i];
+      if (q0 + w < ncols && FH_IN(CK_COL_S, sl0 + (long long)c * g.nhalf + goff(w, n), nS))
+        Sl[(size_t)c * g.nhalf + goff(w, n)] = v[i];
     }
   }
 }

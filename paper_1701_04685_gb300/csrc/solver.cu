@@ -1185,7 +1185,81 @@ fh_status profile_passes(fh_solver* s, int prec, int nload, int reps, double* ms
 }
 }  // namespace
 
+namespace {
+
+const char* check_site_name(int site) {
+  static const char* names[fh::CK_NSITES] = {
+      "?", "row pass: half spectrum", "row pass: strain", "row pass: phase", "row pass: work buffer",
+      "row pass: stiffness field", "partial sums", "line pass: half spectrum", "line pass: table",
+      "line pass: line buffer", "warp row pass: half spectrum", "warp row pass: strain", "warp row pass: phase",
+      "warp row pass: scratch", "warp column pass: half spectrum", "warp column pass: table",
+      "warp column pass: tile", "two-step column pass: half spectrum", "two-step column pass: table",
+      "two-step column pass: tile", "1-D Green step", "mean stress", "Krylov vectors", "cluster solve",
+      "Green table", "self test"};
+  return (site > 0 && site < fh::CK_NSITES) ? names[site] : "?";
+}
+
+// Checked build: after an entry point's work, the record of the first index
+// found outside its array turns the call's status into FH_ERR_INTERNAL (the
+// record is cleared).  Without FH_CHECKED the status passes through.
+fh_status checked(fh_status rc) {
+#ifdef FH_CHECKED
+  CK(cudaDeviceSynchronize());
+  fh::CheckRecord rec{};
+  CK(cudaMemcpyFromSymbol(&rec, fh::g_check, sizeof(rec)));
+  if (rec.count != 0ull) {
+    const fh::CheckRecord zero{};
+    CK(cudaMemcpyToSymbol(fh::g_check, &zero, sizeof(zero)));
+    fh::set_error(std::string("index check failed (") + std::to_string(rec.count) + " accesses): " +
+                  check_site_name(rec.site) + ", index " + std::to_string(rec.index) + " outside [0, " +
+                  std::to_string(rec.extent) + ")");
+    return FH_ERR_INTERNAL;
+  }
+#endif
+  return rc;
+}
+
+#ifdef FH_CHECKED
+// one index inside and one outside a declared extent of 4 (the buffer holds
+// 64 entries, so even a failed check would stay inside it)
+__global__ void check_selftest_kernel(int* buf) {
+  for (int i = 3; i <= 5; i += 2)
+    if (FH_IN(fh::CK_SELFTEST, i, 4)) buf[i] = 1;
+}
+#endif
+
+}  // namespace
+
 extern "C" {
+
+int fh_checked_build(void) {
+#ifdef FH_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+fh_status fh_check_selftest(void) {
+#ifdef FH_CHECKED
+  fh_status rc = checked(FH_OK);   // start from a clear record
+  if (rc != FH_OK) return rc;
+  int* buf = nullptr;
+  CK(cudaMalloc(&buf, 64 * sizeof(int)));
+  check_selftest_kernel<<<1, 1>>>(buf);
+  cudaError_t e = cudaGetLastError();
+  rc = checked(FH_OK);
+  cudaFree(buf);
+  if (e != cudaSuccess) {
+    fh::set_error(std::string("self test launch: ") + cudaGetErrorString(e));
+    return FH_ERR_CUDA;
+  }
+  return rc;
+#else
+  fh::set_error("not a checked build (compile with FH_CHECKED)");
+  return FH_ERR_UNSUPPORTED;
+#endif
+}
 
 const char* fh_status_string(fh_status st) {
   switch (st) {
@@ -1507,7 +1581,7 @@ fh_status fh_set_stiffness_field(fh_solver* s, const double* C) {
   return fh_set_stiffness_phases(s, ids.data(), nphase, table);
 }
 
-fh_status fh_set_reference(fh_solver* s, const double* C0) {
+static fh_status fh_set_reference_impl(fh_solver* s, const double* C0) {
   NvtxRange range("fh_set_reference (Gamma^p table)");
   if (!s) { fh::set_error("null solver"); return FH_ERR_ARG; }
   if (!s->have_phases) { fh::set_error("set the stiffness before the reference medium"); return FH_ERR_STATE; }
@@ -1603,6 +1677,10 @@ fh_status fh_set_reference(fh_solver* s, const double* C0) {
   }
   s->have_table = true;
   return FH_OK;
+}
+
+fh_status fh_set_reference(fh_solver* s, const double* C0) {
+  return checked(fh_set_reference_impl(s, C0));
 }
 
 }  // extern "C"
@@ -2094,7 +2172,7 @@ fh_status batch_cluster_choice(fh_solver* s, int prec, int* path, int* cs) {
 
 extern "C" {
 
-fh_status fh_solve(fh_solver* s, int nload, const double* eps0, const fh_solve_opts* opts, fh_result* res) {
+static fh_status fh_solve_impl(fh_solver* s, int nload, const double* eps0, const fh_solve_opts* opts, fh_result* res) {
   NvtxRange range("fh_solve");
   fh_status rc = validate_solve(s, nload, eps0, opts);
   if (rc != FH_OK) return rc;
@@ -2152,7 +2230,11 @@ fh_status fh_solve(fh_solver* s, int nload, const double* eps0, const fh_solve_o
   return finish_solve(s, nload, eps0, A, &B, mixed, res);
 }
 
-fh_status fh_solve_batch(fh_solver* const* solvers, int n, const int* nload, const double* const* eps0,
+fh_status fh_solve(fh_solver* s, int nload, const double* eps0, const fh_solve_opts* opts, fh_result* res) {
+  return checked(fh_solve_impl(s, nload, eps0, opts, res));
+}
+
+static fh_status fh_solve_batch_impl(fh_solver* const* solvers, int n, const int* nload, const double* const* eps0,
                          const fh_solve_opts* opts, fh_result* res) {
   NvtxRange range("fh_solve_batch");
   if (!solvers || !nload || !eps0 || !opts || n < 1) { fh::set_error("null argument or empty batch"); return FH_ERR_ARG; }
@@ -2239,6 +2321,11 @@ fh_status fh_solve_batch(fh_solver* const* solvers, int n, const int* nload, con
     if (status_rank(st) > status_rank(worst)) worst = st;
   }
   return worst;
+}
+
+fh_status fh_solve_batch(fh_solver* const* solvers, int n, const int* nload, const double* const* eps0,
+                         const fh_solve_opts* opts, fh_result* res) {
+  return checked(fh_solve_batch_impl(solvers, n, nload, eps0, opts, res));
 }
 
 fh_status fh_get_strain(const fh_solver* sc, int load, double* E) {
@@ -2372,7 +2459,7 @@ fh_status fh_get_green(const fh_solver* s, double* G) {
 }
 
 
-fh_status fh_profile_passes(fh_solver* s, int nload, int precision, int reps, double* ms) {
+static fh_status fh_profile_passes_impl(fh_solver* s, int nload, int precision, int reps, double* ms) {
   if (!s || !ms) { fh::set_error("null argument"); return FH_ERR_ARG; }
   if (!s->have_solution || nload != s->last_nload) { fh::set_error("profile needs a prior solve with the same nload"); return FH_ERR_STATE; }
   if (reps < 1 || reps > 100000) { fh::set_error("reps out of range"); return FH_ERR_ARG; }
@@ -2382,6 +2469,10 @@ fh_status fh_profile_passes(fh_solver* s, int nload, int precision, int reps, do
   if (rc != FH_OK) return rc;
   return precision == FH_PREC_FP64 ? profile_passes<double>(s, precision, nload, reps, ms)
                                    : profile_passes<float>(s, precision, nload, reps, ms);
+}
+
+fh_status fh_profile_passes(fh_solver* s, int nload, int precision, int reps, double* ms) {
+  return checked(fh_profile_passes_impl(s, nload, precision, reps, ms));
 }
 
 fh_status fh_get_tuning(const fh_solver* s, int precision, int* path, int* cluster, int* candidate,

@@ -532,6 +532,15 @@ __global__ void __launch_bounds__(kWarpRowThreads, (P <= 4 ? 2 : 1)) row_pass_wa
     const T* Eload = E + (size_t)load * NV * cstrE;
     cplx<T>* Sload = S + (size_t)load * NV * cstrS;
     for (long long row = (long long)qb * NW + warp; row < g.nrows; row += (long long)blocks_per_load * NW) {
+      // checked build: the largest S, E, phase and scratch offsets of the row
+      // (every access of the row lies between the row's first and these)
+      if (!(FH_IN(CK_WROW_S, ((long long)load * NV + NV - 1) * (long long)cstrS + row * H + H - 1,
+                  (long long)ctl->nload * NV * g.nhalf) &&
+            FH_IN(CK_WROW_E, ((long long)load * NV + NV - 1) * (long long)cstrE + row * L + L - 1,
+                  (long long)ctl->nload * NV * g.m) &&
+            FH_IN(CK_WROW_PHASE, row * L + L - 1, g.m) &&
+            FH_IN(CK_WROW_SCRATCH, wpad((6 * H > 3 * L ? 6 * H : 3 * L) - 1), WS)))
+        continue;
       T* Er = E + (size_t)load * NV * cstrE + row * L;
       cplx<T>* Sr = Sload + row * H;
       // 1. every global load of the row
@@ -552,7 +561,10 @@ __global__ void __launch_bounds__(kWarpRowThreads, (P <= 4 ? 2 : 1)) row_pass_wa
 #pragma unroll
         for (int j = 0; j < P; ++j) ev[c][j] = Eload[c * cstrE + row * L + lane + 32 * j];
 #pragma unroll
-      for (int j = 0; j < P; ++j) ph[j] = KINV ? 0 : phase[row * L + lane + 32 * j];
+      for (int j = 0; j < P; ++j) {
+        ph[j] = KINV ? 0 : phase[row * L + lane + 32 * j];
+        if (!FH_IN(CK_WROW_PHASE, ph[j], 16)) ph[j] = 0;
+      }
       cplx<T> z[3][P];
       if (!FIRST) {
         // 2. Z = A + i B per line pair from the half spectra, inverse FFT
