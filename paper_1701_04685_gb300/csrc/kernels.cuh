@@ -700,13 +700,20 @@ __global__ void green_1d(GridInfo g, cplx<T>* __restrict__ S, const T* __restric
 
 // ---------------------------------------------------------------------------
 // mean stress <C:(E + eps0)> per load, FP64, fixed-order reduction.
+// With at most four phases (and no point-by-point stiffness) C is constant on
+// each phase, so the block sums E + eps0 over the points of every phase
+// (additions only) and applies the phase matrices to those sums:
+// sum_x C(x):(E(x) + eps0) = sum_p C_p : sum_{x in phase p} (E(x) + eps0).
 // ---------------------------------------------------------------------------
+constexpr int kMeanPhaseSums = 4;
+
 template <typename T>
 __global__ void __launch_bounds__(256) mean_stress(GridInfo g, const T* __restrict__ E,
                                                    const uint8_t* __restrict__ phase,
                                                    const double* __restrict__ Cp, Control* ctl,
                                                    double* __restrict__ partials, double* __restrict__ out,
-                                                   int blocks_per_load, const double* __restrict__ Cfld = nullptr) {
+                                                   int blocks_per_load, const double* __restrict__ Cfld = nullptr,
+                                                   int nphase = 16) {
   __shared__ double red[32];
   __shared__ unsigned int s_ticket;
   const int load = blockIdx.x / blocks_per_load;
@@ -716,6 +723,31 @@ __global__ void __launch_bounds__(256) mean_stress(GridInfo g, const T* __restri
   double e0[MAXV];
   for (int c = 0; c < nv; ++c) e0[c] = ctl->eps0[load][c];
   const size_t Ebase = (size_t)load * nv * g.m;
+  if (!Cfld && nphase <= kMeanPhaseSums) {
+    double sp[kMeanPhaseSums][MAXV];
+#pragma unroll
+    for (int p = 0; p < kMeanPhaseSums; ++p)
+#pragma unroll
+      for (int c = 0; c < MAXV; ++c) sp[p][c] = 0.0;
+    for (long long i = (long long)q * blockDim.x + threadIdx.x; i < g.m; i += (long long)blocks_per_load * blockDim.x) {
+      if (!FH_IN(CK_MEAN, (long long)Ebase + (long long)(nv - 1) * g.m + i, (long long)ctl->nload * nv * g.m)) continue;
+      const int ph = phase[i];
+#pragma unroll
+      for (int c = 0; c < MAXV; ++c) {
+        if (c >= nv) break;
+        const double e = (double)E[Ebase + (size_t)c * g.m + i] + e0[c];
+#pragma unroll
+        for (int p = 0; p < kMeanPhaseSums; ++p) sp[p][c] += (ph == p) ? e : 0.0;
+      }
+    }
+    for (int p = 0; p < nphase; ++p)
+      for (int c = 0; c < nv; ++c) {
+        const double v = block_sum(sp[p][c], red);
+        if (threadIdx.x == 0)
+          for (int a = 0; a < nv; ++a) acc[a] += Cp[((size_t)p * nv + a) * nv + c] * v;
+        __syncthreads();
+      }
+  } else
   for (long long i = (long long)q * blockDim.x + threadIdx.x; i < g.m; i += (long long)blocks_per_load * blockDim.x) {
     double e[MAXV];
     if (!FH_IN(CK_MEAN, (long long)Ebase + (long long)(nv - 1) * g.m + i, (long long)ctl->nload * nv * g.m)) continue;

@@ -686,7 +686,7 @@ fh_status run_solve(fh_solver* s, int prec, int nload, int chunk, int max_iter, 
   }
   const int bpl = std::max(1, (int)std::min<long long>((s->g.m + kThreads - 1) / kThreads, kMeanBlocks));
   fh::mean_stress<T><<<nload * bpl, kThreads, 0, s->work>>>(s->g, Eptr<T>(s), s->phase, s->Cp64, s->ctl, s->partials2,
-                                                            s->mstress, bpl, s->field ? s->Cf64 : nullptr);
+                                                            s->mstress, bpl, s->field ? s->Cf64 : nullptr, s->nphase);
   CK(cudaGetLastError());
   CK(cudaEventRecord(s->ev1, s->work));
   *launches = 2 + launched * (1 + line_launches_per_iter(s, prec));
@@ -835,7 +835,7 @@ fh_status run_bicgstab(fh_solver* s, int prec, int nload, int chunk, int max_ite
   }
   const int bpl = std::max(1, (int)std::min<long long>((s->g.m + kThreads - 1) / kThreads, kMeanBlocks));
   fh::mean_stress<T><<<nload * bpl, kThreads, 0, s->work>>>(s->g, x, s->phase, s->Cp64, s->ctl, s->partials2,
-                                                            s->mstress, bpl, s->field ? s->Cf64 : nullptr);
+                                                            s->mstress, bpl, s->field ? s->Cf64 : nullptr, s->nphase);
   CK(cudaGetLastError());
   CK(cudaEventRecord(s->ev1, s->work));
   *launches = (2 + line_launches_per_iter(s->g)) + 2 + 1 + launched * kry_launches_per_iter(s->g);
@@ -997,7 +997,7 @@ fh_status run_solve_cluster(fh_solver* s, int nload, int cs, long long* launches
   if (rc != FH_OK) return rc;
   const int bpl = std::max(1, (int)std::min<long long>((s->g.m + kThreads - 1) / kThreads, kMeanBlocks));
   fh::mean_stress<T><<<nload * bpl, kThreads, 0, s->work>>>(s->g, Eptr<T>(s), s->phase, s->Cp64, s->ctl, s->partials2,
-                                                            s->mstress, bpl, s->field ? s->Cf64 : nullptr);
+                                                            s->mstress, bpl, s->field ? s->Cf64 : nullptr, s->nphase);
   CK(cudaGetLastError());
   CK(cudaEventRecord(s->ev1, s->work));
   *launches = 2;
@@ -2027,7 +2027,7 @@ template <typename T>
 fh_status finish_deferred(fh_solver* s, int nload, PhaseOut* out) {
   const int bpl = std::max(1, (int)std::min<long long>((s->g.m + kThreads - 1) / kThreads, kMeanBlocks));
   fh::mean_stress<T><<<nload * bpl, kThreads, 0, s->work>>>(s->g, Eptr<T>(s), s->phase, s->Cp64, s->ctl, s->partials2,
-                                                            s->mstress, bpl, s->field ? s->Cf64 : nullptr);
+                                                            s->mstress, bpl, s->field ? s->Cf64 : nullptr, s->nphase);
   CK(cudaGetLastError());
   CK(cudaEventRecord(s->ev1, s->work));
   CK(cudaMemcpyAsync(s->h_states, s->st, sizeof(LoadState) * nload, cudaMemcpyDeviceToHost, s->work));
