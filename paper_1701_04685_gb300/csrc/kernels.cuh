@@ -724,29 +724,55 @@ __global__ void __launch_bounds__(256) mean_stress(GridInfo g, const T* __restri
   for (int c = 0; c < nv; ++c) e0[c] = ctl->eps0[load][c];
   const size_t Ebase = (size_t)load * nv * g.m;
   if (!Cfld && nphase <= kMeanPhaseSums) {
-    double sp[kMeanPhaseSums][MAXV];
+    // per thread: the sum of E over all its points and over its points of
+    // phases 1 .. nphase-1 (phase 0 = all - the others), and the point counts;
+    // eps0 enters through the counts
+    double tot[MAXV], sp[kMeanPhaseSums][MAXV];
+    long long cnt[kMeanPhaseSums] = {0, 0, 0, 0};
 #pragma unroll
-    for (int p = 0; p < kMeanPhaseSums; ++p)
+    for (int c = 0; c < MAXV; ++c) {
+      tot[c] = 0.0;
 #pragma unroll
-      for (int c = 0; c < MAXV; ++c) sp[p][c] = 0.0;
+      for (int p = 0; p < kMeanPhaseSums; ++p) sp[p][c] = 0.0;
+    }
     for (long long i = (long long)q * blockDim.x + threadIdx.x; i < g.m; i += (long long)blocks_per_load * blockDim.x) {
       if (!FH_IN(CK_MEAN, (long long)Ebase + (long long)(nv - 1) * g.m + i, (long long)ctl->nload * nv * g.m)) continue;
       const int ph = phase[i];
 #pragma unroll
+      for (int p = 1; p < kMeanPhaseSums; ++p) cnt[p] += (ph == p);
+      cnt[0] += 1;
+#pragma unroll
       for (int c = 0; c < MAXV; ++c) {
         if (c >= nv) break;
-        const double e = (double)E[Ebase + (size_t)c * g.m + i] + e0[c];
+        const double e = (double)E[Ebase + (size_t)c * g.m + i];
+        tot[c] += e;
 #pragma unroll
-        for (int p = 0; p < kMeanPhaseSums; ++p) sp[p][c] += (ph == p) ? e : 0.0;
+        for (int p = 1; p < kMeanPhaseSums; ++p)
+          if (p < nphase && ph == p) sp[p][c] += e;
       }
     }
-    for (int p = 0; p < nphase; ++p)
-      for (int c = 0; c < nv; ++c) {
-        const double v = block_sum(sp[p][c], red);
-        if (threadIdx.x == 0)
-          for (int a = 0; a < nv; ++a) acc[a] += Cp[((size_t)p * nv + a) * nv + c] * v;
-        __syncthreads();
+    // block sums; thread 0 forms sum_p C_p : (sum over phase p of E + n_p eps0)
+    double n[kMeanPhaseSums], S[kMeanPhaseSums][MAXV];
+    for (int p = 0; p < nphase; ++p) n[p] = block_sum((double)cnt[p], red);
+    for (int c = 0; c < nv; ++c) {
+      const double t = block_sum(tot[c], red);
+      double rest = 0.0;
+      for (int p = 1; p < nphase; ++p) {
+        S[p][c] = block_sum(sp[p][c], red);
+        rest += S[p][c];
       }
+      S[0][c] = t - rest;
+    }
+    if (threadIdx.x == 0) {
+      double n0 = n[0];
+      for (int p = 1; p < nphase; ++p) n0 -= n[p];
+      n[0] = n0;
+      for (int p = 0; p < nphase; ++p)
+        for (int c = 0; c < nv; ++c) {
+          const double sc = S[p][c] + n[p] * e0[c];
+          for (int a = 0; a < nv; ++a) acc[a] += Cp[((size_t)p * nv + a) * nv + c] * sc;
+        }
+    }
   } else
   for (long long i = (long long)q * blockDim.x + threadIdx.x; i < g.m; i += (long long)blocks_per_load * blockDim.x) {
     double e[MAXV];
@@ -1051,6 +1077,18 @@ __device__ __forceinline__ double axis_symbol(const GreenParams& P, int i, long 
   return fmin(1.0, fmax(0.0, (0.5 + a - u) / (2.0 * a)));
 }
 
+// 1 / r for r >= 1 by Newton's method: an FP32 seed (relative error about
+// 2^-23), then two steps y <- y + y (1 - r y) in FP64, each squaring the
+// relative error, so the result is within a few units in the last place of
+// FP64 (the alias loops take one reciprocal per alias; FP64 is their bound)
+__device__ __forceinline__ double recip_newton(double r) {
+  double y = (double)(1.0f / (float)r);
+  double e = fma(-r, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-r, y, 1.0);
+  return fma(y, e, y);
+}
+
 // index of the fourth moment with exponents (e0, e1, e2) of n_0, n_1, n_2 in
 // the accumulation order of green_table_iso<3>
 __device__ __forceinline__ int moment_index3(int e1, int e2) {
@@ -1127,7 +1165,7 @@ __global__ void __launch_bounds__(128) green_table_iso(GreenParams P, double* __
         const double p00 = k0 * k0, p11 = k1 * k1, p01 = k0 * k1;
         const double r2 = p00 + p11;
         if (r2 == 0.0) continue;  // Gamma^0(0) = 0
-        const double inv = __drcp_rn(r2);
+        const double inv = recip_newton(r2);
         const double q = wa * wl[1][b] * inv * inv;
         const double q00 = q * p00, q01 = q * p01, q11 = q * p11;
         B[0] = fma(q00, p00, B[0]);  // n0^4
@@ -1156,7 +1194,7 @@ __global__ void __launch_bounds__(128) green_table_iso(GreenParams P, double* __
           const double r2 = p00 + p11 + p22;
           if (r2 == 0.0) continue;  // Gamma^0(0) = 0
           const double p01 = k0 * k1, p02 = k0 * k2, p12 = k1 * k2;
-          const double inv = __drcp_rn(r2);
+          const double inv = recip_newton(r2);
           const double q = wab * wl[2][c] * inv * inv;
           const double q00 = q * p00, q01 = q * p01, q02 = q * p02, q11 = q * p11, q12 = q * p12, q22 = q * p22;
           B[0] = fma(q00, p00, B[0]);    // (4,0,0)

@@ -131,6 +131,7 @@ struct fh_solver {
   int plane[2] = {0, 0};     // 3-D FP32: > 0 = the fused plane pass applies (axis-1 P, axis-2 P packed as 10 P1 + P2)
   bool plane_on = false;     // path 3 of the solve in progress: take the fused plane pass where it applies
   bool col2s = true;         // 3-D FP32 columns of 32, 64 or 128 points: the two-step pass (else the warp-exchange pass)
+  bool skip_mean = false;   // the phase in progress is followed by another (mixed mode): its mean stress is not used
   int warp_res[2] = {0, 0};  // resident blocks per SM of that pass
   int sms = 0;               // multiprocessors of the device
   int row_bpl[2] = {1, 1};
@@ -685,11 +686,12 @@ fh_status run_solve(fh_solver* s, int prec, int nload, int chunk, int max_iter, 
     }
   }
   const int bpl = std::max(1, (int)std::min<long long>((s->g.m + kThreads - 1) / kThreads, kMeanBlocks));
-  fh::mean_stress<T><<<nload * bpl, kThreads, 0, s->work>>>(s->g, Eptr<T>(s), s->phase, s->Cp64, s->ctl, s->partials2,
-                                                            s->mstress, bpl, s->field ? s->Cf64 : nullptr, s->nphase);
+  if (!s->skip_mean)
+    fh::mean_stress<T><<<nload * bpl, kThreads, 0, s->work>>>(s->g, Eptr<T>(s), s->phase, s->Cp64, s->ctl, s->partials2,
+                                                              s->mstress, bpl, s->field ? s->Cf64 : nullptr, s->nphase);
   CK(cudaGetLastError());
   CK(cudaEventRecord(s->ev1, s->work));
-  *launches = 2 + launched * (1 + line_launches_per_iter(s, prec));
+  *launches = (s->skip_mean ? 1 : 2) + launched * (1 + line_launches_per_iter(s, prec));
   return FH_OK;
 }
 
@@ -834,11 +836,12 @@ fh_status run_bicgstab(fh_solver* s, int prec, int nload, int chunk, int max_ite
     }
   }
   const int bpl = std::max(1, (int)std::min<long long>((s->g.m + kThreads - 1) / kThreads, kMeanBlocks));
-  fh::mean_stress<T><<<nload * bpl, kThreads, 0, s->work>>>(s->g, x, s->phase, s->Cp64, s->ctl, s->partials2,
-                                                            s->mstress, bpl, s->field ? s->Cf64 : nullptr, s->nphase);
+  if (!s->skip_mean)
+    fh::mean_stress<T><<<nload * bpl, kThreads, 0, s->work>>>(s->g, x, s->phase, s->Cp64, s->ctl, s->partials2,
+                                                              s->mstress, bpl, s->field ? s->Cf64 : nullptr, s->nphase);
   CK(cudaGetLastError());
   CK(cudaEventRecord(s->ev1, s->work));
-  *launches = (2 + line_launches_per_iter(s->g)) + 2 + 1 + launched * kry_launches_per_iter(s->g);
+  *launches = (2 + line_launches_per_iter(s->g)) + 2 + (s->skip_mean ? 0 : 1) + launched * kry_launches_per_iter(s->g);
   return FH_OK;
 }
 
@@ -996,11 +999,12 @@ fh_status run_solve_cluster(fh_solver* s, int nload, int cs, long long* launches
   fh_status rc = cs == 16 ? launch_cluster<T, 16>(s, nload) : launch_cluster<T, 8>(s, nload);
   if (rc != FH_OK) return rc;
   const int bpl = std::max(1, (int)std::min<long long>((s->g.m + kThreads - 1) / kThreads, kMeanBlocks));
-  fh::mean_stress<T><<<nload * bpl, kThreads, 0, s->work>>>(s->g, Eptr<T>(s), s->phase, s->Cp64, s->ctl, s->partials2,
-                                                            s->mstress, bpl, s->field ? s->Cf64 : nullptr, s->nphase);
+  if (!s->skip_mean)
+    fh::mean_stress<T><<<nload * bpl, kThreads, 0, s->work>>>(s->g, Eptr<T>(s), s->phase, s->Cp64, s->ctl, s->partials2,
+                                                              s->mstress, bpl, s->field ? s->Cf64 : nullptr, s->nphase);
   CK(cudaGetLastError());
   CK(cudaEventRecord(s->ev1, s->work));
-  *launches = 2;
+  *launches = s->skip_mean ? 1 : 2;
   return FH_OK;
 }
 
@@ -2026,13 +2030,14 @@ namespace {
 template <typename T>
 fh_status finish_deferred(fh_solver* s, int nload, PhaseOut* out) {
   const int bpl = std::max(1, (int)std::min<long long>((s->g.m + kThreads - 1) / kThreads, kMeanBlocks));
-  fh::mean_stress<T><<<nload * bpl, kThreads, 0, s->work>>>(s->g, Eptr<T>(s), s->phase, s->Cp64, s->ctl, s->partials2,
-                                                            s->mstress, bpl, s->field ? s->Cf64 : nullptr, s->nphase);
+  if (!s->skip_mean)
+    fh::mean_stress<T><<<nload * bpl, kThreads, 0, s->work>>>(s->g, Eptr<T>(s), s->phase, s->Cp64, s->ctl, s->partials2,
+                                                              s->mstress, bpl, s->field ? s->Cf64 : nullptr, s->nphase);
   CK(cudaGetLastError());
   CK(cudaEventRecord(s->ev1, s->work));
   CK(cudaMemcpyAsync(s->h_states, s->st, sizeof(LoadState) * nload, cudaMemcpyDeviceToHost, s->work));
   CK(cudaMemcpyAsync(s->h_ms, s->mstress, sizeof(double) * nload * fh::MAXV, cudaMemcpyDeviceToHost, s->work));
-  out->launches = 2;   // its share of the queue launch, and the mean stress
+  out->launches = s->skip_mean ? 1 : 2;   // its share of the queue launch, and the mean stress
   return FH_OK;
 }
 
@@ -2173,6 +2178,7 @@ fh_status batch_cluster_choice(fh_solver* s, int prec, int* path, int* cs) {
 extern "C" {
 
 static fh_status fh_solve_impl(fh_solver* s, int nload, const double* eps0, const fh_solve_opts* opts, fh_result* res) {
+  if (s) s->skip_mean = false;
   NvtxRange range("fh_solve");
   fh_status rc = validate_solve(s, nload, eps0, opts);
   if (rc != FH_OK) return rc;
@@ -2214,8 +2220,10 @@ static fh_status fh_solve_impl(fh_solver* s, int nload, const double* eps0, cons
   // which drifts from the true one, so it aims at half the tolerance; the FP64
   // phase then usually needs a single fixed-point step to confirm it
   const double tol1 = (mixed && opts->method == 1) ? 0.5 * opts->tol : opts->tol;
+  s->skip_mean = mixed;   // the FP64 phase computes the mean stress that is returned
   rc = solve_phase(s, nload, eps0, tol1, opts->max_iter, prec1, opts->init, chunk, path1, cs1, nullptr, &A,
                    mixed ? kStallWindow : 0);
+  s->skip_mean = false;
   s->method = 0;
   if (rc != FH_OK) return rc;
   if (mixed) {
@@ -2241,6 +2249,7 @@ static fh_status fh_solve_batch_impl(fh_solver* const* solvers, int n, const int
   for (int i = 0; i < n; ++i) {
     fh_status rc = validate_solve(solvers[i], nload[i], eps0[i], opts);
     if (rc != FH_OK) return rc;
+    solvers[i]->skip_mean = false;
     for (int j = 0; j < i; ++j)
       if (solvers[j] == solvers[i]) { fh::set_error("a solver appears twice in the batch"); return FH_ERR_ARG; }
   }
@@ -2274,6 +2283,7 @@ static fh_status fh_solve_batch_impl(fh_solver* const* solvers, int n, const int
     }
     solvers[i]->method = opts->method;
     if (opts->method == 1) p1 = 1;
+    solvers[i]->skip_mean = mixed;   // the FP64 phase computes the mean stress that is returned
     rc = begin_phase(solvers[i], nload[i], eps0[i], (mixed && opts->method == 1) ? 0.5 * opts->tol : opts->tol,
                      opts->max_iter, prec1, opts->init, chunk, p1, c1, nullptr, &A[i], mixed ? kStallWindow : 0, true);
     solvers[i]->method = 0;
@@ -2282,6 +2292,7 @@ static fh_status fh_solve_batch_impl(fh_solver* const* solvers, int n, const int
   }
   {
     fh_status rc = run_queued(solvers, nload, deferred1, prec1, A);
+    for (int i = 0; i < n; ++i) solvers[i]->skip_mean = false;
     if (rc != FH_OK) return rc;
   }
   for (int i = 0; i < n; ++i) {

@@ -59,6 +59,12 @@ WARP_CASES = [
     # every column pass of 64 points, the Green step's included
     ("cols64_cube", [[64, 0, 0], [0, 64, 0], [0, 0, 64]], {"kind": "dlvp", "alpha": [0.2, 0.25, 0.3]},
      [(1.0, 0.3), (20.0, 0.25)], _ball(0.27), [64, 64, 64]),
+    # ragged tiles: 4 x 17 = 68 columns of 32 points (the last tile holds 4),
+    # and a two-axis grid whose Green pass has 33 columns of 64 points
+    ("cols32_ragged", [[4, 0, 0], [0, 32, 0], [0, 0, 32]], {"kind": "boxspline", "order": 2, "radius": 2},
+     [(1.0, 0.3), (25.0, 0.3)], _ball(0.3), [4, 32, 32]),
+    ("cols64_two_axes_ragged", [[2, 1, 0], [0, 32, 0], [0, 0, 64]], {"kind": "dlvp", "alpha": [0.25, 0.2, 0.15]},
+     [(1.0, 0.3), (15.0, 0.3)], _ball(0.25), [64, 64]),
 ]
 IDS = [c[0] for c in WARP_CASES]
 
@@ -157,7 +163,7 @@ def test_two_step_and_warp_exchange_column_passes_agree(fh):
     """The column passes of 64 points in the two-step form (the default) and in
     the warp-exchange form (autotuner candidate 5, tune = 7) give the same
     iterates to FP32 rounding."""
-    case = _case(WARP_CASES[-1])
+    case = _case([c for c in WARP_CASES if c[0] == "cols64_cube"][0])
     s = case.product(fh)
     n = 20
     s.solve(case.eps0, tol=0.0, max_iter=n, precision=FP32, tune=2)
