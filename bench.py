@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--only-fno", action="store_true",
                     help="profiling aid: time the learned start's network forward (tensor-core and SIMT "
                          "hidden layers) and print that object")
+    ap.add_argument("--only-2d", action="store_true",
+                    help="profiling aid: run only the 2-D section (dlvp_sheared, every mode) and print that object")
     ap.add_argument("--ncu-iteration", action="store_true",
                     help="profiling aid: set up the headline workload, run 3 FP32 iterations, then launch each "
                          "pass of one FP32 iteration twice (fh_profile_passes, reps=1) and exit")
@@ -407,14 +409,14 @@ def run_headline(fh, args, dist, local_rank):
     s.solve(eps0, tol=0.0, max_iter=3, precision=prec["fp32"])
     ms = s.profile_passes(6, prec["fp32"], reps=20)
     spec, field, tab32 = 6 * 6 * nhalf * 8, 6 * 6 * p.m * 4, 21 * nhalf * 4
-    pass_bytes = {"row_pass_warp6": 2 * spec + 2 * field + p.m, "line_pass_warp6_axis0_green": 2 * spec + tab32,
-                  "line_pass_warp6_axis1_forward": 2 * spec, "line_pass_warp6_axis1_inverse": 2 * spec}
+    pass_bytes = {"row_pass_warp6": 2 * spec + 2 * field + p.m, "line_pass_2s_axis0_green": 2 * spec + tab32,
+                  "line_pass_2s_axis1_forward": 2 * spec, "line_pass_2s_axis1_inverse": 2 * spec}
     passes = {k: {"ms": float(ms[i]), "bytes": int(b), "gbs": b / (ms[i] * 1e-3) / 1e9,
                   "frac_of_hbm": b / (ms[i] * 1e-3) / 1e9 / peak} for i, (k, b) in enumerate(pass_bytes.items())}
     it_ms = float(sum(ms[:4]))
     algo = 2 * field + p.m + tab32
     traffic = profile_traffic("ncu_iteration_fp32_box3d.md")
-    roofline = {"bound": "hbm", "kernel": "one FP32 iteration: row_pass_warp6 + line_pass_warp6 (axis 1 forward, "
+    roofline = {"bound": "hbm", "kernel": "one FP32 iteration: row_pass_warp6 + line_pass_2s (axis 1 forward, "
                 "axis 0 + Green, axis 1 inverse)",
                 "achieved": algo / (it_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                 "frac": algo / (it_ms * 1e-3) / 1e9 / peak, "traffic": traffic,
@@ -597,6 +599,9 @@ def main():
     fh.library()
     if args.only_fno:
         print(json.dumps({"fno_layers": run_fno_layers(fh)}), flush=True)
+        return
+    if args.only_2d:
+        print(json.dumps({"dlvp_sheared_2d": run_2d(fh, args)}), flush=True)
         return
     if args.ncu_iteration:
         w = W.box3d()

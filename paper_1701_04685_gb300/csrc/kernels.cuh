@@ -1077,18 +1077,6 @@ __device__ __forceinline__ double axis_symbol(const GreenParams& P, int i, long 
   return fmin(1.0, fmax(0.0, (0.5 + a - u) / (2.0 * a)));
 }
 
-// 1 / r for r >= 1 by Newton's method: an FP32 seed (relative error about
-// 2^-23), then two steps y <- y + y (1 - r y) in FP64, each squaring the
-// relative error, so the result is within a few units in the last place of
-// FP64 (the alias loops take one reciprocal per alias; FP64 is their bound)
-__device__ __forceinline__ double recip_newton(double r) {
-  double y = (double)(1.0f / (float)r);
-  double e = fma(-r, y, 1.0);
-  y = fma(y, e, y);
-  e = fma(-r, y, 1.0);
-  return fma(y, e, y);
-}
-
 // index of the fourth moment with exponents (e0, e1, e2) of n_0, n_1, n_2 in
 // the accumulation order of green_table_iso<3>
 __device__ __forceinline__ int moment_index3(int e1, int e2) {
@@ -1165,7 +1153,7 @@ __global__ void __launch_bounds__(128) green_table_iso(GreenParams P, double* __
         const double p00 = k0 * k0, p11 = k1 * k1, p01 = k0 * k1;
         const double r2 = p00 + p11;
         if (r2 == 0.0) continue;  // Gamma^0(0) = 0
-        const double inv = recip_newton(r2);
+        const double inv = __drcp_rn(r2);
         const double q = wa * wl[1][b] * inv * inv;
         const double q00 = q * p00, q01 = q * p01, q11 = q * p11;
         B[0] = fma(q00, p00, B[0]);  // n0^4
@@ -1194,7 +1182,7 @@ __global__ void __launch_bounds__(128) green_table_iso(GreenParams P, double* __
           const double r2 = p00 + p11 + p22;
           if (r2 == 0.0) continue;  // Gamma^0(0) = 0
           const double p01 = k0 * k1, p02 = k0 * k2, p12 = k1 * k2;
-          const double inv = recip_newton(r2);
+          const double inv = __drcp_rn(r2);
           const double q = wab * wl[2][c] * inv * inv;
           const double q00 = q * p00, q01 = q * p01, q02 = q * p02, q11 = q * p11, q12 = q * p12, q22 = q * p22;
           B[0] = fma(q00, p00, B[0]);    // (4,0,0)
