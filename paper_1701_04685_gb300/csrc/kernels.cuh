@@ -746,9 +746,11 @@ __global__ void __launch_bounds__(256) mean_stress(GridInfo g, const T* __restri
         if (c >= nv) break;
         const double e = (double)E[Ebase + (size_t)c * g.m + i];
         tot[c] += e;
+        // the phase selects the addend, not the addition (FP64 additions are
+        // the scarce resource here: one per phase and component)
 #pragma unroll
         for (int p = 1; p < kMeanPhaseSums; ++p)
-          if (p < nphase && ph == p) sp[p][c] += e;
+          if (p < nphase) sp[p][c] += (ph == p) ? e : 0.0;
       }
     }
     // block sums; thread 0 forms sum_p C_p : (sum over phase p of E + n_p eps0)
