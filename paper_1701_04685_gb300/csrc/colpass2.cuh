@@ -62,11 +62,12 @@ __device__ __forceinline__ int c2off(int k1, int j2) { return j2 + (R2 + 1) * k1
 // w[t] = w_N^{DIR base t} for t < R (R = 4, 8 or 16): the powers t = 1, 2, 4, 8
 // come from the table tw[t] = exp(-2 pi i t / N), every other one is the
 // product of two earlier ones (at most three roundings deep)
-template <int R, int DIR>
-__device__ __forceinline__ void twiddle_powers(const float2* tw, int base, float2* w) {
-  w[0] = make_float2(1.f, 0.f);
+template <int R, int DIR, typename T = float>
+__device__ __forceinline__ void twiddle_powers(const cplx<T>* tw, int base, cplx<T>* w) {
+  w[0].x = T(1);
+  w[0].y = T(0);
 #pragma unroll
-  for (int p = 1; p < R; p <<= 1) w[p] = twl<DIR, float>(tw, base * p);
+  for (int p = 1; p < R; p <<= 1) w[p] = twl<DIR, T>(tw, base * p);
 #pragma unroll
   for (int t = 3; t < R; ++t) {
     if ((t & (t - 1)) == 0) continue;

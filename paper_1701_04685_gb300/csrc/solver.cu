@@ -22,6 +22,7 @@
 #include "warprow.cuh"
 #include "linewarp.cuh"
 #include "colpass2.cuh"
+#include "rowpass2.cuh"
 #include "krylov.cuh"
 #include "planewarp.cuh"
 
@@ -130,7 +131,9 @@ struct fh_solver {
   int row_warp[2] = {0, 0};  // > 0: warp-per-row pass with L = 32 * row_warp
   int plane[2] = {0, 0};     // 3-D FP32: > 0 = the fused plane pass applies (axis-1 P, axis-2 P packed as 10 P1 + P2)
   bool plane_on = false;     // path 3 of the solve in progress: take the fused plane pass where it applies
-  bool col2s = true;         // 3-D FP32 columns of 32, 64 or 128 points: the two-step pass (else the warp-exchange pass)
+  bool col2s = true;         // rows and columns of 32, 64 or 128 points: the two-step passes (else the earlier forms)
+  int row2[2] = {0, 0};      // 3-D fields with rows of 32, 64 or 128 points: the two-step row pass applies (L), else 0
+  int row2_bpl[2] = {1, 1};  // its blocks per load
   bool skip_mean = false;   // the phase in progress is followed by another (mixed mode): its mean stress is not used
   int warp_res[2] = {0, 0};  // resident blocks per SM of that pass
   int sms = 0;               // multiprocessors of the device
@@ -218,6 +221,15 @@ void choose_shapes(fh_solver* s, int prec) {
       s->row_smem[prec] = fh::warprow_smem<float>(g.L);
     }
   }
+  // FP64 3-D fields whose contiguous axis is 32, 64 or 128 points long: the
+  // two-step row pass (128^3 x 6 loads: 5.4 ms against 7.5 ms for the block
+  // row pass; in FP32 the warp row pass is faster, 0.288 against 0.354 ms)
+  s->row2[prec] = 0;
+  if (prec == FH_PREC_FP64 && g.nv == 6 && (g.L == 32 || g.L == 64 || g.L == 128)) {
+    const int rb = g.L == 32 ? fh::Row2<4, 8>::RB : fh::Row2<8, 8>::RB;
+    s->row2[prec] = g.L;
+    s->row2_bpl[prec] = (int)((g.nrows + rb - 1) / rb);
+  }
   // FP32 3-D grids whose axis-1 and axis-2 lengths are 32, 64 or 128 points
   // (and whose plane fits in a CTA's shared memory): the fused plane pass
   s->plane[prec] = 0;
@@ -235,7 +247,10 @@ void choose_shapes(fh_solver* s, int prec) {
     auto smem = [&](int w) { return (size_t)2 * g.nv * w * (N + 1) * csize(prec); };
     auto blocks = [&](int w) { return (long long)nl * others * ((g.H + w - 1) / w); };
     const int wmin = prec == FH_PREC_FP64 ? 2 : 4;
-    const size_t line_cap = 96 * 1024;
+    // FP64 allows a wider tile (four 128-point columns: 99 KB, two blocks per
+    // SM), measured faster than two (5.07 against 5.38 ms for the axis-0 pass
+    // at 128^3 x 6 loads)
+    const size_t line_cap = (prec == FH_PREC_FP64 ? 112 : 96) * 1024;
     while (W > wmin && (smem(W) > line_cap || blocks(W) < 2 * sms)) W /= 2;
     while (W > 1 && smem(W) > kMaxSmem) W /= 2;
     s->lineW[prec][a] = W;
@@ -490,8 +505,39 @@ void enqueue_plane(fh_solver* s, int nload) {
   }
 }
 
+// the two-step row pass (rowpass2.cuh) applies: rows of 32, 64 or 128
+// points of 3-D fields, phase-wise stiffness, not switched off by the
+// autotuner's candidate 5
+bool use_row2(const fh_solver* s, int prec) { return s->col2s && s->row2[prec] > 0 && !s->field; }
+
+template <typename T, int R1, int R2, bool FIRST, bool KINV>
+void launch_row2(fh_solver* s, int prec, int nload, T* X, const T* dC, Control* ctl, T* Wout, const T* Yaux) {
+  using C = typename fh::cplx_t<T>::type;
+  const GridInfo& g = s->g;
+  const int bpl = s->row2_bpl[prec];
+  fh::row_pass_2s<T, R1, R2, FIRST, KINV><<<(unsigned)(nload * bpl), fh::Row2<R1, R2>::THREADS,
+                                             fh::row2_smem<T, R1, R2>(), s->work>>>(
+      g, twp<T>(s->ax[g.nd - 1]), X, reinterpret_cast<C*>(s->S), s->phase, dC, ctl, s->st, s->partials, s->hist, bpl,
+      Wout, Yaux);
+}
+
+// returns the blocks per load (the partial sums' layout)
+template <typename T, bool FIRST, bool KINV>
+int enqueue_row2(fh_solver* s, int prec, int nload, T* X, const T* dC, Control* ctl, T* Wout, const T* Yaux) {
+  switch (s->row2[prec]) {
+    case 32: launch_row2<T, 4, 8, FIRST, KINV>(s, prec, nload, X, dC, ctl, Wout, Yaux); break;
+    case 64: launch_row2<T, 8, 8, FIRST, KINV>(s, prec, nload, X, dC, ctl, Wout, Yaux); break;
+    default: launch_row2<T, 8, 16, FIRST, KINV>(s, prec, nload, X, dC, ctl, Wout, Yaux); break;
+  }
+  return s->row2_bpl[prec];
+}
+
 template <typename T, bool FIRST>
 void enqueue_row_pass(fh_solver* s, int prec, int nload) {
+  if (use_row2(s, prec) && !(sizeof(T) == 4 && use_plane(s, prec))) {
+    enqueue_row2<T, FIRST, false>(s, prec, nload, Eptr<T>(s), dCptr<T>(s), s->ctl, nullptr, nullptr);
+    return;
+  }
   if constexpr (sizeof(T) == 4) {
     if (s->field) {   // point-by-point stiffness: the block row pass
       if (s->g.nv == 3) enqueue_row_pass_nv<T, 3, FIRST>(s, prec, nload);
@@ -568,9 +614,28 @@ cudaError_t set_plane_attrs_of(int code) {
   }
 }
 
+template <typename T, int R1, int R2>
+cudaError_t set_row2_attrs() {
+  const int sm = (int)fh::row2_smem<T, R1, R2>();
+  cudaError_t e = cudaFuncSetAttribute(fh::row_pass_2s<T, R1, R2, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fh::row_pass_2s<T, R1, R2, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fh::row_pass_2s<T, R1, R2, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  return e;
+}
+
 template <typename T, int NV>
 fh_status set_smem_attrs_nv(fh_solver* s, int prec) {
   const size_t rs = s->row_smem[prec];
+  if constexpr (NV == 6) {
+    switch (s->row2[prec]) {
+      case 32: CK((set_row2_attrs<T, 4, 8>())); break;
+      case 64: CK((set_row2_attrs<T, 8, 8>())); break;
+      case 128: CK((set_row2_attrs<T, 8, 16>())); break;
+      default: break;
+    }
+  }
   if (sizeof(T) == 4 && s->plane[prec] > 0) CK(set_plane_attrs_of(s->plane[prec]));
   if (rs > kMaxSmem) {
     fh::set_error("contiguous axis too long for this precision (shared memory)");
@@ -722,6 +787,7 @@ int enqueue_row_x(fh_solver* s, int prec, int nload, T* X, Control* ctl, T* Wout
   const GridInfo& g = s->g;
   C* S = reinterpret_cast<C*>(s->S);
   const int last = g.nd - 1;
+  if (use_row2(s, prec)) return enqueue_row2<T, FIRST, KINV>(s, prec, nload, X, dC_form0<T>(s), ctl, Wout, Yaux);
   if constexpr (sizeof(T) == 4) {
     const int P = s->field ? 0 : s->row_warp[prec];
     if (P > 0) {
@@ -1413,6 +1479,7 @@ fh_status fh_solver_create(const fh_pattern* p, const fh_generator* gen, int nlo
   CKS(cudaMalloc(&s->ctl, sizeof(Control)));
   CKS(cudaMalloc(&s->st, FH_MAX_LOADS * sizeof(LoadState)));
   const size_t nblk = (size_t)nload_max * std::max({s->row_bpl[0], s->row_bpl[1], s->row_bpl_gen[0], s->row_bpl_gen[1],
+                                                    s->row2_bpl[0], s->row2_bpl[1],
                                                     2 * g.dims[0]});
   CKS(cudaMalloc(&s->partials, 2 * nblk * sizeof(double)));
   CKS(cudaMalloc(&s->partials2, (size_t)nload_max * kMeanBlocks * fh::MAXV * sizeof(double)));
@@ -1897,8 +1964,9 @@ int status_rank(fh_status st) {
 //   0 the defaults
 //   4 the block row pass with twice the rows per block
 //   5 the block line passes with twice the tile width (columns per block);
-//     the 3-D FP32 columns of 32-128 points by the warp-exchange pass in
-//     place of the two-step pass
+//     rows and 3-D FP32 columns of 32-128 points by the earlier passes (warp
+//     exchange in FP32, the block row pass in FP64) in place of the two-step
+//     passes
 //   6 every axis's radix schedule in reverse order
 //   7 radix-4 stages in place of radix-8 and radix-2 pairs
 bool apply_variant(fh_solver* s, int prec, int var) {
@@ -1917,6 +1985,7 @@ bool apply_variant(fh_solver* s, int prec, int var) {
   if (var == 0) return true;
   if (var == 4) {
     if (s->row_warp[prec] > 0 && !s->field) return false;   // the warp row pass runs instead
+    if (s->row2[prec] > 0 && !s->field) return false;       // the two-step row pass runs instead
     const int rpb = 2 * d.rpb_gen;
     if (rpb > g.nrows) return false;
     const int Lp = prec == FH_PREC_FP64 ? fh::padded_len<3>(g.L) : fh::padded_len<4>(g.L);
@@ -1929,6 +1998,10 @@ bool apply_variant(fh_solver* s, int prec, int var) {
   }
   if (var == 5) {
     bool any = false;
+    if (s->row2[prec] > 0 && !s->field) {
+      s->col2s = false;
+      any = true;
+    }
     for (int a = 0; a + 1 < g.nd; ++a) {
       if (col2_len(s, prec, a) > 0) {
         s->col2s = false;
