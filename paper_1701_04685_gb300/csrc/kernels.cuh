@@ -724,56 +724,49 @@ __global__ void __launch_bounds__(256) mean_stress(GridInfo g, const T* __restri
   for (int c = 0; c < nv; ++c) e0[c] = ctl->eps0[load][c];
   const size_t Ebase = (size_t)load * nv * g.m;
   if (!Cfld && nphase <= kMeanPhaseSums) {
-    // per thread: the sum of E over all its points and over its points of
-    // phases 1 .. nphase-1 (phase 0 = all - the others), and the point counts;
-    // eps0 enters through the counts
-    double tot[MAXV], sp[kMeanPhaseSums][MAXV];
+    // per thread: the sum of E over its points of each phase and the point
+    // counts (eps0 enters through the counts).  Each phase's sum covers the
+    // same points whatever label the phase carries, and the phases'
+    // contributions are added last, so relabelling two phases (a stiffness
+    // field reduced to its distinct matrices) gives the same bits.
+    double sp[kMeanPhaseSums][MAXV];
     long long cnt[kMeanPhaseSums] = {0, 0, 0, 0};
 #pragma unroll
-    for (int c = 0; c < MAXV; ++c) {
-      tot[c] = 0.0;
+    for (int c = 0; c < MAXV; ++c)
 #pragma unroll
       for (int p = 0; p < kMeanPhaseSums; ++p) sp[p][c] = 0.0;
-    }
     for (long long i = (long long)q * blockDim.x + threadIdx.x; i < g.m; i += (long long)blocks_per_load * blockDim.x) {
       if (!FH_IN(CK_MEAN, (long long)Ebase + (long long)(nv - 1) * g.m + i, (long long)ctl->nload * nv * g.m)) continue;
       const int ph = phase[i];
 #pragma unroll
-      for (int p = 1; p < kMeanPhaseSums; ++p) cnt[p] += (ph == p);
-      cnt[0] += 1;
+      for (int p = 0; p < kMeanPhaseSums; ++p) cnt[p] += (ph == p);
 #pragma unroll
       for (int c = 0; c < MAXV; ++c) {
         if (c >= nv) break;
         const double e = (double)E[Ebase + (size_t)c * g.m + i];
-        tot[c] += e;
         // the phase selects the addend, not the addition (FP64 additions are
         // the scarce resource here: one per phase and component)
 #pragma unroll
-        for (int p = 1; p < kMeanPhaseSums; ++p)
+        for (int p = 0; p < kMeanPhaseSums; ++p)
           if (p < nphase) sp[p][c] += (ph == p) ? e : 0.0;
       }
     }
     // block sums; thread 0 forms sum_p C_p : (sum over phase p of E + n_p eps0)
     double n[kMeanPhaseSums], S[kMeanPhaseSums][MAXV];
-    for (int p = 0; p < nphase; ++p) n[p] = block_sum((double)cnt[p], red);
-    for (int c = 0; c < nv; ++c) {
-      const double t = block_sum(tot[c], red);
-      double rest = 0.0;
-      for (int p = 1; p < nphase; ++p) {
-        S[p][c] = block_sum(sp[p][c], red);
-        rest += S[p][c];
-      }
-      S[0][c] = t - rest;
+    for (int p = 0; p < nphase; ++p) {
+      n[p] = block_sum((double)cnt[p], red);
+      for (int c = 0; c < nv; ++c) S[p][c] = block_sum(sp[p][c], red);
     }
     if (threadIdx.x == 0) {
-      double n0 = n[0];
-      for (int p = 1; p < nphase; ++p) n0 -= n[p];
-      n[0] = n0;
-      for (int p = 0; p < nphase; ++p)
-        for (int c = 0; c < nv; ++c) {
-          const double sc = S[p][c] + n[p] * e0[c];
-          for (int a = 0; a < nv; ++a) acc[a] += Cp[((size_t)p * nv + a) * nv + c] * sc;
+      for (int p = 0; p < nphase; ++p) {
+        double v[MAXV];
+        for (int a = 0; a < nv; ++a) {
+          double t = 0.0;
+          for (int c = 0; c < nv; ++c) t += Cp[((size_t)p * nv + a) * nv + c] * (S[p][c] + n[p] * e0[c]);
+          v[a] = t;
         }
+        for (int a = 0; a < nv; ++a) acc[a] += v[a];
+      }
     }
   } else
   for (long long i = (long long)q * blockDim.x + threadIdx.x; i < g.m; i += (long long)blocks_per_load * blockDim.x) {

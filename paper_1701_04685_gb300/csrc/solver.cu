@@ -355,31 +355,41 @@ void launch_col_pass_mode(fh_solver* s, int a, int mode, int nload) {
   else launch_col_pass<P, 2>(s, a, nload);
 }
 
-// The two-step column pass (colpass2.cuh) applies to the warp-pass axes of 32,
-// 64 or 128 points: returns N there, else 0.
+// The two-step column pass (colpass2.cuh) applies to the axes of 32, 64 or
+// 128 points of 3-D fields (either precision): returns N there, else 0.
 int col2_len(const fh_solver* s, int prec, int a) {
-  if (!s->col2s || col_warp_p(s, prec, a) == 0) return 0;
+  (void)prec;
+  if (!s->col2s || s->g.nv != 6) return 0;
   const int N = s->g.dims[a];
   return (N == 32 || N == 64 || N == 128) ? N : 0;
 }
 
-template <int R1, int R2, int MODE>
+// columns per block and resident blocks per SM of the two-step column pass:
+// 8 in FP32, 4 in FP64 (whose tile of 8 would leave one block per SM)
+template <typename T>
+constexpr int col2_ct() { return sizeof(T) == 4 ? fh::kColTile : 4; }
+template <typename T, int MODE>
+constexpr int col2_mb() { return sizeof(T) == 4 ? fh::col2_minb<MODE>() : 3; }
+
+template <typename T, int R1, int R2, int MODE>
 void launch_col2(fh_solver* s, int a, int nload) {
+  using C = typename fh::cplx_t<T>::type;
+  constexpr int CT = col2_ct<T>();
   const GridInfo& g = s->g;
   long long stride = g.H;
   for (int k = a + 1; k + 1 < g.nd; ++k) stride *= g.dims[k];
   const long long ncols = g.nhalf / g.dims[a];
-  const long long tiles = (ncols + fh::kColTile - 1) / fh::kColTile;
-  fh::line_pass_2s<R1, R2, MODE><<<(unsigned)(tiles * nload), fh::Col2<R1, R2>::THREADS, fh::col2_smem<R1, R2>(),
-                                   s->work>>>(g, s->ax[a].tw32, reinterpret_cast<float2*>(s->S), s->G32, s->st,
-                                              stride, ncols, nload);
+  const long long tiles = (ncols + CT - 1) / CT;
+  fh::line_pass_2s<R1, R2, MODE, CT, col2_mb<T, MODE>(), T>
+      <<<(unsigned)(tiles * nload), fh::Col2<R1, R2, CT, T>::THREADS, fh::col2_smem<R1, R2, CT, T>(), s->work>>>(
+          g, twp<T>(s->ax[a]), reinterpret_cast<C*>(s->S), Gptr<T>(s), s->st, stride, ncols, nload);
 }
 
-template <int R1, int R2>
+template <typename T, int R1, int R2>
 void launch_col2_mode(fh_solver* s, int a, int mode, int nload) {
-  if (mode == 0) launch_col2<R1, R2, 0>(s, a, nload);
-  else if (mode == 1) launch_col2<R1, R2, 1>(s, a, nload);
-  else launch_col2<R1, R2, 2>(s, a, nload);
+  if (mode == 0) launch_col2<T, R1, R2, 0>(s, a, nload);
+  else if (mode == 1) launch_col2<T, R1, R2, 1>(s, a, nload);
+  else launch_col2<T, R1, R2, 2>(s, a, nload);
 }
 
 // line pass along axis a in the given mode (0 forward, 1 inverse, 2 forward +
@@ -387,13 +397,13 @@ void launch_col2_mode(fh_solver* s, int a, int mode, int nload) {
 template <typename T>
 void launch_axis(fh_solver* s, int prec, int a, int mode, int nload) {
   const GridInfo& g = s->g;
+  switch (col2_len(s, prec, a)) {
+    case 32: launch_col2_mode<T, 4, 8>(s, a, mode, nload); return;
+    case 64: launch_col2_mode<T, 8, 8>(s, a, mode, nload); return;
+    case 128: launch_col2_mode<T, 8, 16>(s, a, mode, nload); return;
+    default: break;
+  }
   if constexpr (sizeof(T) == 4) {
-    switch (col2_len(s, prec, a)) {
-      case 32: launch_col2_mode<4, 8>(s, a, mode, nload); return;
-      case 64: launch_col2_mode<8, 8>(s, a, mode, nload); return;
-      case 128: launch_col2_mode<8, 16>(s, a, mode, nload); return;
-      default: break;
-    }
     switch (col_warp_p(s, prec, a)) {
       case 1: launch_col_pass_mode<1>(s, a, mode, nload); return;
       case 2: launch_col_pass_mode<2>(s, a, mode, nload); return;
@@ -581,12 +591,18 @@ cudaError_t set_col_attrs() {
   return e;
 }
 
-template <int R1, int R2>
+template <typename T, int R1, int R2>
 cudaError_t set_col2_attrs() {
-  const int sm = (int)fh::col2_smem<R1, R2>();
-  cudaError_t e = cudaFuncSetAttribute(fh::line_pass_2s<R1, R2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(fh::line_pass_2s<R1, R2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(fh::line_pass_2s<R1, R2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  constexpr int CT = col2_ct<T>();
+  const int sm = (int)fh::col2_smem<R1, R2, CT, T>();
+  cudaError_t e = cudaFuncSetAttribute(fh::line_pass_2s<R1, R2, 0, CT, col2_mb<T, 0>(), T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fh::line_pass_2s<R1, R2, 1, CT, col2_mb<T, 1>(), T>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fh::line_pass_2s<R1, R2, 2, CT, col2_mb<T, 2>(), T>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   return e;
 }
 
@@ -664,13 +680,13 @@ fh_status set_smem_attrs_nv(fh_solver* s, int prec) {
   }
   size_t lm = 0;
   for (int a = 0; a + 1 < s->g.nd; ++a) {
+    switch (col2_len(s, prec, a)) {
+      case 32: CK((set_col2_attrs<T, 4, 8>())); continue;
+      case 64: CK((set_col2_attrs<T, 8, 8>())); continue;
+      case 128: CK((set_col2_attrs<T, 8, 16>())); continue;
+      default: break;
+    }
     if constexpr (sizeof(T) == 4) {
-      switch (col2_len(s, prec, a)) {
-        case 32: CK((set_col2_attrs<4, 8>())); continue;
-        case 64: CK((set_col2_attrs<8, 8>())); continue;
-        case 128: CK((set_col2_attrs<8, 16>())); continue;
-        default: break;
-      }
       switch (col_warp_p(s, prec, a)) {
         case 1: CK((set_col_attrs<1>())); continue;
         case 2: CK((set_col_attrs<2>())); continue;
