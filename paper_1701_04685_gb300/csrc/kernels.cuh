@@ -106,8 +106,36 @@ struct Control {
   int stall_window;  // > 0: stop a load whose residual has not improved by 1% for this many iterations
   int form;          // 0: Eq. (pde_coefficients), E <- -Gamma^p (C - C0)(E + eps0)
                      // 1: Eq. (pde_coefficients_variational), E <- E - Gamma^p C (E + eps0)
-  int pad2;
+  int decoupled;     // 3-D phase tables with zero normal-shear blocks and a diagonal shear
+                     // block (isotropic, cubic, orthotropic phases in the grid axes): the
+                     // constitutive stage skips the structural zeros (stress6_decoupled)
 };
+
+// tau = D x for a 6 x 6 Mandel matrix D whose normal-shear blocks are zero and
+// whose shear block is diagonal, from its 12 nonzero entries
+//   d = (D00, D01, D02, D10, D11, D12, D20, D21, D22, D33, D44, D55).
+// The products are summed in the order of the full row-by-row product and the
+// skipped terms are exact zeros, so the result has the value of the full
+// 36-term product (12 FMAs instead of 36).
+template <typename T>
+__device__ __forceinline__ void stress6_decoupled(const T* d, const T* x, T* tau) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    T t = T(0);
+    t = fma(d[3 * a], x[0], t);
+    t = fma(d[3 * a + 1], x[1], t);
+    t = fma(d[3 * a + 2], x[2], t);
+    tau[a] = t;
+  }
+#pragma unroll
+  for (int a = 3; a < 6; ++a) tau[a] = fma(d[6 + a], x[a], T(0));
+}
+
+// the 12 entries stress6_decoupled reads, from a 6 x 6 row-major matrix
+template <typename T>
+__device__ __forceinline__ T decoupled_entry(const T* D, int q) {
+  return q < 9 ? D[(q / 3) * 6 + q % 3] : D[(q - 6) * 7];
+}
 
 // ---------------------------------------------------------------------------
 // block reductions (fixed order -> deterministic)
@@ -1081,6 +1109,10 @@ __device__ __forceinline__ int moment_index3(int e1, int e2) {
   return T[e1][e2];
 }
 
+// Gamma^p entries of one storage frequency f (coordinates l0, l1, l2 when
+// mirroring) from its moments Bm, written to f and, when mirroring, to its
+// mirror images.
+//
 // mirror: M diagonal and the Smith grid's axes are M's axes (Fmap a signed
 // permutation, mirror_geo[k] = the geometric axis of storage axis k).  The
 // symbols are even per axis and the alias sets mirror with u_i -> -u_i, so
@@ -1089,13 +1121,119 @@ __device__ __forceinline__ int moment_index3(int e1, int e2) {
 // storage frequencies with l_k <= dims_k / 2 on the full (non-half) axes and
 // write every mirror image: 1/2 (2-D) or 1/4 (3-D) of the alias sums.
 template <int DIM>
+__device__ void iso_emit(const GreenParams& P, const double* Bm, long long f, long long l0, long long l1, long long l2,
+                         int mirror, int mirror_geo0, int mirror_geo1, double* __restrict__ G64,
+                         float* __restrict__ G32) {
+  auto moment = [&](int i, int j, int p, int q) -> double {
+    int e[3] = {0, 0, 0};
+    ++e[i]; ++e[j]; ++e[p]; ++e[q];
+    if (DIM == 2) return Bm[e[1]];
+    return Bm[moment_index3(e[1], e[2])];
+  };
+  // second moment A_ij = sum_p B_ijpp
+  double A[3][3];
+  for (int i = 0; i < DIM; ++i)
+    for (int j = 0; j < DIM; ++j) {
+      double s = 0.0;
+      for (int p = 0; p < DIM; ++p) s += moment(i, j, p, p);
+      A[i][j] = s;
+    }
+  const double c4 = 0.25 / P.mu0;
+  const double cb = (P.lam0 + P.mu0) / (P.mu0 * (P.lam0 + 2.0 * P.mu0));
+  const double s2 = 1.41421356237309504880;
+  // mirror images (s0, s1) of the storage frequency; (0, 0) is f itself
+  long long fm[4];
+  fm[0] = f;
+  fm[1] = fm[2] = fm[3] = -1;
+  if (mirror) {
+    const long long m0 = (P.dims[0] - l0) % P.dims[0];
+    const long long m1 = DIM == 3 ? (P.dims[1] - l1) % P.dims[1] : 0;
+    const bool d0 = m0 != l0, d1 = DIM == 3 && m1 != l1;
+    if (DIM == 3) {
+      if (d0) fm[1] = (m0 * P.dims[1] + l1) * P.H + l2;
+      if (d1) fm[2] = (l0 * P.dims[1] + m1) * P.H + l2;
+      if (d0 && d1) fm[3] = (m0 * P.dims[1] + m1) * P.H + l2;
+    } else if (d0) {
+      fm[1] = m0 * P.H + l2;
+    }
+  }
+  int t = 0;
+  for (int a = 0; a < P.nv; ++a) {
+    int i, j;
+    mandel_pair(DIM, a, i, j);
+    const double sa = (i == j) ? 1.0 : s2;
+    for (int b = a; b < P.nv; ++b) {
+      int p, q;
+      mandel_pair(DIM, b, p, q);
+      const double sb = (p == q) ? 1.0 : s2;
+      const double lin = (i == p ? A[j][q] : 0.0) + (i == q ? A[j][p] : 0.0) + (j == p ? A[i][q] : 0.0) +
+                         (j == q ? A[i][p] : 0.0);
+      const double v = sa * sb * (c4 * lin - cb * moment(i, j, p, q));
+      const int c0 = (i == mirror_geo0) + (j == mirror_geo0) + (p == mirror_geo0) + (q == mirror_geo0);
+      const int c1 = (i == mirror_geo1) + (j == mirror_geo1) + (p == mirror_geo1) + (q == mirror_geo1);
+      for (int r = 0; r < 4; ++r) {
+        if (fm[r] < 0) continue;
+        const int flips = ((r & 1) ? c0 : 0) + ((r & 2) ? c1 : 0);
+        const double vr = (flips & 1) ? -v : v;
+        if (!FH_IN(CK_TABLE, (long long)t * P.nhalf + fm[r], (long long)P.ntri * P.nhalf)) continue;
+        G64[(size_t)t * P.nhalf + fm[r]] = vr;
+        G32[(size_t)t * P.nhalf + fm[r]] = (float)vr;
+      }
+      ++t;
+    }
+  }
+}
+
+// exponents (e1, e2) of moment t in the accumulation order of green_table_iso<3>
+// (inverse of moment_index3; e0 = 4 - e1 - e2)
+__device__ __forceinline__ void moment_exponents3(int t, int& e1, int& e2) {
+  const signed char E1[15] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 4, 3, 2, 0, 1, 0};
+  const signed char E2[15] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 0, 1, 2, 3, 3, 4};
+  e1 = E1[t];
+  e2 = E2[t];
+}
+
+// cubic: in addition to the mirror conditions, the three storage axes have the
+// same length N, |M_00| = |M_11| = |M_22| and the per-axis symbols are the same
+// function (Dirichlet, dlVP with equal ramps, a box spline with the same count
+// of each e_i).  Permuting the geometric axes then maps the alias set and the
+// weights onto themselves, so the moments at a permuted frequency are the
+// moments at the original one with their exponents permuted:
+//   sum_z w_z n'^e = sum_z w_z prod_g n_{pi(g)}^{e_g}   when |h'_g| = |h_{pi(g)}|.
+// Threads take the storage frequencies with N/2 >= l0 >= l1 >= l2 >= 0 (thread
+// index -> the triple by tetrahedral numbers), sum the aliases once, and write
+// every distinct permutation of (l0, l1, l2) with its mirror images: 1/6 of the
+// alias sums of the mirror path.  Signs go through |h|: the moments at the
+// reduced frequency h carry prod_g sign(h_g)^(e_g) relative to those at |h|
+// (the alias sets of the reduced u are symmetric).
+__device__ __forceinline__ long long tet3(long long a) { return a * (a + 1) * (a + 2) / 6; }
+
+__device__ __forceinline__ void cubic_triple(long long idx, long long& L0, long long& L1, long long& L2) {
+  long long a = (long long)cbrt(6.0 * (double)idx);
+  while (tet3(a + 1) <= idx) ++a;
+  while (a > 0 && tet3(a) > idx) --a;
+  const long long r = idx - tet3(a);
+  long long b = (long long)((sqrt(8.0 * (double)r + 1.0) - 1.0) * 0.5);
+  while ((b + 1) * (b + 2) / 2 <= r) ++b;
+  while (b > 0 && b * (b + 1) / 2 > r) --b;
+  L0 = a;
+  L1 = b;
+  L2 = r - b * (b + 1) / 2;
+}
+
+template <int DIM>
 __global__ void __launch_bounds__(128) green_table_iso(GreenParams P, double* __restrict__ G64,
                                                        float* __restrict__ G32, int* err, int mirror,
-                                                       int mirror_geo0, int mirror_geo1) {
+                                                       int mirror_geo0, int mirror_geo1, int cubic) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long f = idx;
   long long l0 = 0, l1 = 0, l2 = 0;  // storage coordinates when mirroring
-  if (mirror) {
+  if (DIM == 3 && cubic) {
+    const long long n = P.dims[0] / 2 + 1;
+    if (idx >= tet3(n)) return;
+    cubic_triple(idx, l0, l1, l2);
+    f = (l0 * P.dims[1] + l1) * P.H + l2;
+  } else if (mirror) {
     const long long n0 = P.dims[0] / 2 + 1, n1 = DIM == 3 ? P.dims[1] / 2 + 1 : 1;
     if (idx >= n0 * n1 * P.H) return;
     l2 = idx % P.H;
@@ -1199,67 +1337,64 @@ __global__ void __launch_bounds__(128) green_table_iso(GreenParams P, double* __
       }
     }
   }
-  // fourth moment B_ijpq by exponents, second moment A_ij = sum_p B_ijpp (a copy
-  // is indexed at run time, so that B itself stays in registers in the loops)
+  // fourth moment B_ijpq by exponents (a copy is indexed at run time, so that
+  // B itself stays in registers in the loops)
   double Bm[NB];
 #pragma unroll
   for (int t = 0; t < NB; ++t) Bm[t] = B[t];
-  auto moment = [&](int i, int j, int p, int q) -> double {
-    int e[3] = {0, 0, 0};
-    ++e[i]; ++e[j]; ++e[p]; ++e[q];
-    if (DIM == 2) return Bm[e[1]];
-    return Bm[moment_index3(e[1], e[2])];
-  };
-  double A[3][3];
-  for (int i = 0; i < DIM; ++i)
-    for (int j = 0; j < DIM; ++j) {
-      double s = 0.0;
-      for (int p = 0; p < DIM; ++p) s += moment(i, j, p, p);
-      A[i][j] = s;
-    }
-  const double c4 = 0.25 / P.mu0;
-  const double cb = (P.lam0 + P.mu0) / (P.mu0 * (P.lam0 + 2.0 * P.mu0));
-  const double s2 = 1.41421356237309504880;
-  // mirror images (s0, s1) of the storage frequency; (0, 0) is f itself
-  long long fm[4];
-  fm[0] = f;
-  fm[1] = fm[2] = fm[3] = -1;
-  if (mirror) {
-    const long long m0 = (P.dims[0] - l0) % P.dims[0];
-    const long long m1 = DIM == 3 ? (P.dims[1] - l1) % P.dims[1] : 0;
-    const bool d0 = m0 != l0, d1 = DIM == 3 && m1 != l1;
-    if (DIM == 3) {
-      if (d0) fm[1] = (m0 * P.dims[1] + l1) * P.H + l2;
-      if (d1) fm[2] = (l0 * P.dims[1] + m1) * P.H + l2;
-      if (d0 && d1) fm[3] = (m0 * P.dims[1] + m1) * P.H + l2;
-    } else if (d0) {
-      fm[1] = m0 * P.H + l2;
-    }
+  if constexpr (DIM == 2) {
+    iso_emit<DIM>(P, Bm, f, l0, l1, l2, mirror, mirror_geo0, mirror_geo1, G64, G32);
+  } else {
+  if (!cubic) {
+    iso_emit<DIM>(P, Bm, f, l0, l1, l2, mirror, mirror_geo0, mirror_geo1, G64, G32);
+    return;
   }
-  int t = 0;
-  for (int a = 0; a < P.nv; ++a) {
-    int i, j;
-    mandel_pair(DIM, a, i, j);
-    const double sa = (i == j) ? 1.0 : s2;
-    for (int b = a; b < P.nv; ++b) {
-      int p, q;
-      mandel_pair(DIM, b, p, q);
-      const double sb = (p == q) ? 1.0 : s2;
-      const double lin = (i == p ? A[j][q] : 0.0) + (i == q ? A[j][p] : 0.0) + (j == p ? A[i][q] : 0.0) +
-                         (j == q ? A[i][p] : 0.0);
-      const double v = sa * sb * (c4 * lin - cb * moment(i, j, p, q));
-      const int c0 = (i == mirror_geo0) + (j == mirror_geo0) + (p == mirror_geo0) + (q == mirror_geo0);
-      const int c1 = (i == mirror_geo1) + (j == mirror_geo1) + (p == mirror_geo1) + (q == mirror_geo1);
-      for (int r = 0; r < 4; ++r) {
-        if (fm[r] < 0) continue;
-        const int flips = ((r & 1) ? c0 : 0) + ((r & 2) ? c1 : 0);
-        const double vr = (flips & 1) ? -v : v;
-        if (!FH_IN(CK_TABLE, (long long)t * P.nhalf + fm[r], (long long)P.ntri * P.nhalf)) continue;
-        G64[(size_t)t * P.nhalf + fm[r]] = vr;
-        G32[(size_t)t * P.nhalf + fm[r]] = (float)vr;
+  // every distinct permutation (l0', l1', l2') of the storage triple
+  const long long L[3] = {l0, l1, l2};
+  const signed char PERM[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  long long seen[6][3];
+  int nseen = 0;
+  for (int pi = 0; pi < 6; ++pi) {
+    const long long lp[3] = {L[PERM[pi][0]], L[PERM[pi][1]], L[PERM[pi][2]]};
+    bool dup = false;
+    for (int q = 0; q < nseen; ++q)
+      dup = dup || (seen[q][0] == lp[0] && seen[q][1] == lp[1] && seen[q][2] == lp[2]);
+    if (dup) continue;
+    seen[nseen][0] = lp[0];
+    seen[nseen][1] = lp[1];
+    seen[nseen][2] = lp[2];
+    ++nseen;
+    const long long fp = (lp[0] * P.dims[1] + lp[1]) * P.H + lp[2];
+    long long hp[3], up[3];
+    reduce_frequency(P, fp, hp, up);
+    // geometric axis map: |h'_g| = |h_{ax[g]}|
+    int ax[3] = {-1, -1, -1};
+    bool used[3] = {false, false, false};
+    for (int g = 0; g < 3; ++g) {
+      const long long want = hp[g] < 0 ? -hp[g] : hp[g];
+      for (int g2 = 0; g2 < 3 && ax[g] < 0; ++g2) {
+        const long long have = h[g2] < 0 ? -h[g2] : h[g2];
+        if (!used[g2] && have == want) { ax[g] = g2; used[g2] = true; }
       }
-      ++t;
     }
+    if (ax[0] < 0 || ax[1] < 0 || ax[2] < 0) {  // cannot happen when the cubic conditions hold
+      atomicExch(err, (int)FH_ERR_INTERNAL);
+      return;
+    }
+    double Bp[NB];
+    for (int t = 0; t < NB; ++t) {
+      int e[3];
+      moment_exponents3(t, e[1], e[2]);
+      e[0] = 4 - e[1] - e[2];
+      int src[3] = {0, 0, 0};
+      for (int g = 0; g < 3; ++g) src[ax[g]] = e[g];
+      int par = 0;
+      for (int g = 0; g < 3; ++g) par += (h[g] < 0 ? src[g] : 0) + (hp[g] < 0 ? e[g] : 0);
+      const double v = Bm[moment_index3(src[1], src[2])];
+      Bp[t] = (par & 1) ? -v : v;
+    }
+    iso_emit<DIM>(P, Bp, fp, lp[0], lp[1], lp[2], mirror, mirror_geo0, mirror_geo1, G64, G32);
+  }
   }
 }
 

@@ -68,14 +68,19 @@ __global__ void __launch_bounds__(Row2<R1, R2>::THREADS, sizeof(T) == 4 ? 3 : 1)
   C* tw = reinterpret_cast<C*>(smem_raw);   // tw[t] = exp(-2 pi i t / L)
   C* buf = tw + L;                          // [LINES][LS]: line 3 r + p = row r, components 2p, 2p + 1
   __shared__ __align__(16) T dcs[16 * NV * NV];
+  __shared__ __align__(16) T dcp[16 * 12];   // the 12 nonzeros of decoupled phase matrices
   __shared__ double red[32];
   __shared__ int s_skip;
+  const bool decoupled = ctl->decoupled != 0;
   const int load = blockIdx.x / blocks_per_load;
   const int qb = blockIdx.x - load * blocks_per_load;
   const long long row0 = (long long)qb * RB;
   for (int i = threadIdx.x; i < L; i += NT) tw[i] = twg[i];
-  if (!KINV)
+  if (!KINV) {
     for (int i = threadIdx.x; i < 16 * NV * NV; i += NT) dcs[i] = dC[i];
+    if (decoupled)
+      for (int i = threadIdx.x; i < 16 * 12; i += NT) dcp[i] = decoupled_entry(dC + (i / 12) * NV * NV, i % 12);
+  }
   if (threadIdx.x == 0) s_skip = st[load].done;
   __syncthreads();
   ResAcc<T> acc_d, acc_n;
@@ -213,6 +218,19 @@ __global__ void __launch_bounds__(Row2<R1, R2>::THREADS, sizeof(T) == 4 ? 3 : 1)
       }
       int ph = phase[pt];
       if (!FH_IN(CK_ROW_PHASE, ph, 16)) ph = 0;
+      if (decoupled) {
+        T xv[NV], tau[NV];
+#pragma unroll
+        for (int b = 0; b < NV; ++b) xv[b] = en[b] + e0[b];
+        stress6_decoupled<T>(dcp + ph * 12, xv, tau);
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+          C z;
+          z.x = tau[2 * p];
+          z.y = tau[2 * p + 1];
+          ln[p * LS] = z;
+        }
+      } else {
       const T* dc = dcs + ph * NV * NV;
 #pragma unroll
       for (int p = 0; p < 3; ++p) {
@@ -226,6 +244,7 @@ __global__ void __launch_bounds__(Row2<R1, R2>::THREADS, sizeof(T) == 4 ? 3 : 1)
         z.x = t0;
         z.y = t1;
         ln[p * LS] = z;
+      }
       }
     }
 

@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -98,6 +99,7 @@ struct fh_solver {
   float* dC32 = nullptr;
   float* Cp32 = nullptr;
   int form = 0;  // iteration form of the solve in progress (0 or 1)
+  bool dc_decoupled = false;  // 3-D phase matrices and C0 with zero normal-shear blocks, diagonal shear block
   // autotuned (path, cluster size) per bulk precision [fp64, fp32]; path 0 = not tuned yet
   int tuned_path[2] = {0, 0};
   int tuned_cs[2] = {0, 0};
@@ -1195,6 +1197,33 @@ bool mirror_axes(const fh_solver* s, int* geo) {
   return true;
 }
 
+// A 6 x 6 Mandel matrix whose normal-shear blocks are zero and whose shear
+// block is diagonal (isotropic, cubic or orthotropic in the grid axes)
+bool decoupled6(const double* c) {
+  for (int a = 0; a < 6; ++a)
+    for (int b = 0; b < 6; ++b) {
+      const bool structural_zero = ((a < 3) != (b < 3)) || (a >= 3 && b >= 3 && a != b);
+      if (structural_zero && c[a * 6 + b] != 0.0) return false;
+    }
+  return true;
+}
+
+// Cubic symmetry of the table (green_table_iso<3>): on top of the mirror
+// conditions, three storage axes of one length, |M_00| = |M_11| = |M_22|, and
+// the same per-axis symbol on every axis (Dirichlet; dlVP with equal ramps; a
+// box spline with the same count of each direction).  Then permuting the
+// geometric axes maps the alias set and its weights onto themselves.
+bool cubic_axes(const fh_solver* s, const fh::GreenParams& GP) {
+  if (s->g.d != 3 || s->g.nd != 3) return false;
+  if (s->g.dims[0] != s->g.dims[1] || s->g.dims[1] != s->g.dims[2]) return false;
+  const long long a0 = std::llabs(s->P.M[0][0]);
+  if (std::llabs(s->P.M[1][1]) != a0 || std::llabs(s->P.M[2][2]) != a0) return false;
+  if (s->gen.kind == FH_GEN_DLVP)
+    return s->gen.alpha[0] == s->gen.alpha[1] && s->gen.alpha[1] == s->gen.alpha[2];
+  if (s->gen.kind == FH_GEN_BOXSPLINE) return GP.xcount[0] == GP.xcount[1] && GP.xcount[1] == GP.xcount[2];
+  return true;
+}
+
 void mandel_to_c4(const double* Cm, int d, double* C4) {
   const int I2[3] = {0, 1, 0}, J2[3] = {0, 1, 1};
   const int I3[6] = {0, 1, 2, 1, 0, 0}, J3[6] = {0, 1, 2, 2, 2, 1};
@@ -1726,17 +1755,29 @@ static fh_status fh_set_reference_impl(fh_solver* s, const double* C0) {
   if (closed_form_table(s, c0, &GP)) {
     int geo[2] = {-1, -1};
     const bool mirror = mirror_axes(s, geo);
+    const bool cubic = mirror && cubic_axes(s, GP);
     long long nthreads = s->g.nhalf;
     if (mirror) nthreads = (long long)(s->g.dims[0] / 2 + 1) * (d == 3 ? s->g.dims[1] / 2 + 1 : 1) * s->g.H;
-    const int mblocks = (int)((nthreads + 127) / 128);
+    if (cubic) {   // storage triples N/2 >= l0 >= l1 >= l2 >= 0
+      const long long n = s->g.dims[0] / 2 + 1;
+      nthreads = n * (n + 1) * (n + 2) / 6;
+    }
+    // 64-thread blocks: the cubic grid is small (47 905 threads at 128^3)
+    const int tpb = cubic ? 64 : 128;
+    const int mblocks = (int)((nthreads + tpb - 1) / tpb);
     if (d == 2)
-      fh::green_table_iso<2><<<mblocks, 128, 0, s->work>>>(GP, s->G64, s->G32, s->err, mirror, geo[0], geo[1]);
+      fh::green_table_iso<2><<<mblocks, tpb, 0, s->work>>>(GP, s->G64, s->G32, s->err, mirror, geo[0], geo[1], 0);
     else
-      fh::green_table_iso<3><<<mblocks, 128, 0, s->work>>>(GP, s->G64, s->G32, s->err, mirror, geo[0], geo[1]);
+      fh::green_table_iso<3><<<mblocks, tpb, 0, s->work>>>(GP, s->G64, s->G32, s->err, mirror, geo[0], geo[1],
+                                                           cubic ? 1 : 0);
   } else {
     fh::green_table<<<blocks, 128, 0, s->work>>>(GP, s->G64, s->G32, s->err);
   }
   CK(cudaGetLastError());
+  // the constitutive stage of the 3-D row passes skips structural zeros when
+  // every phase matrix and C0 have them (then C_p - C0 has them too)
+  s->dc_decoupled = nv == 6 && !s->field && decoupled6(c0);
+  for (int q = 0; q < s->nphase && s->dc_decoupled; ++q) s->dc_decoupled = decoupled6(s->Cp + q * 36);
   // stiffness differences C_p - C0
   double dc[kMaxPhases * 36];
   float dcf[kMaxPhases * 36];
@@ -1797,6 +1838,7 @@ fh_status begin_phase(fh_solver* s, int nload, const double* eps0, double tol, i
   Control h{};
   h.stall_window = stall_window;
   h.form = s->form;
+  h.decoupled = s->dc_decoupled ? 1 : 0;
   for (int l = 0; l < nload; ++l)
     for (int c = 0; c < nv; ++c) h.eps0[l][c] = eps0[l * nv + c];
   h.tol = tol;

@@ -510,13 +510,17 @@ __global__ void __launch_bounds__(kWarpRowThreads, (P <= 4 ? 2 : 1)) row_pass_wa
   cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);          // L
   cplx<T>* scratch = tw + L;                                    // NW * WS
   __shared__ __align__(16) T dcs[16 * NV * NV];
+  __shared__ __align__(16) T dcp[16 * 12];   // the 12 nonzeros of decoupled phase matrices
   __shared__ double red[32];
   __shared__ int s_skip;
   const int load = blockIdx.x / blocks_per_load;
   const int qb = blockIdx.x - load * blocks_per_load;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool decoupled = ctl->decoupled != 0;
   for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = twg[i];
   for (int i = threadIdx.x; i < 16 * NV * NV; i += blockDim.x) dcs[i] = dC[i];
+  if (decoupled)
+    for (int i = threadIdx.x; i < 16 * 12; i += blockDim.x) dcp[i] = decoupled_entry(dC + (i / 12) * NV * NV, i % 12);
   if (threadIdx.x == 0) s_skip = st[load].done;
   __syncthreads();
   ResAcc<T> acc_d, acc_n;
@@ -626,6 +630,18 @@ __global__ void __launch_bounds__(kWarpRowThreads, (P <= 4 ? 2 : 1)) row_pass_wa
             Er[c * cstrE + x] = en[c];
           }
         }
+        if (decoupled) {
+          T dc[12], xv[NV], tau[NV];
+          load_rows<T>(dcp + ph[j] * 12, dc);
+#pragma unroll
+          for (int b = 0; b < NV; ++b) xv[b] = en[b] + e0[b];
+          stress6_decoupled<T>(dc, xv, tau);
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            z[a][j].x = tau[2 * a];
+            z[a][j].y = tau[2 * a + 1];
+          }
+        } else {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           T dc[12];
@@ -638,6 +654,7 @@ __global__ void __launch_bounds__(kWarpRowThreads, (P <= 4 ? 2 : 1)) row_pass_wa
           }
           z[a][j].x = t0;
           z[a][j].y = t1;
+        }
         }
       }
       if (!FIRST) {

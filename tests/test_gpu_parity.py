@@ -309,6 +309,40 @@ def test_benchmark_workload_ceff_accuracy(fh, prec, bound):
     assert err < bound
 
 
+@pytest.fixture(scope="module")
+def converged_dlvp_sheared():
+    """The oracle's fixed point on the benchmark workload, iterated to r <= 1e-11."""
+    case = Case.from_workload(W.dlvp_sheared())
+    return case, case.oracle_solve(tol=1e-11, max_iter=20000)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+def test_benchmark_workload_strain_accuracy(fh, converged_dlvp_sheared, prec):
+    """Strain fields at the benchmark tolerance (r <= 1e-6) against the converged FP64
+    oracle, per precision mode: ||E - E_conv|| / ||E_conv + eps0|| (Frobenius over P(M),
+    worst load).  Sec. 4 stops on the Cauchy residual, so the distance to the fixed
+    point is about r rho / (1 - rho) for the contraction rate rho of the iteration;
+    the bound takes rho from the last residuals of the solve itself, plus the FP32
+    rounding floor for the FP32 mode."""
+    P = {"fp64": fh.FH_PREC_FP64, "mixed": fh.FH_PREC_MIXED, "fp32": fh.FH_PREC_FP32}[prec]
+    oc, ref = converged_dlvp_sheared
+    case = Case.from_workload(W.dlvp_sheared())
+    s = case.product(fh)
+    out = s.solve(case.eps0, tol=1e-6, max_iter=20000, precision=P)
+    assert out["status"] == 0
+    worst, bound = 0.0, 0.0
+    for L in range(case.nload):
+        Eg = s.get_strain(L)
+        Eo = ref["E"][L][case.perm].T
+        err = np.linalg.norm(Eg - Eo) / np.linalg.norm(Eo + case.eps0[L][:, None])
+        h = s.get_residuals(L)
+        rho = min((h[-1] / h[-11]) ** 0.1, 0.999)
+        bound = max(bound, 2.0 * h[-1] * rho / (1.0 - rho) + (5e-6 if prec == "fp32" else 0.0))
+        worst = max(worst, err)
+    print(f"{prec}: strain relative error {worst:.3e} (bound {bound:.3e}), iterations {out['iterations']}")
+    assert worst < bound
+
+
 def test_mixed_mode_continues_the_iteration_count(fh):
     case = _case(CASES[0])
     s = case.product(fh)
