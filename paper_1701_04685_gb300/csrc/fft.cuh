@@ -33,6 +33,46 @@ template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
 }
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+// padd / psub: the same sums, in FP32 as one packed two-wide instruction
+// (sm_100 and later) instead of two, each part rounded as the scalar operation
+// would be (a - b as b * (-1) + a: one rounding of an exact product).  Used
+// where both operands are plain values; where an operand is a product (the
+// sqrt(1/2) rotations of the 8-point DFT) the scalar form lets the compiler
+// fuse the multiplication into the addition instead.
+template <typename C> __device__ __forceinline__ C padd(C a, C b) { return cadd(a, b); }
+template <typename C> __device__ __forceinline__ C psub(C a, C b) { return csub(a, b); }
+// a + s b and s a per part (scalar s)
+template <typename C> __device__ __forceinline__ C pfma(decltype(C::x) s, C b, C a) {
+  C r;
+  r.x = fma(s, b.x, a.x);
+  r.y = fma(s, b.y, a.y);
+  return r;
+}
+template <typename C> __device__ __forceinline__ C pscale(decltype(C::x) s, C a) {
+  C r;
+  r.x = s * a.x;
+  r.y = s * a.y;
+  return r;
+}
+template <> __device__ __forceinline__ float2 pfma<float2>(float s, float2 b, float2 a) {
+  return __ffma2_rn(make_float2(s, s), b, a);
+}
+template <> __device__ __forceinline__ float2 pscale<float2>(float s, float2 a) { return __fmul2_rn(make_float2(s, s), a); }
+template <> __device__ __forceinline__ float2 padd<float2>(float2 a, float2 b) { return __fadd2_rn(a, b); }
+template <> __device__ __forceinline__ float2 psub<float2>(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+// the packed or the plain form, chosen per caller: the packed form pays in the
+// register-resident warp FFTs of the row pass and measured slower in the
+// shared-memory column passes
+template <bool PK, typename C> __device__ __forceinline__ C kadd(C a, C b) {
+  if constexpr (PK) return padd(a, b);
+  else return cadd(a, b);
+}
+template <bool PK, typename C> __device__ __forceinline__ C ksub(C a, C b) {
+  if constexpr (PK) return psub(a, b);
+  else return csub(a, b);
+}
 // multiply by DIR * i   (DIR = -1: -i, DIR = +1: +i)
 template <int DIR, typename C> __device__ __forceinline__ C mul_i(C a) {
   C r;
@@ -50,30 +90,30 @@ struct DevPlan {
 constexpr int MAX_RADIX = 13;
 
 // Small DFTs in registers, X_k = sum_t v_t w^{kt}, w = exp(DIR 2 pi i / r).
-template <int DIR, typename T>
+template <int DIR, typename T, bool PK = false>
 __device__ __forceinline__ void dft2(cplx<T>* v) {
   cplx<T> a = v[0], b = v[1];
-  v[0] = cadd(a, b);
-  v[1] = csub(a, b);
+  v[0] = kadd<PK>(a, b);
+  v[1] = ksub<PK>(a, b);
 }
 
-template <int DIR, typename T>
+template <int DIR, typename T, bool PK = false>
 __device__ __forceinline__ void dft4(cplx<T>* v) {
-  cplx<T> t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-  cplx<T> t2 = cadd(v[1], v[3]), t3 = mul_i<DIR>(csub(v[1], v[3]));
-  v[0] = cadd(t0, t2);
-  v[2] = csub(t0, t2);
-  v[1] = cadd(t1, t3);
-  v[3] = csub(t1, t3);
+  cplx<T> t0 = kadd<PK>(v[0], v[2]), t1 = ksub<PK>(v[0], v[2]);
+  cplx<T> t2 = kadd<PK>(v[1], v[3]), t3 = mul_i<DIR>(ksub<PK>(v[1], v[3]));
+  v[0] = kadd<PK>(t0, t2);
+  v[2] = ksub<PK>(t0, t2);
+  v[1] = kadd<PK>(t1, t3);
+  v[3] = ksub<PK>(t1, t3);
 }
 
-template <int DIR, typename T>
+template <int DIR, typename T, bool PK = false>
 __device__ __forceinline__ void dft8(cplx<T>* v) {
   const T h = T(0.70710678118654752440084436210485);
   cplx<T> e[4] = {v[0], v[2], v[4], v[6]};
   cplx<T> o[4] = {v[1], v[3], v[5], v[7]};
-  dft4<DIR, T>(e);
-  dft4<DIR, T>(o);
+  dft4<DIR, T, PK>(e);
+  dft4<DIR, T, PK>(o);
   // w8^k with w8 = (1 + DIR i)/sqrt2
   cplx<T> o1, o2, o3;
   o1.x = h * (o[1].x - DIR * o[1].y);
@@ -81,9 +121,9 @@ __device__ __forceinline__ void dft8(cplx<T>* v) {
   o2 = mul_i<DIR>(o[2]);
   o3.x = h * (-o[3].x - DIR * o[3].y);
   o3.y = h * (-o[3].y + DIR * o[3].x);
-  v[0] = cadd(e[0], o[0]); v[4] = csub(e[0], o[0]);
+  v[0] = kadd<PK>(e[0], o[0]); v[4] = ksub<PK>(e[0], o[0]);
   v[1] = cadd(e[1], o1);   v[5] = csub(e[1], o1);
-  v[2] = cadd(e[2], o2);   v[6] = csub(e[2], o2);
+  v[2] = kadd<PK>(e[2], o2); v[6] = ksub<PK>(e[2], o2);
   v[3] = cadd(e[3], o3);   v[7] = csub(e[3], o3);
 }
 

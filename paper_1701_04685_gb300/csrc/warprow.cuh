@@ -71,11 +71,11 @@ __device__ __forceinline__ void dft16(cplx<T>* v) {
   }
 }
 
-template <int P, int DIR, typename T>
+template <int P, int DIR, typename T, bool PK = false>
 __device__ __forceinline__ void small_dft(cplx<T>* v) {
-  if (P == 2) dft2<DIR, T>(v);
-  else if (P == 4) dft4<DIR, T>(v);
-  else if (P == 8) dft8<DIR, T>(v);
+  if (P == 2) dft2<DIR, T, PK>(v);
+  else if (P == 4) dft4<DIR, T, PK>(v);
+  else if (P == 8) dft8<DIR, T, PK>(v);
   else if (P == 16) dft16<DIR, T>(v);
 }
 
@@ -173,12 +173,12 @@ __device__ __forceinline__ int pair_freq(int lane, int q, int P) {
   return 2 * (q >> 1) + (lane >> 4) + P * bitrev5(((lane & 15) << 1) | (q & 1));
 }
 
-template <int P, int NL, typename T>
+template <int P, int NL, typename T, bool PK = false>
 __device__ __forceinline__ void warp_fft_fwd_pairs(cplx<T> (&v)[NL][P], const cplx<T>* tw, int lane) {
   constexpr int L = 32 * P;
 #pragma unroll
   for (int n = 0; n < NL; ++n) {
-    small_dft<P, -1, T>(v[n]);
+    small_dft<P, -1, T, PK>(v[n]);
 #pragma unroll
     for (int q = 1; q < P; ++q) v[n][q] = cmul(v[n][q], twl<-1, T>(tw, lane * q));
   }
@@ -199,10 +199,12 @@ __device__ __forceinline__ void warp_fft_fwd_pairs(cplx<T> (&v)[NL][P], const cp
         const cplx<T> r0 = v[n][2 * j], r1 = v[n][2 * j + 1];
         const cplx<T> s = upper ? r1 : r0;
         const cplx<T> t = shfl_xor_c<T>(upper ? r0 : r1, h);
-        v[n][2 * j] = cadd(s, t);
-        const cplx<T> d = csub(s, t);
+        v[n][2 * j] = kadd<PK>(s, t);
+        const cplx<T> d = ksub<PK>(s, t);
         if (h > 1) {
           v[n][2 * j + 1] = cmul(d, w);
+        } else if (PK) {
+          v[n][2 * j + 1] = pscale(sgn, d);
         } else {
           v[n][2 * j + 1].x = sgn * d.x;
           v[n][2 * j + 1].y = sgn * d.y;
@@ -211,7 +213,7 @@ __device__ __forceinline__ void warp_fft_fwd_pairs(cplx<T> (&v)[NL][P], const cp
   }
 }
 
-template <int P, int NL, typename T>
+template <int P, int NL, typename T, bool PK = false>
 __device__ __forceinline__ void warp_fft_inv_pairs(cplx<T> (&v)[NL][P], const cplx<T>* tw, int lane) {
   constexpr int L = 32 * P;
 #pragma unroll
@@ -229,15 +231,22 @@ __device__ __forceinline__ void warp_fft_inv_pairs(cplx<T> (&v)[NL][P], const cp
 #pragma unroll
       for (int j = 0; j < P / 2; ++j) {
         const cplx<T> r0 = v[n][2 * j], r1 = v[n][2 * j + 1];
-        cplx<T> u;
+        cplx<T> s2, d2;
         if (h > 1) {
-          u = cmul(r1, w);
+          const cplx<T> u = cmul(r1, w);
+          s2 = kadd<PK>(r0, u);
+          d2 = ksub<PK>(r0, u);
+        } else if (PK) {   // r0 +- sgn r1, one rounding each as in the fused scalar form
+          s2 = pfma(sgn, r1, r0);
+          d2 = pfma(-sgn, r1, r0);
         } else {
+          cplx<T> u;
           u.x = sgn * r1.x;
           u.y = sgn * r1.y;
+          s2 = cadd(r0, u);
+          d2 = csub(r0, u);
         }
-        const cplx<T> s2 = cadd(r0, u);
-        const cplx<T> recv = shfl_xor_c<T>(csub(r0, u), h);
+        const cplx<T> recv = shfl_xor_c<T>(d2, h);
         v[n][2 * j] = upper ? recv : s2;
         v[n][2 * j + 1] = upper ? s2 : recv;
       }
@@ -246,7 +255,7 @@ __device__ __forceinline__ void warp_fft_inv_pairs(cplx<T> (&v)[NL][P], const cp
   for (int n = 0; n < NL; ++n) {
 #pragma unroll
     for (int q = 1; q < P; ++q) v[n][q] = cmul(v[n][q], twl<+1, T>(tw, lane * q));
-    small_dft<P, +1, T>(v[n]);
+    small_dft<P, +1, T, PK>(v[n]);
   }
 }
 
@@ -257,14 +266,15 @@ template <int P>
 __device__ __forceinline__ int warp_freq(int lane, int q) {
   return P >= 2 ? pair_freq(lane, q, P) : q + P * bitrev5(lane);
 }
-template <int P, int NL, typename T>
+// PK: packed two-wide FP32 additions (the row pass)
+template <int P, int NL, typename T, bool PK = false>
 __device__ __forceinline__ void warp_fft_fwd_any(cplx<T> (&v)[NL][P], const cplx<T>* tw, int lane) {
-  if constexpr (P >= 2) warp_fft_fwd_pairs<P, NL, T>(v, tw, lane);
+  if constexpr (P >= 2) warp_fft_fwd_pairs<P, NL, T, PK>(v, tw, lane);
   else warp_fft_fwd<P, NL, T>(v, tw, lane);
 }
-template <int P, int NL, typename T>
+template <int P, int NL, typename T, bool PK = false>
 __device__ __forceinline__ void warp_fft_inv_any(cplx<T> (&v)[NL][P], const cplx<T>* tw, int lane) {
-  if constexpr (P >= 2) warp_fft_inv_pairs<P, NL, T>(v, tw, lane);
+  if constexpr (P >= 2) warp_fft_inv_pairs<P, NL, T, PK>(v, tw, lane);
   else warp_fft_inv<P, NL, T>(v, tw, lane);
 }
 
@@ -593,7 +603,7 @@ __global__ void __launch_bounds__(kWarpRowThreads, (P <= 4 ? 2 : 1)) row_pass_wa
             z[p][q].y = A.y + B.x;
           }
         __syncwarp();
-        warp_fft_inv_any<P, 3, T>(z, tw, lane);
+        warp_fft_inv_any<P, 3, T, true>(z, tw, lane);
       }
       if constexpr (KINV) {
         const T* Yl = Yaux ? Yaux + (size_t)load * NV * cstrE : Eload;
@@ -663,7 +673,7 @@ __global__ void __launch_bounds__(kWarpRowThreads, (P <= 4 ? 2 : 1)) row_pass_wa
       }
       // 4. forward FFT, then split each line's spectrum into the half
       //    spectra of its two components
-      warp_fft_fwd_any<P, 3, T>(z, tw, lane);
+      warp_fft_fwd_any<P, 3, T, true>(z, tw, lane);
 #pragma unroll
       for (int p = 0; p < 3; ++p)
 #pragma unroll
