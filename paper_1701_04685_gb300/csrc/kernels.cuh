@@ -109,6 +109,10 @@ struct Control {
   int decoupled;     // 3-D phase tables with zero normal-shear blocks and a diagonal shear
                      // block (isotropic, cubic, orthotropic phases in the grid axes): the
                      // constitutive stage skips the structural zeros (stress6_decoupled)
+  int no_forward;    // two-step row pass: stop after the E update and the residual (no tau,
+                     // no forward transform); the spectra are then stale and a FIRST pass
+                     // must precede the next iteration
+  int pad3;
 };
 
 // tau = D x for a 6 x 6 Mandel matrix D whose normal-shear blocks are zero and

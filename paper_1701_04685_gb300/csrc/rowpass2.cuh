@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(Row2<R1, R2>::THREADS, sizeof(T) == 4 ? 3 : 1)
   __shared__ double red[32];
   __shared__ int s_skip;
   const bool decoupled = ctl->decoupled != 0;
+  const bool no_fwd = !FIRST && !KINV && ctl->no_forward != 0;
   const int load = blockIdx.x / blocks_per_load;
   const int qb = blockIdx.x - load * blocks_per_load;
   const long long row0 = (long long)qb * RB;
@@ -216,6 +217,7 @@ __global__ void __launch_bounds__(Row2<R1, R2>::THREADS, sizeof(T) == 4 ? 3 : 1)
         acc_d.add(rd);
         acc_n.add(rn);
       }
+      if (no_fwd) continue;
       int ph = phase[pt];
       if (!FH_IN(CK_ROW_PHASE, ph, 16)) ph = 0;
       if (decoupled) {
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(Row2<R1, R2>::THREADS, sizeof(T) == 4 ? 3 : 1)
     }
 
     // ---- forward: tau -> half spectra
-    if (!KINV) {
+    if (!KINV && !no_fwd) {
       __syncthreads();
       C v[K::A_PER][R1];
 #pragma unroll

@@ -100,6 +100,7 @@ struct fh_solver {
   float* Cp32 = nullptr;
   int form = 0;  // iteration form of the solve in progress (0 or 1)
   bool dc_decoupled = false;  // 3-D phase matrices and C0 with zero normal-shear blocks, diagonal shear block
+  bool polish = false;        // the FP64 phase of a mixed solve is in progress
   // autotuned (path, cluster size) per bulk precision [fp64, fp32]; path 0 = not tuned yet
   int tuned_path[2] = {0, 0};
   int tuned_cs[2] = {0, 0};
@@ -756,8 +757,30 @@ fh_status run_solve(fh_solver* s, int prec, int nload, int chunk, int max_iter, 
   CK(cudaEventRecord(s->ev0, s->work));
   enqueue_row_pass<T, true>(s, prec, nload);
   CK(cudaGetLastError());
-  long long launched = 0;
-  for (;;) {
+  long long launched = 0, extra = 0;
+  bool finished = false;
+  if (s->polish && prec == FH_PREC_FP64 && use_row2(s, prec) && !s->plane_on) {
+    // The FP64 phase of a mixed solve usually stops after its first
+    // iteration: that iteration's row pass ends after the E update and the
+    // residual (the two-step row pass skips tau and the forward transform).
+    // If a load goes on, a FIRST pass rebuilds the spectra from E (the same
+    // values the full pass would have written) before the graph replays.
+    enqueue_line_passes<T>(s, prec, nload);
+    CK(cudaMemsetAsync(&s->ctl->no_forward, 1, sizeof(int), s->work));
+    enqueue_row_pass<T, false>(s, prec, nload);
+    CK(cudaMemsetAsync(&s->ctl->no_forward, 0, sizeof(int), s->work));
+    CK(cudaGetLastError());
+    launched = 1;
+    CK(cudaMemcpyAsync(s->h_flag, &s->ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, s->work));
+    CK(cudaStreamSynchronize(s->work));
+    finished = *s->h_flag != 0;
+    if (!finished) {
+      enqueue_row_pass<T, true>(s, prec, nload);
+      CK(cudaGetLastError());
+      extra = 1;
+    }
+  }
+  while (!finished) {
     CK(cudaGraphLaunch(exec, s->work));
     launched += chunk;
     CK(cudaMemcpyAsync(s->h_flag, &s->ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, s->work));
@@ -774,7 +797,7 @@ fh_status run_solve(fh_solver* s, int prec, int nload, int chunk, int max_iter, 
                                                               s->mstress, bpl, s->field ? s->Cf64 : nullptr, s->nphase);
   CK(cudaGetLastError());
   CK(cudaEventRecord(s->ev1, s->work));
-  *launches = (s->skip_mean ? 1 : 2) + launched * (1 + line_launches_per_iter(s, prec));
+  *launches = (s->skip_mean ? 1 : 2) + extra + launched * (1 + line_launches_per_iter(s, prec));
   return FH_OK;
 }
 
@@ -2362,8 +2385,10 @@ static fh_status fh_solve_impl(fh_solver* s, int nload, const double* eps0, cons
     // the residual of the FP32 result, so it also removes the FP32 rounding
     LoadState st0[FH_MAX_LOADS];
     polish_start(A, st0);
+    s->polish = true;
     rc = solve_phase(s, nload, eps0, opts->tol, opts->max_iter, FH_PREC_FP64, 1, polish_chunk(chunk), path2, cs2,
                      st0, &B);
+    s->polish = false;
     if (rc != FH_OK) return rc;
   }
   return finish_solve(s, nload, eps0, A, &B, mixed, res);

@@ -86,3 +86,50 @@ def test_constitutive_stage_matches_oracle(fh, setup, inclusion, prec):
     assert worst < bound
     assert rel(out["mean_stress"], ref["mean_stress"]) < bound
     s.close()
+
+
+def _iso_case(fh, setup):
+    T, ids, centres, radii, C0, Gp = setup
+    p = fh.Pattern(M)
+    idx = {tuple(a): i for i, a in enumerate(T.points.tolist())}
+    perm = np.array([idx[tuple(a)] for a in p.numerators().tolist()])
+    Cp = np.stack([OM.isotropic_mandel(*OM.lame(E, 0.3), 3) for E in (1.0, 12.0)])
+    s = fh.Solver(p, fh.generator("dirichlet"), 6, 0)
+    s.set_stiffness_phases(ids[perm], Cp)
+    s.set_reference(None)
+    return s
+
+
+def test_mixed_mode_equals_fp32_then_fp64(fh, setup):
+    """Mixed precision (Sec. 4's fixed point in FP32 to the tolerance, then in FP64
+    to the same tolerance) gives the bits of an FP32 solve followed by an FP64 solve
+    that continues from its strain: the FP64 phase's first row pass, which stops
+    after the E update and the residual, leaves the same E."""
+    s = _iso_case(fh, setup)
+    eps0 = np.eye(6)
+    mixed = s.solve(eps0, tol=1e-6, max_iter=5000, precision=fh.FH_PREC_MIXED)
+    Em = [s.get_strain(L).copy() for L in range(6)]
+    a = s.solve(eps0, tol=1e-6, max_iter=5000, precision=fh.FH_PREC_FP32)
+    b = s.solve(eps0, tol=1e-6, max_iter=5000, precision=fh.FH_PREC_FP64, init=1)
+    assert list(mixed["iterations"]) == [i + j for i, j in zip(a["iterations"], b["iterations"])]
+    for L in range(6):
+        assert np.array_equal(s.get_strain(L), Em[L])
+    assert np.array_equal(np.asarray(b["mean_stress"]), np.asarray(mixed["mean_stress"]))
+    s.close()
+
+
+def test_mixed_mode_polish_of_several_iterations(fh, setup):
+    """A tolerance below the FP32 rounding floor: the FP32 phase stops on its stall
+    rule and the FP64 phase runs several iterations (the spectra rebuilt after its
+    first row pass); the result meets the FP64 solve at the same tolerance."""
+    s = _iso_case(fh, setup)
+    eps0 = np.eye(6)
+    ref = s.solve(eps0, tol=1e-10, max_iter=5000, precision=fh.FH_PREC_FP64)
+    E64 = [s.get_strain(L).copy() for L in range(6)]
+    C64 = s.get_ceff()
+    mixed = s.solve(eps0, tol=1e-10, max_iter=5000, precision=fh.FH_PREC_MIXED)
+    assert mixed["status"] == 0 and ref["status"] == 0
+    for L in range(6):
+        assert np.abs(s.get_strain(L) - E64[L]).max() < 1e-8
+    assert rel(s.get_ceff(), C64) < 1e-9
+    s.close()
