@@ -766,6 +766,7 @@ fh_status run_solve(fh_solver* s, int prec, int nload, int chunk, int max_iter, 
     // If a load goes on, a FIRST pass rebuilds the spectra from E (the same
     // values the full pass would have written) before the graph replays.
     enqueue_line_passes<T>(s, prec, nload);
+    // bytes of 1: any nonzero value sets the flag
     CK(cudaMemsetAsync(&s->ctl->no_forward, 1, sizeof(int), s->work));
     enqueue_row_pass<T, false>(s, prec, nload);
     CK(cudaMemsetAsync(&s->ctl->no_forward, 0, sizeof(int), s->work));
