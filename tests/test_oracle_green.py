@@ -1,4 +1,6 @@
 """Pins of the oracle's generator weights, Gamma^0 and Gamma^p (Sec. 2.2, 3.1, 3.2)."""
+import itertools
+
 import numpy as np
 import pytest
 
@@ -254,3 +256,43 @@ def test_literal_dirichlet_is_not_even():
     assert np.abs(a - b).max() > 1e-3
     sym = G.Generator("dirichlet")
     assert np.abs(green.gamma_p_table(M, sym, C0, h) - green.gamma_p_table(M, sym, C0, hn)).max() < 1e-15
+
+
+# ------------------------------------------------ symmetry of the cubic pattern
+
+_PAIRS3 = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]   # Mandel order in 3-D
+
+
+def _mandel_index(i, j):
+    return _PAIRS3.index((min(i, j), max(i, j)))
+
+
+@pytest.mark.parametrize("gen", [G.Generator("dirichlet"), G.Generator("dlvp", alpha=[0.3] * 3),
+                                 G.Generator("boxspline", xi=G.tensor_boxspline_xi(3, 2), radius=2)],
+                         ids=["dirichlet", "dlvp", "boxspline"])
+def test_gamma_p_follows_axis_permutations_and_mirrors(gen, rng):
+    """M = diag(N, N, N), an isotropic C0 and the same symbol on every axis: a
+    rotation R that permutes or mirrors the axes maps the alias set onto itself
+    and keeps the weights (Def. gamma_tilde_fourier), and Gamma^0 of an
+    isotropic C0 is covariant, so Gamma^p(R h)_ijkl = R_ia R_jb R_kc R_ld
+    Gamma^p(h)_abcd.  In Mandel form a permutation relabels the components and a
+    mirror of axis g flips the sign of the entries whose index pairs hold g an
+    odd number of times."""
+    N = 6
+    M = [[N, 0, 0], [0, N, 0], [0, 0, N]]
+    C0 = material.isotropic_mandel(2.0, 1.5, 3)
+    for _ in range(6):
+        h = rng.integers(-N // 2, N // 2, size=3)
+        Gh = green.gamma_p(M, gen, C0, h)
+        scale = np.abs(Gh).max()
+        for perm in itertools.permutations(range(3)):
+            hp = h[list(perm)]                     # (R h)_g = h_perm(g)
+            A = [_mandel_index(perm[i], perm[j]) for i, j in _PAIRS3]
+            assert np.abs(green.gamma_p(M, gen, C0, hp) - Gh[np.ix_(A, A)]).max() <= 1e-13 * scale
+        for g in range(3):
+            if h[g] == -N // 2:                    # -h_g would leave the reduced set
+                continue
+            hm = h.copy()
+            hm[g] = -h[g]
+            s = np.array([-1.0 if (i == g) != (j == g) else 1.0 for i, j in _PAIRS3])
+            assert np.abs(green.gamma_p(M, gen, C0, hm) - np.outer(s, s) * Gh).max() <= 1e-13 * scale
